@@ -1,0 +1,237 @@
+/*
+ * ndgsbp.h -- C ABI of the GB300 (sm_103a) NDGSBP decoding library.
+ *
+ * Non-disjoint group shuffled belief propagation (NDGSBP) decoding of binary LDPC codes, after
+ * Hsu, Chang, Su and Weng, "A Non-Disjoint Group Shuffled Decoding for LDPC Codes".  The
+ * library builds check-node (CN) groups from a parity-check matrix H and decodes batches of
+ * channel LLR frames on the GPU with a flooding, disjoint-group (GSBP) or overlapping-group
+ * (NDGSBP) schedule.
+ *
+ * Conventions for every call:
+ *   - Return value: NDGSBP_OK (0) or a negative ndgsbp_status.  On failure nothing is written
+ *     to the outputs and ndgsbp_last_error() returns a message for the calling thread.  No call
+ *     throws across the ABI.
+ *   - Pointers named d_* are device pointers (memory on the current CUDA device), all others
+ *     host pointers.  The caller owns every buffer it passes; the library owns only the opaque
+ *     handles it returns and the device copies of their descriptors.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Device
+ *     work is enqueued on it; outputs are valid once that stream has been synchronised.
+ *   - Sizes are element counts unless named *_bytes.  Arrays are row-major and contiguous.
+ *   - Handles are immutable after creation and may be shared by threads; one decode call at a
+ *     time may use a given workspace buffer.
+ */
+#ifndef NDGSBP_H
+#define NDGSBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ndgsbp_status;
+
+#define NDGSBP_OK 0
+#define NDGSBP_ERR_INVALID (-1)      /* bad argument, bad H, bad group list */
+#define NDGSBP_ERR_INFEASIBLE (-2)   /* (G, r) cannot be realised on this code */
+#define NDGSBP_ERR_CUDA (-3)         /* a CUDA runtime call failed (message has the detail) */
+#define NDGSBP_ERR_WORKSPACE (-4)    /* workspace missing or smaller than ndgsbp_workspace_size */
+#define NDGSBP_ERR_BUDGET (-5)       /* request exceeds the server's device-memory budget */
+#define NDGSBP_ERR_TIMEOUT (-6)      /* a bounded device or host wait ran out */
+#define NDGSBP_ERR_DEVICE (-7)       /* the kernel reported an error in its status word */
+#define NDGSBP_ERR_UNSUPPORTED (-8)  /* valid request this build does not handle (e.g. degree) */
+#define NDGSBP_ERR_NOMEM (-9)        /* host or device allocation failed */
+
+/* element types */
+#define NDGSBP_F32 0
+#define NDGSBP_F16 1
+#define NDGSBP_BF16 2
+#define NDGSBP_F64 3
+
+/* grouping units and flags for ndgsbp_groups_build */
+#define NDGSBP_UNIT_CN 0         /* groups are built from single CNs */
+#define NDGSBP_UNIT_LAYER 1      /* groups are built from layers of Z consecutive CNs (QC codes) */
+#define NDGSBP_GROUPS_CYCLIC 1   /* G windows around a ring of units (see ndgsbp_group_sizes) */
+#define NDGSBP_GROUPS_NATURAL 2  /* take units in index order instead of drawing them at random */
+
+/* schedules */
+#define NDGSBP_SCHEDULE_GROUPS 0 /* the groups of the handle: GSBP when disjoint, NDGSBP when not */
+#define NDGSBP_SCHEDULE_FLOOD 1  /* one group holding every CN: standard (flooding) BP */
+
+/* decode kernel variants */
+#define NDGSBP_VARIANT_AUTO 0    /* autotuned choice when cached, else the heuristic below */
+#define NDGSBP_VARIANT_SMEM 1    /* edge messages resident in shared memory (small codes) */
+#define NDGSBP_VARIANT_GLOBAL 2  /* edge messages in per-CTA global-memory slots */
+#define NDGSBP_VARIANT_QC 3      /* layered QC kernel: circulant index arithmetic, no tables */
+
+/* stats counters accumulated by ndgsbp_decode_ex (uint64 each) */
+#define NDGSBP_STAT_FRAMES 0
+#define NDGSBP_STAT_FRAME_ERRORS 1   /* decoded word != transmitted word */
+#define NDGSBP_STAT_BIT_ERRORS 2     /* over the N code bits */
+#define NDGSBP_STAT_UNDETECTED 3     /* syndrome satisfied but decoded word != transmitted word */
+#define NDGSBP_STAT_ITERATIONS 4     /* sum of iterations used */
+#define NDGSBP_STAT_UNSATISFIED 5    /* frames that stopped with a nonzero syndrome */
+#define NDGSBP_STATS_LEN 8
+
+typedef struct ndgsbp_code ndgsbp_code;
+typedef struct ndgsbp_groups ndgsbp_groups;
+
+/* Decoder parameters (Sec. II-C).  Use ndgsbp_params_default and change what you need. */
+typedef struct ndgsbp_params {
+    int32_t schedule;       /* NDGSBP_SCHEDULE_GROUPS or NDGSBP_SCHEDULE_FLOOD */
+    int32_t max_iter;       /* I_Max >= 1 */
+    int32_t msg_dtype;      /* storage type of CN->VN messages: F32, F16 or BF16 (math is FP32) */
+    float llr_max;          /* clip for VN->CN inputs and CN->VN outputs of Eq. (1), in (0, 30] */
+    int32_t early_stop;     /* 1: stop a frame at the first zero syndrome (Step 4 b) */
+    int32_t variant;        /* NDGSBP_VARIANT_* */
+    int32_t block_threads;  /* 0 = chosen by the library; else a multiple of 32, <= 1024 */
+    int32_t ctas_per_sm;    /* 0 = as many as fit; else an upper bound */
+} ndgsbp_params;
+
+/* Launch plan the library picked for a decode (filled by ndgsbp_decode_plan). */
+typedef struct ndgsbp_plan {
+    int32_t variant;        /* NDGSBP_VARIANT_SMEM / GLOBAL / QC */
+    int32_t block_threads;
+    int32_t grid;           /* persistent CTAs */
+    int32_t ctas_per_sm;
+    int32_t max_row_degree; /* compile-time degree bound of the kernel instance */
+    int32_t delta_in_smem;
+    int64_t smem_bytes;     /* dynamic shared memory per CTA */
+    int64_t workspace_bytes;
+    int64_t stored_edges;   /* edge slots per frame including tile padding */
+    int64_t edge_updates_per_iter; /* sum over groups of the CN degrees (the paper's cost unit) */
+} ndgsbp_plan;
+
+/* Optional extras of ndgsbp_decode_ex (all may be NULL / 0). */
+typedef struct ndgsbp_extras {
+    const uint32_t* d_ref_bits; /* transmitted word(s), packed like d_hard_bits; NULL = all-zero */
+    int32_t ref_per_frame;      /* 1: d_ref_bits is [n_frames][W]; 0: one word [W] for every frame */
+    uint64_t* d_stats;          /* [NDGSBP_STATS_LEN] counters, added to (caller zeroes them) */
+    uint64_t* d_iter_hist;      /* [max_iter + 1] frames per iteration count, added to */
+    uint64_t* d_start_ns;       /* [n_frames] device %globaltimer (ns) when each frame's decode began */
+    uint64_t* d_retire_ns;      /* [n_frames] device %globaltimer (ns) when each frame retired */
+    float* d_messages;          /* [n_frames][E] CN->VN messages at exit, CSR edge order */
+} ndgsbp_extras;
+
+/* Fill *p with: GROUPS schedule, max_iter 50, F32 messages, llr_max 20, early stop on, AUTO. */
+void ndgsbp_params_default(ndgsbp_params* p);
+
+/* Message for the last failed call on this thread ("" if none).  Owned by the library. */
+const char* ndgsbp_last_error(void);
+
+/* Library version string, e.g. "ndgsbp 1.0 sm_103a".  Owned by the library. */
+const char* ndgsbp_version(void);
+
+/* ---- Code (Sec. II-B: H as a bipartite graph with N VNs and M CNs) ------------------------
+ * Copy an M x N parity-check matrix given in CSR form: row_ptr[M+1] (row_ptr[0] = 0,
+ * nondecreasing) and col_idx[row_ptr[M]] with 0 <= col < N and no repeated column in a row.
+ * lift_Z > 0 declares a QC code whose rows come in M / lift_Z layers of lift_Z CNs in which
+ * every VN appears at most once (checked); 0 = unstructured.  *out receives a handle that
+ * ndgsbp_code_destroy frees.  Host-only: needs no GPU.
+ * Errors: INVALID for malformed CSR or a layer that repeats a VN; NOMEM. */
+ndgsbp_status ndgsbp_code_create(const int32_t* row_ptr, const int32_t* col_idx, int32_t M,
+                                 int32_t N, int32_t lift_Z, ndgsbp_code** out);
+ndgsbp_status ndgsbp_code_destroy(ndgsbp_code* code);
+/* Sizes of a code handle; any output pointer may be NULL. */
+ndgsbp_status ndgsbp_code_info(const ndgsbp_code* code, int32_t* M, int32_t* N, int64_t* E,
+                               int32_t* max_row_degree, int32_t* max_col_degree, int32_t* lift_Z);
+
+/* ---- Grouping (Sec. II-A size relation, Sec. II-C Step 1) --------------------------------
+ * Group sizes from G N_G - (G-1) N_G r = M over M_units units:
+ *   linear:  N_G = ceil(M_units / (G - (G-1) r)), overlap o = round-half-up(r N_G); group 1 has
+ *            N_G units, groups 2..G take o units from their predecessor plus fresh units that
+ *            share the other M_units - N_G as evenly as possible (larger shares first).
+ *   CYCLIC:  stride s = M_units / G (must divide), o = round-half-up(r s / (1 - r)), N_G = s + o;
+ *            window g is units (g s + j) mod M_units of the drawn order, j < N_G.
+ * Errors: INVALID when G < 1, G > M_units or r outside [0, 1); INFEASIBLE when a group would
+ * get no fresh unit or the cyclic stride does not divide. */
+ndgsbp_status ndgsbp_group_sizes(int32_t M_units, int32_t G, double r, int32_t flags,
+                                 int32_t* NG, int32_t* overlap);
+
+/* Step 1 of Sec. II-C.  Units (CNs, or layers of Z CNs for NDGSBP_UNIT_LAYER) are drawn with a
+ * forward Fisher-Yates shuffle driven by SplitMix64(seed): draw step i swaps position i with
+ * position i + (next() mod (remaining)).  G_1 takes the first N_G drawn units; G_g takes the
+ * last o units of G_{g-1} followed by the next fresh units drawn (the overlap is a uniformly
+ * random subset of G_{g-1} \ G_{g-2} whenever o does not exceed that set).  r = 0 gives
+ * disjoint groups (GSBP); G = 1 gives one group of every CN (flooding).  The groups are kept
+ * for every iteration.  Host-only.  *out receives a handle freed by ndgsbp_groups_destroy; it
+ * keeps its own copy of the code.  Errors: as ndgsbp_group_sizes, INVALID for UNIT_LAYER on a
+ * code without lift_Z, NOMEM. */
+ndgsbp_status ndgsbp_groups_build(const ndgsbp_code* code, int32_t G, double r, uint64_t seed,
+                                  int32_t unit, int32_t flags, ndgsbp_groups** out);
+
+/* Explicit groups: grp_ptr[G+1] offsets into cn_idx[grp_ptr[G]] (0-based CN indices).  A CN
+ * may appear in several groups but at most once per group.  Host-only.  Errors: INVALID. */
+ndgsbp_status ndgsbp_groups_from_lists(const ndgsbp_code* code, const int32_t* grp_ptr,
+                                       const int32_t* cn_idx, int32_t G, ndgsbp_groups** out);
+
+/* Read a grouping back.  Any output may be NULL.  grp_ptr needs G+1 entries and cn_idx
+ * n_entries entries (query both counts first with the arrays NULL).  cocsg is the paper's
+ * l: the mean over consecutive groups of the VNs adjacent to both (Sec. I, II-B).
+ * cn_updates_per_iter = sum of group sizes; edge_updates_per_iter = sum of their CN degrees. */
+ndgsbp_status ndgsbp_groups_query(const ndgsbp_groups* groups, int32_t* G, int64_t* n_entries,
+                                  int32_t* grp_ptr, int32_t* cn_idx, double* cocsg,
+                                  int64_t* cn_updates_per_iter, int64_t* edge_updates_per_iter);
+ndgsbp_status ndgsbp_groups_destroy(ndgsbp_groups* groups);
+
+/* ---- Channel (Sec. II-C: BPSK over AWGN, L_n = 2 y_n / sigma^2) --------------------------
+ * Write n_frames x N channel LLRs to d_llr (dtype F32, F16 or BF16) for the word(s) in
+ * d_codeword_bits (packed like d_hard_bits; NULL = all-zero word; codeword_per_frame selects
+ * [n_frames][W] or one [W]).  sigma^2 = 1 / (2 rate 10^(ebn0_db/10)).  Normals come from
+ * Philox4x32-10 keyed by seed with counter (b, frame low, frame high, 0) for VNs 4b..4b+3,
+ * u = ((x >> 9) + 1/2) 2^-23 (exact in FP32), and Box-Muller on (u0, u1) and (u2, u3) (cos
+ * then sin).
+ * Errors: INVALID (rate <= 0, bad dtype), CUDA. */
+ndgsbp_status ndgsbp_awgn_llr(const ndgsbp_code* code, int64_t n_frames, double ebn0_db,
+                              double rate, uint64_t seed, const uint32_t* d_codeword_bits,
+                              int32_t codeword_per_frame, void* d_llr, int32_t dtype, void* stream);
+
+/* Raw Philox4x32-10 blocks for testing the generator: d_ctr[n][4] -> d_out[n][4] under key
+ * (key0, key1).  Errors: INVALID, CUDA. */
+ndgsbp_status ndgsbp_philox4x32_10(const uint32_t* d_ctr, uint32_t key0, uint32_t key1,
+                                   int64_t n, uint32_t* d_out, void* stream);
+
+/* ---- Decoding (Sec. II-C Steps 2-4) -------------------------------------------------------
+ * Launch plan and workspace size for decoding n_frames frames on the current device.  Uploads
+ * the grouping's device descriptor on first use on a device (allocates; call before any
+ * stream capture).  Errors: INVALID, UNSUPPORTED (CN degree above 32), CUDA. */
+ndgsbp_status ndgsbp_decode_plan(const ndgsbp_groups* groups, const ndgsbp_params* params,
+                                 int64_t n_frames, ndgsbp_plan* plan);
+ndgsbp_status ndgsbp_workspace_size(const ndgsbp_groups* groups, const ndgsbp_params* params,
+                                    int64_t n_frames, size_t* bytes);
+
+/* Decode n_frames frames of channel LLRs d_llr [n_frames][N] (llr_dtype F32, F64, F16 or
+ * BF16).  Per frame and iteration l = 1..max_iter, each group g in order runs Step 2: every CN
+ * of the group computes Eq. (1) from VN->CN messages L_{n->m} = P_n - L_{m->n} taken at the start
+ * of the sub-iteration (P_n is the running total LLR of Eq. (3)), with inputs and outputs
+ * clipped to llr_max; then P_n absorbs the change of every message of the group (Eq. (2) in
+ * posterior form), in a fixed order.  After the last group, Step 4: d_n = 1 iff P_n < 0; the
+ * frame stops when D H^T = 0 (early_stop) or l = max_iter.  Messages start at 0.
+ * Outputs: d_hard_bits [n_frames][W], W = ceil(N/32), bit n%32 of word n/32 is d_n (required);
+ * d_iters [n_frames] iterations used in 1..max_iter; d_syndrome_ok [n_frames] 1 if D H^T = 0 at
+ * exit; d_posterior [n_frames][N] P_n at exit (FP32).  The last three may be NULL.
+ * d_workspace: device buffer of at least ndgsbp_workspace_size bytes, 256-byte aligned.
+ * Frames are independent: a frame's result does not depend on the others in the batch.
+ * Errors: INVALID, WORKSPACE, UNSUPPORTED, CUDA (launch errors; execution errors surface at
+ * the caller's next synchronisation). */
+ndgsbp_status ndgsbp_decode(const ndgsbp_groups* groups, const ndgsbp_params* params,
+                            const void* d_llr, int32_t llr_dtype, int64_t n_frames,
+                            void* d_workspace, size_t workspace_bytes, uint32_t* d_hard_bits,
+                            int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
+                            void* stream);
+
+/* ndgsbp_decode plus the fused statistics epilogue and debug outputs of ndgsbp_extras
+ * (FER/BER counters against the transmitted word, iteration histogram, retire timestamps,
+ * final CN->VN messages).  extras may be NULL. */
+ndgsbp_status ndgsbp_decode_ex(const ndgsbp_groups* groups, const ndgsbp_params* params,
+                               const void* d_llr, int32_t llr_dtype, int64_t n_frames,
+                               void* d_workspace, size_t workspace_bytes, uint32_t* d_hard_bits,
+                               int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
+                               const ndgsbp_extras* extras, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NDGSBP_H */

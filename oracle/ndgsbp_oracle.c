@@ -660,7 +660,8 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
  * sigma^2 = 1 / (2 R 10^(EbN0/10)).  The normal samples follow one fixed definition that the
  * CUDA generator implements on its own:
  *   key = (seed mod 2^32, seed div 2^32); for frame f and block b, counter = (b, f mod 2^32,
- *   f div 2^32, 0); the four outputs x_i give u_i = ((x_i >> 8) + 1/2) 2^-24 in (0, 1);
+ *   f div 2^32, 0); the four outputs x_i give u_i = ((x_i >> 9) + 1/2) 2^-23 in (0, 1) (a value
+ *   every binary32 implementation represents exactly);
  *   Box-Muller: z_{4b}   = sqrt(-2 ln u_0) cos(2 pi u_1),  z_{4b+1} = sqrt(-2 ln u_0) sin(2 pi u_1),
  *               z_{4b+2} = sqrt(-2 ln u_2) cos(2 pi u_3),  z_{4b+3} = sqrt(-2 ln u_2) sin(2 pi u_3).
  * codeword: NULL (all-zero word) or [N] bits. */
@@ -677,7 +678,7 @@ int oracle_awgn_llr(int N, long n_frames, double ebn0_db, double rate, uint64_t 
             uint32_t x[4];
             oracle_philox4x32_10(ctr, key, x);
             double u[4], z[4];
-            for (int i = 0; i < 4; ++i) u[i] = ((double)(x[i] >> 8) + 0.5) * (1.0 / 16777216.0);
+            for (int i = 0; i < 4; ++i) u[i] = ((double)(x[i] >> 9) + 0.5) * (1.0 / 8388608.0);
             double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
             z[0] = r0 * cos(two_pi * u[1]);
             z[1] = r0 * sin(two_pi * u[1]);

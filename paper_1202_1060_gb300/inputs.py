@@ -331,21 +331,25 @@ def sigma2_from_ebn0(ebn0_db: float, rate: float) -> float:
 
 
 def channel_llr(N: int, n_frames: int, ebn0_db: float, rate: float, seed: int,
-                codeword: np.ndarray | None = None) -> np.ndarray:
-    """Channel LLRs [n_frames, N] (float64) for BPSK (bit 0 -> +1) over AWGN.
+                codeword: np.ndarray | None = None, dtype=np.float64) -> np.ndarray:
+    """Channel LLRs [n_frames, N] for BPSK (bit 0 -> +1) over AWGN.
 
     y = (1 - 2 c) + sigma * z with z ~ N(0, 1) from numpy's PCG64 stream seeded by ``seed``,
     and L = 2 y / sigma^2 (Sec. II-C).  ``codeword`` is one word [N] or one per frame
-    [n_frames, N]; None sends the all-zero word.
+    [n_frames, N]; None sends the all-zero word.  dtype float32 draws and computes in single
+    precision (a different stream from float64), for batches too large to hold in float64.
     """
+    dtype = np.dtype(dtype)
     s2 = sigma2_from_ebn0(ebn0_db, rate)
     rng = np.random.Generator(np.random.PCG64(seed))
-    z = rng.standard_normal((n_frames, N))
-    x = np.ones((n_frames, N))
-    if codeword is not None:
-        x = 1.0 - 2.0 * np.broadcast_to(np.asarray(codeword, np.float64), (n_frames, N))
-    y = x + math.sqrt(s2) * z
-    return 2.0 * y / s2
+    z = rng.standard_normal((n_frames, N), dtype=dtype)
+    z *= dtype.type(math.sqrt(s2))
+    if codeword is None:
+        z += dtype.type(1.0)
+    else:
+        z += (1.0 - 2.0 * np.broadcast_to(np.asarray(codeword, dtype), (n_frames, N))).astype(dtype)
+    z *= dtype.type(2.0 / s2)
+    return z
 
 
 def _gf2_nullspace(code: Code) -> np.ndarray:

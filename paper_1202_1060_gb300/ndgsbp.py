@@ -1,0 +1,318 @@
+"""Python binding of the NDGSBP C ABI (include/ndgsbp.h).
+
+Argument marshalling only: every step of decoding runs in the CUDA library.  Device buffers
+are torch tensors (their data_ptr() is passed through), streams are torch CUDA streams.
+Importing this module loads paper_1202_1060_gb300/_lib/libndgsbp.so and raises if it is
+missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libndgsbp.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"NDGSBP CUDA library not built ({_LIB_PATH} missing): run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'` first")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+OK = 0
+ERR_INVALID, ERR_INFEASIBLE, ERR_CUDA, ERR_WORKSPACE = -1, -2, -3, -4
+ERR_BUDGET, ERR_TIMEOUT, ERR_DEVICE, ERR_UNSUPPORTED, ERR_NOMEM = -5, -6, -7, -8, -9
+F32, F16, BF16, F64 = 0, 1, 2, 3
+UNIT_CN, UNIT_LAYER = 0, 1
+GROUPS_CYCLIC, GROUPS_NATURAL = 1, 2
+SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
+VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC = 0, 1, 2, 3
+STAT_FRAMES, STAT_FRAME_ERRORS, STAT_BIT_ERRORS, STAT_UNDETECTED = 0, 1, 2, 3
+STAT_ITERATIONS, STAT_UNSATISFIED, STATS_LEN = 4, 5, 8
+
+
+class NdgsbpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("msg_dtype", ctypes.c_int32), ("llr_max", ctypes.c_float),
+                ("early_stop", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("max_row_degree", ctypes.c_int32), ("delta_in_smem", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("stored_edges", ctypes.c_int64), ("edge_updates_per_iter", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Extras(ctypes.Structure):
+    _fields_ = [("d_ref_bits", ctypes.c_void_p), ("ref_per_frame", ctypes.c_int32),
+                ("d_stats", ctypes.c_void_p), ("d_iter_hist", ctypes.c_void_p),
+                ("d_start_ns", ctypes.c_void_p), ("d_retire_ns", ctypes.c_void_p),
+                ("d_messages", ctypes.c_void_p)]
+
+
+_P, _I32, _I64, _U64, _D, _U32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                  ctypes.c_double, ctypes.c_uint32)
+_SIGS = {
+    "ndgsbp_params_default": (None, [ctypes.POINTER(Params)]),
+    "ndgsbp_last_error": (ctypes.c_char_p, []),
+    "ndgsbp_version": (ctypes.c_char_p, []),
+    "ndgsbp_code_create": (_I32, [_P, _P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
+    "ndgsbp_code_destroy": (_I32, [_P]),
+    "ndgsbp_code_info": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+    "ndgsbp_group_sizes": (_I32, [_I32, _I32, _D, _I32, _P, _P]),
+    "ndgsbp_groups_build": (_I32, [_P, _I32, _D, _U64, _I32, _I32, ctypes.POINTER(_P)]),
+    "ndgsbp_groups_from_lists": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_P)]),
+    "ndgsbp_groups_query": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "ndgsbp_groups_destroy": (_I32, [_P]),
+    "ndgsbp_awgn_llr": (_I32, [_P, _I64, _D, _D, _U64, _P, _I32, _P, _I32, _P]),
+    "ndgsbp_philox4x32_10": (_I32, [_P, _U32, _U32, _I64, _P, _P]),
+    "ndgsbp_decode_plan": (_I32, [_P, ctypes.POINTER(Params), _I64, ctypes.POINTER(Plan)]),
+    "ndgsbp_workspace_size": (_I32, [_P, ctypes.POINTER(Params), _I64, ctypes.POINTER(ctypes.c_size_t)]),
+    "ndgsbp_decode": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, ctypes.c_size_t,
+                             _P, _P, _P, _P, _P]),
+    "ndgsbp_decode_ex": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, ctypes.c_size_t,
+                                _P, _P, _P, _P, ctypes.POINTER(Extras), _P]),
+}
+
+
+def _bind(lib, sigs):
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+_bind(_lib, _SIGS)
+DECLARED_SYMBOLS = tuple(_SIGS)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def last_error() -> str:
+    return _lib.ndgsbp_last_error().decode()
+
+
+def version() -> str:
+    return _lib.ndgsbp_version().decode()
+
+
+def _check(status: int):
+    if status != OK:
+        raise NdgsbpError(status, last_error())
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _addr(t):
+    """Device address of a CUDA tensor as an int (None for None)."""
+    return None if t is None else _dptr(t).value
+
+
+def _hptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream) or 0)
+
+
+def params_default(**overrides) -> Params:
+    p = Params()
+    _lib.ndgsbp_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def group_sizes(M_units: int, G: int, r: float, flags: int = 0):
+    ng, o = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.ndgsbp_group_sizes(M_units, G, float(r), flags, ctypes.byref(ng), ctypes.byref(o)))
+    return ng.value, o.value
+
+
+class Code:
+    """Owned ndgsbp_code handle (ndgsbp_code_create / ndgsbp_code_destroy)."""
+
+    def __init__(self, row_ptr, col_idx, M: int, N: int, lift_Z: int = 0):
+        rp = np.ascontiguousarray(row_ptr, np.int32)
+        ci = np.ascontiguousarray(col_idx, np.int32)
+        h = ctypes.c_void_p()
+        _check(_lib.ndgsbp_code_create(_hptr(rp), _hptr(ci), M, N, lift_Z, ctypes.byref(h)))
+        self._h = h
+        self.M, self.N, self.E, self.Z = M, N, int(rp[-1]), lift_Z
+
+    @classmethod
+    def from_inputs(cls, code):
+        """From a paper_1202_1060_gb300.inputs.Code."""
+        return cls(code.row_ptr, code.col_idx, code.M, code.N, code.Z)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        M, N, mr, mc, Z = (ctypes.c_int32() for _ in range(5))
+        E = ctypes.c_int64()
+        _check(_lib.ndgsbp_code_info(self._h, ctypes.byref(M), ctypes.byref(N), ctypes.byref(E),
+                                     ctypes.byref(mr), ctypes.byref(mc), ctypes.byref(Z)))
+        return dict(M=M.value, N=N.value, E=E.value, max_row_degree=mr.value,
+                    max_col_degree=mc.value, lift_Z=Z.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.ndgsbp_code_destroy(h)
+            self._h = None
+
+
+class Groups:
+    """Owned ndgsbp_groups handle (Step 1 grouping plus its device layout)."""
+
+    def __init__(self, handle, code: Code):
+        self._h = handle
+        self.code = code
+
+    @classmethod
+    def build(cls, code: Code, G: int, r: float, seed: int, unit: int = UNIT_CN, flags: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib.ndgsbp_groups_build(code.handle, G, float(r), seed & (2**64 - 1), unit, flags,
+                                        ctypes.byref(h)))
+        return cls(h, code)
+
+    @classmethod
+    def from_lists(cls, code: Code, grp_ptr, cn_idx):
+        gp = np.ascontiguousarray(grp_ptr, np.int32)
+        gc = np.ascontiguousarray(cn_idx, np.int32)
+        h = ctypes.c_void_p()
+        _check(_lib.ndgsbp_groups_from_lists(code.handle, _hptr(gp), _hptr(gc), len(gp) - 1,
+                                             ctypes.byref(h)))
+        return cls(h, code)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def query(self):
+        G, n = ctypes.c_int32(), ctypes.c_int64()
+        _check(_lib.ndgsbp_groups_query(self._h, ctypes.byref(G), ctypes.byref(n), None, None,
+                                        None, None, None))
+        gp = np.zeros(G.value + 1, np.int32)
+        gc = np.zeros(n.value, np.int32)
+        cocsg = ctypes.c_double()
+        cnu, edu = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.ndgsbp_groups_query(self._h, None, None, _hptr(gp), _hptr(gc), ctypes.byref(cocsg),
+                                        ctypes.byref(cnu), ctypes.byref(edu)))
+        return dict(G=G.value, grp_ptr=gp, cn_idx=gc, cocsg=cocsg.value,
+                    cn_updates_per_iter=cnu.value, edge_updates_per_iter=edu.value)
+
+    def plan(self, params: Params, n_frames: int) -> Plan:
+        pl = Plan()
+        _check(_lib.ndgsbp_decode_plan(self._h, ctypes.byref(params), n_frames, ctypes.byref(pl)))
+        return pl
+
+    def workspace_size(self, params: Params, n_frames: int) -> int:
+        b = ctypes.c_size_t()
+        _check(_lib.ndgsbp_workspace_size(self._h, ctypes.byref(params), n_frames, ctypes.byref(b)))
+        return b.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.ndgsbp_groups_destroy(h)
+            self._h = None
+
+
+_DT = {}
+
+
+def dtype_code(t) -> int:
+    import torch
+    if not _DT:
+        _DT.update({torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16, torch.float64: F64})
+    return _DT[t.dtype]
+
+
+def awgn_llr(code: Code, n_frames: int, ebn0_db: float, rate: float, seed: int, out,
+             codeword_bits=None, codeword_per_frame: bool = False, stream=None):
+    """ndgsbp_awgn_llr into the CUDA tensor ``out`` [n_frames, N] (float32/16/bf16)."""
+    _check(_lib.ndgsbp_awgn_llr(code.handle, n_frames, float(ebn0_db), float(rate), seed & (2**64 - 1),
+                                _dptr(codeword_bits), int(codeword_per_frame), _dptr(out),
+                                dtype_code(out), _stream(stream)))
+    return out
+
+
+def philox4x32_10(ctr, key0: int, key1: int, out, stream=None):
+    """Raw Philox4x32-10 blocks: ctr, out are CUDA int32/uint32 tensors [n, 4]."""
+    _check(_lib.ndgsbp_philox4x32_10(_dptr(ctr), key0 & 0xFFFFFFFF, key1 & 0xFFFFFFFF, ctr.shape[0],
+                                     _dptr(out), _stream(stream)))
+    return out
+
+
+def decode(groups: Groups, params: Params, llr, workspace, hard_bits, iters=None, syndrome_ok=None,
+           posterior=None, ref_bits=None, ref_per_frame: bool = False, stats=None, iter_hist=None,
+           start_ns=None, retire_ns=None, messages=None, stream=None):
+    """ndgsbp_decode_ex on CUDA tensors; llr is [n_frames, N]."""
+    n_frames = llr.shape[0]
+    ex = Extras(d_ref_bits=_addr(ref_bits), ref_per_frame=int(ref_per_frame), d_stats=_addr(stats),
+                d_iter_hist=_addr(iter_hist), d_start_ns=_addr(start_ns), d_retire_ns=_addr(retire_ns),
+                d_messages=_addr(messages))
+    _check(_lib.ndgsbp_decode_ex(groups.handle, ctypes.byref(params), _dptr(llr), dtype_code(llr), n_frames,
+                                 _dptr(workspace), workspace.numel() * workspace.element_size(),
+                                 _dptr(hard_bits), _dptr(iters), _dptr(syndrome_ok), _dptr(posterior),
+                                 ctypes.byref(ex), _stream(stream)))
+
+
+def decode_plain(groups: Groups, params: Params, llr, workspace, hard_bits, iters=None, syndrome_ok=None,
+                 posterior=None, stream=None):
+    """ndgsbp_decode (no extras)."""
+    _check(_lib.ndgsbp_decode(groups.handle, ctypes.byref(params), _dptr(llr), dtype_code(llr), llr.shape[0],
+                              _dptr(workspace), workspace.numel() * workspace.element_size(),
+                              _dptr(hard_bits), _dptr(iters), _dptr(syndrome_ok), _dptr(posterior),
+                              _stream(stream)))
+
+
+def unpack_bits(words, N: int):
+    """Packed decisions [F, W] (int32/uint32, numpy or torch) -> uint8 [F, N] (host)."""
+    a = words.cpu().numpy() if hasattr(words, "cpu") else np.asarray(words)
+    a = np.ascontiguousarray(a).view(np.uint32)
+    bits = ((a[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).astype(np.uint8)
+    return bits.reshape(a.shape[0], -1)[:, :N]
+
+
+def pack_bits(bits):
+    """uint8 [F, N] or [N] (host) -> packed uint32 words as int32 numpy [F, W] / [W]."""
+    b = np.atleast_2d(np.asarray(bits, np.uint8))
+    F, N = b.shape
+    W = (N + 31) // 32
+    pad = np.zeros((F, W * 32), np.uint64)
+    pad[:, :N] = b
+    words = (pad.reshape(F, W, 32) << np.arange(32, dtype=np.uint64)).sum(axis=2).astype(np.uint32)
+    out = words.view(np.int32)
+    return out if np.ndim(bits) == 2 else out[0]
