@@ -314,7 +314,7 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = MUFU_PER_CLK_PER_SM * sms * peak_clock_mhz * 1e6 / 1e12
-    kname = "decode_kernel" if plan.variant != nd.VARIANT_QC else "decode_qc_kernel"
+    kname = "qc_decode_kernel" if plan.variant in (nd.VARIANT_QC, nd.VARIANT_QC_GLOBAL) else "decode_kernel"
     traffic, traffic_rec = profiled_traffic(kname)
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,

@@ -1,4 +1,5 @@
-// Batched NDGSBP decode kernels for sm_103a and their launcher.
+// Batched NDGSBP decoding for sm_103a: the general (table-driven) kernel and the host-side
+// planner and launcher for every decode kernel.
 //
 // One persistent CTA decodes one frame at a time and takes the next frame from an atomic
 // counter when it finishes, so frames that stop early (Step 4 b) free their CTA at once.
@@ -14,26 +15,20 @@
 //   B) P_n += change for every edge of the group, in "colour" order: colour c of an edge is
 //      the number of earlier edges of the group on the same VN, so each colour touches a VN at
 //      most once and the sum order is fixed (results do not depend on scheduling or batch).
-//
-// Eq. (1) is evaluated as a product of tanh(x/2) factors held as pairs (N, E) with
-// tanh(x/2) = N / (N + E): one edge with u = exp(-|x|) is (1 - u, 2 u) up to a common scale,
-// two pairs combine as (Na Nb, Ea (Eb + Nb) + Na Eb), and 2 atanh(N / (N + E)) = ln(1 + 2 N / E).
-// All terms are positive, so nothing cancels: both saturated inputs (tanh near 1) and tiny
-// ones keep full FP32 relative accuracy, and each edge costs one exp2, one reciprocal and one
-// log2.  The exclusion "all edges but k" uses prefix and suffix combinations (no division).
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
-
+// The layered QC kernel (decode_qc.cu) runs the same two phases with circulant index
+// arithmetic instead of tables.
 #include <algorithm>
 #include <cstring>
 
+#include "decode_qc.h"
+#include "device_common.cuh"
 #include "ndgsbp_internal.h"
 
 namespace ndgsbp {
 
 struct DecodeArgs {
-    int M, N, E, Epad, G, max_gd, W;
+    RunArgs r;
+    int M, Epad, G, max_gd;
     const int32_t* slot_deg;
     const int32_t* tile_base;
     const int32_t* edge_vn;
@@ -44,67 +39,9 @@ struct DecodeArgs {
     const int32_t* grp_colbase;
     const int32_t* grp_ncol;
     const uint8_t* gcol;
-    const void* llr;
-    int llr_dtype;
-    long long n_frames;
-    int max_iter;
-    float llr_max;
-    int early_stop;
     void* ws_msgs;
     float* ws_delta;
-    unsigned long long* counter;
-    uint32_t* hard_bits;
-    int32_t* iters;
-    uint8_t* synd_ok;
-    float* posterior;
-    const uint32_t* ref_bits;
-    int ref_per_frame;
-    unsigned long long* stats;
-    unsigned long long* iter_hist;
-    unsigned long long* start_ns;
-    unsigned long long* retire_ns;
-    float* msgs_out;
 };
-
-// ---- small device helpers ---------------------------------------------------------------
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float lg2_approx(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ unsigned long long global_timer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-template <typename T> __device__ __forceinline__ float to_f(T v);
-template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
-template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <typename T> __device__ __forceinline__ T from_f(float v);
-template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-
-__device__ __forceinline__ float load_llr(const void* p, int dtype, long long i) {
-    switch (dtype) {
-        case NDGSBP_F64: return static_cast<float>(static_cast<const double*>(p)[i]);
-        case NDGSBP_F16: return __half2float(static_cast<const __half*>(p)[i]);
-        case NDGSBP_BF16: return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
-        default: return static_cast<const float*>(p)[i];
-    }
-}
 
 // Phase A for one group entry: Eq. (1) on every edge of the entry's CN.
 template <int MAXDC, typename MsgT>
@@ -114,45 +51,20 @@ __device__ __forceinline__ void cn_update_entry(const DecodeArgs& a, const float
     const int d = __ldg(a.slot_deg + s);
     const int eb = __ldg(a.tile_base + (s >> 5)) + (s & 31);
     const int db = __ldg(a.ge_dpos + i);
-    const float lim = a.llr_max;
-    float xn[MAXDC], xe[MAXDC], old[MAXDC], pn[MAXDC], pe[MAXDC];
-    unsigned neg = 0u;
-    float cn = 1.f, ce = 0.f;
+    float t[MAXDC], old[MAXDC];
 #pragma unroll
     for (int k = 0; k < MAXDC; ++k) {
         if (k < d) {
             const int v = __ldg(a.edge_vn + eb + 32 * k);
-            const float o = to_f(msg[eb + 32 * k]);
-            const float t = P[v] - o;
-            old[k] = o;
-            neg |= (t < 0.f ? 1u : 0u) << k;
-            const float x = fminf(fabsf(t), lim);
-            const float u = ex2_approx(x * -1.4426950408889634f);   // exp(-x)
-            xn[k] = fmaf(-0.5f, u, 0.5f);                           // (1 - u) / 2
-            xe[k] = u;                                              // (2 u) / 2
-            pn[k] = cn;
-            pe[k] = ce;
-            ce = fmaf(ce, xn[k] + xe[k], cn * xe[k]);
-            cn = cn * xn[k];
+            old[k] = to_f(msg[eb + 32 * k]);
+            t[k] = P[v] - old[k];
         }
     }
-    const unsigned par = __popc(neg) & 1u;
-    float sn = 1.f, se = 0.f;
-#pragma unroll
-    for (int k = MAXDC - 1; k >= 0; --k) {
-        if (k < d) {
-            const float en = pn[k] * sn;
-            const float ee = fmaf(pe[k], sn + se, pn[k] * se);
-            const float w = 2.f * en * rcp_approx(ee);
-            const float mag = fminf(0.69314718055994531f * lg2_approx(1.f + w), lim);
-            const float val = ((par ^ (neg >> k)) & 1u) ? -mag : mag;
-            const MsgT q = from_f<MsgT>(val);
-            msg[eb + 32 * k] = q;
-            delta[db + 32 * k] = to_f(q) - old[k];
-            se = fmaf(se, xn[k] + xe[k], sn * xe[k]);
-            sn = sn * xn[k];
-        }
-    }
+    check_node_update<MAXDC>(t, d, a.r.llr_max, [&](int k, float val) {
+        const MsgT q = from_f<MsgT>(val);
+        msg[eb + 32 * k] = q;
+        delta[db + 32 * k] = to_f(q) - old[k];
+    });
 }
 
 // Phase B for one group entry and one colour.
@@ -181,59 +93,15 @@ __device__ __forceinline__ unsigned slot_parity(const DecodeArgs& a, const float
     return p;
 }
 
-// Frame epilogue shared by the kernels: hard decisions, outputs, fused statistics.
-__device__ void write_frame_outputs(const DecodeArgs& a, const float* __restrict__ P, long long f,
-                                    int iters, int unsat, unsigned* s_err) {
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const int W = a.W;
-    unsigned err = 0u;
-    for (int w = warp; w < W; w += nw) {
-        const int n = 32 * w + lane;
-        const bool bit = (n < a.N) && (P[n] < 0.f);
-        const unsigned word = __ballot_sync(0xffffffffu, bit);
-        if (lane == 0) {
-            a.hard_bits[f * W + w] = word;
-            if (a.stats) {
-                const unsigned ref = a.ref_bits ? a.ref_bits[(a.ref_per_frame ? f * W : 0) + w] : 0u;
-                err += __popc(word ^ ref);
-            }
-        }
-    }
-    if (a.posterior)
-        for (int n = tid; n < a.N; n += nt) a.posterior[f * a.N + n] = P[n];
-    if (a.stats && lane == 0 && err) atomicAdd(s_err, err);
-    __syncthreads();
-    if (tid == 0) {
-        if (a.iters) a.iters[f] = iters;
-        if (a.synd_ok) a.synd_ok[f] = unsat ? 0 : 1;
-        if (a.stats) {
-            const unsigned e = *s_err;
-            atomicAdd(a.stats + NDGSBP_STAT_FRAMES, 1ull);
-            atomicAdd(a.stats + NDGSBP_STAT_ITERATIONS, static_cast<unsigned long long>(iters));
-            if (e) {
-                atomicAdd(a.stats + NDGSBP_STAT_FRAME_ERRORS, 1ull);
-                atomicAdd(a.stats + NDGSBP_STAT_BIT_ERRORS, static_cast<unsigned long long>(e));
-                if (!unsat) atomicAdd(a.stats + NDGSBP_STAT_UNDETECTED, 1ull);
-            }
-            if (unsat) atomicAdd(a.stats + NDGSBP_STAT_UNSATISFIED, 1ull);
-            *s_err = 0u;
-        }
-        if (a.iter_hist) atomicAdd(a.iter_hist + iters, 1ull);
-        if (a.retire_ns) a.retire_ns[f] = global_timer_ns();
-    }
-}
-
-// Largest CTA of a kernel instance: the per-edge register arrays grow with the degree bound.
-__host__ __device__ constexpr int max_threads_for(int maxdc) { return maxdc <= 8 ? 1024 : maxdc <= 16 ? 512 : 256; }
-
 template <typename MsgT, bool MSG_SMEM, bool DELTA_SMEM, int MAXDC>
 __global__ void __launch_bounds__(max_threads_for(MAXDC)) decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_frame;
     __shared__ unsigned s_err;
+    const RunArgs& r = a.r;
     const int tid = threadIdx.x, nt = blockDim.x;
     float* P = reinterpret_cast<float*>(smem);
-    size_t off = (static_cast<size_t>(a.N) * 4 + 15) & ~static_cast<size_t>(15);
+    size_t off = (static_cast<size_t>(r.N) * 4 + 15) & ~static_cast<size_t>(15);
     MsgT* msg;
     if (MSG_SMEM) {
         msg = reinterpret_cast<MsgT*>(smem + off);
@@ -245,13 +113,11 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) decode_kernel(const De
                               : a.ws_delta + static_cast<size_t>(blockIdx.x) * a.max_gd;
     if (tid == 0) s_err = 0u;
     for (;;) {
-        if (tid == 0) s_frame = static_cast<long long>(atomicAdd(a.counter, 1ull));
-        __syncthreads();
-        const long long f = s_frame;
-        if (f >= a.n_frames) break;
-        if (a.start_ns && tid == 0) a.start_ns[f] = global_timer_ns();
+        const long long f = next_frame(r, &s_frame);
+        if (f >= r.n_frames) break;
+        if (r.start_ns && tid == 0) r.start_ns[f] = global_timer_ns();
         // initialisation: P_n = L_n, L_{m->n} = 0
-        for (int n = tid; n < a.N; n += nt) P[n] = load_llr(a.llr, a.llr_dtype, f * a.N + n);
+        for (int n = tid; n < r.N; n += nt) P[n] = load_llr(r.llr, r.llr_dtype, f * r.N + n);
         for (int e = tid; e < a.Epad; e += nt) msg[e] = from_f<MsgT>(0.f);
         __syncthreads();
         int it = 1, unsat = 1;
@@ -267,22 +133,22 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) decode_kernel(const De
                     __syncthreads();
                 }
             }
-            const bool last = it >= a.max_iter;
-            if (a.early_stop || last) {
+            const bool last = it >= r.max_iter;
+            if (r.early_stop || last) {
                 unsigned bad = 0u;
                 for (int s = tid; s < a.M && !bad; s += nt) bad |= slot_parity(a, P, s);
                 unsat = __syncthreads_or(bad);
-                if (!unsat && a.early_stop) break;
+                if (!unsat && r.early_stop) break;
             }
             if (last) break;
         }
-        if (a.msgs_out) {
+        if (r.msgs_out) {
             for (int e = tid; e < a.Epad; e += nt) {
                 const int csr = __ldg(a.edge_csr + e);
-                if (csr >= 0) a.msgs_out[f * a.E + csr] = to_f(msg[e]);
+                if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]);
             }
         }
-        write_frame_outputs(a, P, f, it, unsat, &s_err);
+        write_frame_outputs(r, P, f, it, unsat, &s_err);
         __syncthreads();
     }
 }
@@ -329,52 +195,71 @@ static constexpr size_t kHeaderBytes = 256;
     } while (0)
 
 // ---- device copies of layouts -------------------------------------------------------------
-template <typename T>
-static size_t push_array(std::vector<std::pair<const void*, size_t>>& parts, const std::vector<T>& v,
-                         size_t& off) {
-    const size_t at = off;
-    parts.push_back({v.data(), v.size() * sizeof(T)});
-    off = align256(off + v.size() * sizeof(T) + 1);
-    return at;
-}
+struct BlobBuilder {
+    std::vector<std::pair<const void*, size_t>> parts;
+    std::vector<size_t> at;
+    size_t off = 0;
+    template <typename T>
+    size_t add(const std::vector<T>& v) {
+        at.push_back(off);
+        parts.push_back({v.data(), v.size() * sizeof(T)});
+        off = align256(off + v.size() * sizeof(T) + 1);
+        return at.back();
+    }
+    ndgsbp_status upload(void** blob) {
+        std::vector<unsigned char> host(off, 0);
+        for (size_t i = 0; i < parts.size(); ++i)
+            if (parts[i].second) std::memcpy(host.data() + at[i], parts[i].first, parts[i].second);
+        CUDA_TRY(cudaMalloc(blob, off));
+        cudaError_t e = cudaMemcpy(*blob, host.data(), off, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(*blob);
+            *blob = nullptr;
+            return fail(NDGSBP_ERR_CUDA, "descriptor upload: %s", cudaGetErrorString(e));
+        }
+        return NDGSBP_OK;
+    }
+};
 
 static ndgsbp_status upload_layout(const Layout& L, DeviceLayout& D) {
-    std::vector<std::pair<const void*, size_t>> parts;
-    size_t off = 0;
-    const size_t o_deg = push_array(parts, L.slot_deg, off);
-    const size_t o_tb = push_array(parts, L.tile_base, off);
-    const size_t o_vn = push_array(parts, L.edge_vn, off);
-    const size_t o_csr = push_array(parts, L.edge_csr, off);
-    const size_t o_gp = push_array(parts, L.grp_ptr, off);
-    const size_t o_gs = push_array(parts, L.ge_slot, off);
-    const size_t o_gd = push_array(parts, L.ge_dpos, off);
-    const size_t o_cb = push_array(parts, L.grp_colbase, off);
-    const size_t o_nc = push_array(parts, L.grp_ncol, off);
-    const size_t o_col = push_array(parts, L.gcol, off);
-    std::vector<unsigned char> host(off, 0);
-    size_t at[] = {o_deg, o_tb, o_vn, o_csr, o_gp, o_gs, o_gd, o_cb, o_nc, o_col};
-    for (size_t i = 0; i < parts.size(); ++i)
-        if (parts[i].second) std::memcpy(host.data() + at[i], parts[i].first, parts[i].second);
+    BlobBuilder b;
+    const size_t o_deg = b.add(L.slot_deg), o_tb = b.add(L.tile_base), o_vn = b.add(L.edge_vn);
+    const size_t o_csr = b.add(L.edge_csr), o_gp = b.add(L.grp_ptr), o_gs = b.add(L.ge_slot);
+    const size_t o_gd = b.add(L.ge_dpos), o_cb = b.add(L.grp_colbase), o_nc = b.add(L.grp_ncol);
+    const size_t o_col = b.add(L.gcol);
     void* blob = nullptr;
-    CUDA_TRY(cudaMalloc(&blob, off));
-    cudaError_t e = cudaMemcpy(blob, host.data(), off, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        cudaFree(blob);
-        return fail(NDGSBP_ERR_CUDA, "descriptor upload: %s", cudaGetErrorString(e));
-    }
-    auto* b = static_cast<unsigned char*>(blob);
+    ndgsbp_status st = b.upload(&blob);
+    if (st) return st;
+    auto* p = static_cast<unsigned char*>(blob);
     D.blob = blob;
-    D.bytes = off;
-    D.slot_deg = reinterpret_cast<const int32_t*>(b + o_deg);
-    D.tile_base = reinterpret_cast<const int32_t*>(b + o_tb);
-    D.edge_vn = reinterpret_cast<const int32_t*>(b + o_vn);
-    D.edge_csr = reinterpret_cast<const int32_t*>(b + o_csr);
-    D.grp_ptr = reinterpret_cast<const int32_t*>(b + o_gp);
-    D.ge_slot = reinterpret_cast<const int32_t*>(b + o_gs);
-    D.ge_dpos = reinterpret_cast<const int32_t*>(b + o_gd);
-    D.grp_colbase = reinterpret_cast<const int32_t*>(b + o_cb);
-    D.grp_ncol = reinterpret_cast<const int32_t*>(b + o_nc);
-    D.gcol = reinterpret_cast<const uint8_t*>(b + o_col);
+    D.bytes = b.off;
+    D.slot_deg = reinterpret_cast<const int32_t*>(p + o_deg);
+    D.tile_base = reinterpret_cast<const int32_t*>(p + o_tb);
+    D.edge_vn = reinterpret_cast<const int32_t*>(p + o_vn);
+    D.edge_csr = reinterpret_cast<const int32_t*>(p + o_csr);
+    D.grp_ptr = reinterpret_cast<const int32_t*>(p + o_gp);
+    D.ge_slot = reinterpret_cast<const int32_t*>(p + o_gs);
+    D.ge_dpos = reinterpret_cast<const int32_t*>(p + o_gd);
+    D.grp_colbase = reinterpret_cast<const int32_t*>(p + o_cb);
+    D.grp_ncol = reinterpret_cast<const int32_t*>(p + o_nc);
+    D.gcol = reinterpret_cast<const uint8_t*>(p + o_col);
+    return NDGSBP_OK;
+}
+
+static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
+    BlobBuilder b;
+    const size_t o_tab = b.add(Q.edge_tab), o_deg = b.add(Q.layer_deg), o_off = b.add(Q.layer_off);
+    const size_t o_gl = b.add(Q.group_layers), o_csr = b.add(Q.csr_of);
+    void* blob = nullptr;
+    ndgsbp_status st = b.upload(&blob);
+    if (st) return st;
+    auto* p = static_cast<unsigned char*>(blob);
+    D.blob = blob;
+    D.edge_tab = reinterpret_cast<const int32_t*>(p + o_tab);
+    D.layer_deg = reinterpret_cast<const int32_t*>(p + o_deg);
+    D.layer_off = reinterpret_cast<const int32_t*>(p + o_off);
+    D.group_layers = reinterpret_cast<const int32_t*>(p + o_gl);
+    D.csr_of = reinterpret_cast<const int32_t*>(p + o_csr);
     return NDGSBP_OK;
 }
 
@@ -395,19 +280,34 @@ static ndgsbp_status device_layout(const Groups& g, bool flood, const Layout*& L
     return NDGSBP_OK;
 }
 
+static ndgsbp_status device_qc(const Groups& g, bool flood, const QcLayout*& Q, const DeviceQc*& D) {
+    Q = flood ? &flood_qc_layout(g) : &g.qc;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g.mu);
+    auto& cache = flood ? g.dev_flood_qc : g.dev_qc;
+    auto it = cache.find(dev);
+    if (it == cache.end()) {
+        DeviceQc dq;
+        ndgsbp_status st = upload_qc(*Q, dq);
+        if (st) return st;
+        it = cache.emplace(dev, dq).first;
+    }
+    D = &it->second;
+    return NDGSBP_OK;
+}
+
 void release_device_layouts(Groups& g) {
     int cur = 0;
     if (cudaGetDevice(&cur) != cudaSuccess) return;
     for (auto* cache : {&g.dev_grouped, &g.dev_flood}) {
-        for (auto& kv : *cache) {
+        for (auto& kv : *cache)
             if (cudaSetDevice(kv.first) == cudaSuccess) cudaFree(kv.second.blob);
-        }
         cache->clear();
     }
     for (auto* cache : {&g.dev_qc, &g.dev_flood_qc}) {
-        for (auto& kv : *cache) {
-            if (cudaSetDevice(kv.first) == cudaSuccess) cudaFree(kv.second);
-        }
+        for (auto& kv : *cache)
+            if (cudaSetDevice(kv.first) == cudaSuccess) cudaFree(kv.second.blob);
         cache->clear();
     }
     cudaSetDevice(cur);
@@ -419,10 +319,14 @@ Groups::~Groups() { release_device_layouts(*this); }
 // ---- planning -----------------------------------------------------------------------------
 struct Plan {
     ndgsbp_plan pub;
+    bool qc = false;
     KernelFn fn = nullptr;
+    QcKernelFn qfn = nullptr;
     bool msg_smem = false, delta_smem = false;
     const Layout* L = nullptr;
     const DeviceLayout* D = nullptr;
+    const QcLayout* Q = nullptr;
+    const DeviceQc* DQ = nullptr;
 };
 
 static ndgsbp_status validate_params(const ndgsbp_params* p) {
@@ -436,8 +340,77 @@ static ndgsbp_status validate_params(const ndgsbp_params* p) {
     if (p->block_threads < 0 || p->block_threads > 1024 || p->block_threads % 32)
         return fail(NDGSBP_ERR_INVALID, "block_threads must be 0 or a multiple of 32 up to 1024");
     if (p->ctas_per_sm < 0) return fail(NDGSBP_ERR_INVALID, "ctas_per_sm must be >= 0");
-    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC)
+    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_GLOBAL)
         return fail(NDGSBP_ERR_INVALID, "unknown variant %d", p->variant);
+    return NDGSBP_OK;
+}
+
+struct DeviceInfo {
+    int dev = 0, sms = 0, smem_optin = 0;
+};
+
+static ndgsbp_status device_info(DeviceInfo& di) {
+    CUDA_TRY(cudaGetDevice(&di.dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, di.dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&di.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, di.dev));
+    return NDGSBP_OK;
+}
+
+static ndgsbp_status finish_grid(const void* fn, int threads, size_t smem, const ndgsbp_params* p,
+                                 int64_t n_frames, const DeviceInfo& di, int& per_sm, int64_t& grid) {
+    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+    if (per_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "kernel does not fit on an SM with %d threads", threads);
+    if (p->ctas_per_sm > 0) per_sm = std::min(per_sm, p->ctas_per_sm);
+    grid = static_cast<int64_t>(per_sm) * di.sms;
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::max<int64_t>(n_frames, 1)));
+    return NDGSBP_OK;
+}
+
+// Layered QC kernel plan, when the grouping is made of whole layers and a window fits a CTA.
+static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
+                                  const DeviceInfo& di, Plan& plan, bool* ok) {
+    *ok = false;
+    const QcLayout& Q = flood ? flood_qc_layout(g) : g.qc;
+    if (!Q.ok) return NDGSBP_OK;
+    const int maxdc = degree_bound(Q.max_deg);
+    if (!maxdc) return NDGSBP_OK;
+    const int active = Q.window * Q.Z;
+    const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
+    if (threads < active || threads > max_threads_for(maxdc)) return NDGSBP_OK;
+    const size_t budget = static_cast<size_t>(di.smem_optin) - 64;
+    const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 4);
+    const size_t m_bytes = align16(static_cast<size_t>(g.code->E) * msg_size(p->msg_dtype));
+    const size_t t_bytes = qc_table_bytes(Q);
+    if (p_bytes + t_bytes > budget) return NDGSBP_OK;
+    bool msg_smem = p_bytes + m_bytes + t_bytes <= budget;
+    if (p->variant == NDGSBP_VARIANT_QC_GLOBAL) msg_smem = false;
+    const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
+    QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem);
+    if (!fn) return NDGSBP_OK;
+    int per_sm = 0;
+    int64_t grid = 0;
+    ndgsbp_status st = finish_grid(reinterpret_cast<const void*>(fn), threads, smem, p, n_frames, di, per_sm, grid);
+    if (st) return st;
+    st = device_qc(g, flood, plan.Q, plan.DQ);
+    if (st) return st;
+    plan.qc = true;
+    plan.qfn = fn;
+    plan.msg_smem = msg_smem;
+    ndgsbp_plan& o = plan.pub;
+    o.variant = msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL;
+    o.block_threads = threads;
+    o.grid = static_cast<int32_t>(grid);
+    o.ctas_per_sm = per_sm;
+    o.max_row_degree = maxdc;
+    o.delta_in_smem = 0;
+    o.smem_bytes = static_cast<int64_t>(smem);
+    o.workspace_bytes = static_cast<int64_t>(
+        kHeaderBytes + (msg_smem ? 0 : align256(static_cast<size_t>(grid) * g.code->E * msg_size(p->msg_dtype))));
+    o.stored_edges = g.code->E;
+    o.edge_updates_per_iter = flood ? g.code->E : g.edge_updates;
+    *ok = true;
     return NDGSBP_OK;
 }
 
@@ -445,50 +418,54 @@ static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t 
     ndgsbp_status st = validate_params(p);
     if (st) return st;
     const bool flood = p->schedule == NDGSBP_SCHEDULE_FLOOD;
+    DeviceInfo di;
+    st = device_info(di);
+    if (st) return st;
+    const bool want_qc = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL;
+    if (p->variant == NDGSBP_VARIANT_AUTO || want_qc) {
+        bool ok = false;
+        st = make_qc_plan(g, p, n_frames, flood, di, plan, &ok);
+        if (st) return st;
+        if (ok) return NDGSBP_OK;
+        if (want_qc)
+            return fail(NDGSBP_ERR_UNSUPPORTED, "QC variant needs a QC code grouped in whole layers with a window "
+                                                "that fits one CTA");
+    }
     st = device_layout(g, flood, plan.L, plan.D);
     if (st) return st;
     const Layout& L = *plan.L;
     const int maxdc = degree_bound(L.max_deg);
     if (!maxdc) return fail(NDGSBP_ERR_UNSUPPORTED, "CN degree %d above 32", L.max_deg);
-    int dev = 0, sms = 0, smem_optin = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t static_smem = 64;
-    const size_t budget = static_cast<size_t>(smem_optin) - static_smem;
+    const size_t budget = static_cast<size_t>(di.smem_optin) - 64;
     const size_t p_bytes = align16(static_cast<size_t>(L.N) * 4);
     const size_t m_bytes = align16(static_cast<size_t>(L.Epad) * msg_size(p->msg_dtype));
     const size_t d_bytes = align16(static_cast<size_t>(L.max_gd) * 4);
+    if (p_bytes > budget) return fail(NDGSBP_ERR_UNSUPPORTED, "posterior of %d VNs does not fit in shared memory", L.N);
     bool msg_smem, delta_smem;
-    int variant = p->variant == NDGSBP_VARIANT_QC ? NDGSBP_VARIANT_AUTO : p->variant;
-    if (variant == NDGSBP_VARIANT_SMEM) {
+    if (p->variant == NDGSBP_VARIANT_SMEM) {
         if (p_bytes + m_bytes + d_bytes > budget)
             return fail(NDGSBP_ERR_UNSUPPORTED, "SMEM variant needs %zu bytes of shared memory, device has %zu",
                         p_bytes + m_bytes + d_bytes, budget);
         msg_smem = delta_smem = true;
-    } else if (variant == NDGSBP_VARIANT_GLOBAL) {
+    } else if (p->variant == NDGSBP_VARIANT_GLOBAL) {
         msg_smem = false;
         delta_smem = p_bytes + d_bytes <= budget;
     } else {
         msg_smem = p_bytes + m_bytes + d_bytes <= budget;
         delta_smem = msg_smem || p_bytes + d_bytes <= budget;
     }
-    if (p_bytes > budget) return fail(NDGSBP_ERR_UNSUPPORTED, "posterior of %d VNs does not fit in shared memory", L.N);
     const size_t smem = p_bytes + (msg_smem ? m_bytes : 0) + (delta_smem ? d_bytes : 0);
     const int tmax = max_threads_for(maxdc);
     int threads = p->block_threads;
     if (!threads) threads = std::min(tmax, std::max(64, (L.max_group_entries + 31) / 32 * 32));
-    if (threads > tmax) return fail(NDGSBP_ERR_UNSUPPORTED, "block_threads %d above %d for CN degree %d", threads, tmax, L.max_deg);
+    if (threads > tmax)
+        return fail(NDGSBP_ERR_UNSUPPORTED, "block_threads %d above %d for CN degree %d", threads, tmax, L.max_deg);
     KernelFn fn = pick_kernel(p->msg_dtype, maxdc, msg_smem, delta_smem);
     if (!fn) return fail(NDGSBP_ERR_UNSUPPORTED, "no kernel instance for this configuration");
-    CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem)));
     int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), threads, smem));
-    if (per_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "kernel does not fit on an SM with %d threads", threads);
-    if (p->ctas_per_sm > 0) per_sm = std::min(per_sm, p->ctas_per_sm);
-    int64_t grid = static_cast<int64_t>(per_sm) * sms;
-    grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::max<int64_t>(n_frames, 1)));
+    int64_t grid = 0;
+    st = finish_grid(reinterpret_cast<const void*>(fn), threads, smem, p, n_frames, di, per_sm, grid);
+    if (st) return st;
     size_t ws = kHeaderBytes;
     if (!msg_smem) ws += align256(static_cast<size_t>(grid) * L.Epad * msg_size(p->msg_dtype));
     if (!delta_smem) ws += align256(static_cast<size_t>(grid) * L.max_gd * 4);
@@ -507,6 +484,35 @@ static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t 
     o.stored_edges = L.Epad;
     o.edge_updates_per_iter = L.edge_updates;
     return NDGSBP_OK;
+}
+
+static void fill_run(RunArgs& r, const Groups& g, const ndgsbp_params* params, const void* d_llr, int32_t llr_dtype,
+                     int64_t n_frames, void* ws, uint32_t* d_hard_bits, int32_t* d_iters, uint8_t* d_syndrome_ok,
+                     float* d_posterior, const ndgsbp_extras* extras) {
+    std::memset(&r, 0, sizeof(r));
+    r.N = g.code->N;
+    r.E = static_cast<int>(g.code->E);
+    r.W = (r.N + 31) / 32;
+    r.llr = d_llr;
+    r.llr_dtype = llr_dtype;
+    r.n_frames = n_frames;
+    r.max_iter = params->max_iter;
+    r.llr_max = params->llr_max;
+    r.early_stop = params->early_stop ? 1 : 0;
+    r.counter = static_cast<unsigned long long*>(ws);
+    r.hard_bits = d_hard_bits;
+    r.iters = d_iters;
+    r.synd_ok = d_syndrome_ok;
+    r.posterior = d_posterior;
+    if (extras) {
+        r.ref_bits = extras->d_ref_bits;
+        r.ref_per_frame = extras->ref_per_frame;
+        r.stats = reinterpret_cast<unsigned long long*>(extras->d_stats);
+        r.iter_hist = reinterpret_cast<unsigned long long*>(extras->d_iter_hist);
+        r.start_ns = reinterpret_cast<unsigned long long*>(extras->d_start_ns);
+        r.retire_ns = reinterpret_cast<unsigned long long*>(extras->d_retire_ns);
+        r.msgs_out = extras->d_messages;
+    }
 }
 
 }  // namespace ndgsbp
@@ -548,8 +554,9 @@ ndgsbp_status ndgsbp_decode_ex(const ndgsbp_groups* groups, const ndgsbp_params*
     if (llr_dtype != NDGSBP_F32 && llr_dtype != NDGSBP_F64 && llr_dtype != NDGSBP_F16 && llr_dtype != NDGSBP_BF16)
         return fail(NDGSBP_ERR_INVALID, "decode: unknown llr_dtype %d", llr_dtype);
     if (n_frames > 0 && (!d_llr || !d_hard_bits)) return fail(NDGSBP_ERR_INVALID, "decode: d_llr and d_hard_bits are required");
+    const Groups& g = groups->g;
     Plan plan;
-    ndgsbp_status st = make_plan(groups->g, params, n_frames, plan);
+    ndgsbp_status st = make_plan(g, params, n_frames, plan);
     if (st) return st;
     if (n_frames == 0) return NDGSBP_OK;
     if (!d_workspace || workspace_bytes < static_cast<size_t>(plan.pub.workspace_bytes))
@@ -557,57 +564,43 @@ ndgsbp_status ndgsbp_decode_ex(const ndgsbp_groups* groups, const ndgsbp_params*
                     static_cast<long long>(plan.pub.workspace_bytes));
     if (reinterpret_cast<uintptr_t>(d_workspace) % 256)
         return fail(NDGSBP_ERR_WORKSPACE, "decode: workspace must be 256-byte aligned");
-    const Layout& L = *plan.L;
-    const DeviceLayout& D = *plan.D;
-    DecodeArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.M = L.M;
-    a.N = L.N;
-    a.E = static_cast<int>(groups->g.code->E);
-    a.Epad = L.Epad;
-    a.G = L.G;
-    a.max_gd = L.max_gd;
-    a.W = (L.N + 31) / 32;
-    a.slot_deg = D.slot_deg;
-    a.tile_base = D.tile_base;
-    a.edge_vn = D.edge_vn;
-    a.edge_csr = D.edge_csr;
-    a.grp_ptr = D.grp_ptr;
-    a.ge_slot = D.ge_slot;
-    a.ge_dpos = D.ge_dpos;
-    a.grp_colbase = D.grp_colbase;
-    a.grp_ncol = D.grp_ncol;
-    a.gcol = D.gcol;
-    a.llr = d_llr;
-    a.llr_dtype = llr_dtype;
-    a.n_frames = n_frames;
-    a.max_iter = params->max_iter;
-    a.llr_max = params->llr_max;
-    a.early_stop = params->early_stop ? 1 : 0;
     auto* ws = static_cast<unsigned char*>(d_workspace);
-    a.counter = reinterpret_cast<unsigned long long*>(ws);
-    size_t off = kHeaderBytes;
-    if (!plan.msg_smem) {
-        a.ws_msgs = ws + off;
-        off += align256(static_cast<size_t>(plan.pub.grid) * L.Epad * msg_size(params->msg_dtype));
-    }
-    if (!plan.delta_smem) a.ws_delta = reinterpret_cast<float*>(ws + off);
-    a.hard_bits = d_hard_bits;
-    a.iters = d_iters;
-    a.synd_ok = d_syndrome_ok;
-    a.posterior = d_posterior;
-    if (extras) {
-        a.ref_bits = extras->d_ref_bits;
-        a.ref_per_frame = extras->ref_per_frame;
-        a.stats = reinterpret_cast<unsigned long long*>(extras->d_stats);
-        a.iter_hist = reinterpret_cast<unsigned long long*>(extras->d_iter_hist);
-        a.start_ns = reinterpret_cast<unsigned long long*>(extras->d_start_ns);
-        a.retire_ns = reinterpret_cast<unsigned long long*>(extras->d_retire_ns);
-        a.msgs_out = extras->d_messages;
-    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s));
-    plan.fn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
+    CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), s));
+    if (plan.qc) {
+        QcArgs a;
+        std::memset(&a, 0, sizeof(a));
+        fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior, extras);
+        fill_qc_args(a, *plan.Q, *plan.DQ, plan.msg_smem ? nullptr : ws + kHeaderBytes);
+        plan.qfn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
+    } else {
+        const Layout& L = *plan.L;
+        const DeviceLayout& D = *plan.D;
+        DecodeArgs a;
+        std::memset(&a, 0, sizeof(a));
+        fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior, extras);
+        a.M = L.M;
+        a.Epad = L.Epad;
+        a.G = L.G;
+        a.max_gd = L.max_gd;
+        a.slot_deg = D.slot_deg;
+        a.tile_base = D.tile_base;
+        a.edge_vn = D.edge_vn;
+        a.edge_csr = D.edge_csr;
+        a.grp_ptr = D.grp_ptr;
+        a.ge_slot = D.ge_slot;
+        a.ge_dpos = D.ge_dpos;
+        a.grp_colbase = D.grp_colbase;
+        a.grp_ncol = D.grp_ncol;
+        a.gcol = D.gcol;
+        size_t off = kHeaderBytes;
+        if (!plan.msg_smem) {
+            a.ws_msgs = ws + off;
+            off += align256(static_cast<size_t>(plan.pub.grid) * L.Epad * msg_size(params->msg_dtype));
+        }
+        if (!plan.delta_smem) a.ws_delta = reinterpret_cast<float*>(ws + off);
+        plan.fn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
+    }
     CUDA_TRY(cudaGetLastError());
     return NDGSBP_OK;
 }

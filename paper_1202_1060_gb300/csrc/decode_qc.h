@@ -1,0 +1,26 @@
+// Layered QC decode kernel interface (decode_qc.cu), used by the planner in decode.cu.
+#pragma once
+
+#include "device_common.cuh"
+#include "ndgsbp_internal.h"
+
+namespace ndgsbp {
+
+struct QcArgs {
+    RunArgs r;
+    int Z, nl, G, window, maxdeg;
+    const int2* edge_tab;         // [nl][maxdeg]: (b Z + s, Z - s) of edge k of the layer
+    const int32_t* layer_deg;     // [nl]
+    const int32_t* layer_off;     // [nl] first message of the layer
+    const int32_t* group_layers;  // [G][window]
+    const int32_t* csr_of;        // [E] CSR position of each stored message
+    void* ws_msgs;                // per-CTA message slots when messages are not in shared memory
+};
+
+typedef void (*QcKernelFn)(const QcArgs);
+
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem);
+size_t qc_table_bytes(const QcLayout& Q);
+void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs);
+
+}  // namespace ndgsbp

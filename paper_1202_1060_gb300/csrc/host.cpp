@@ -229,7 +229,10 @@ void compile_qc_layout(const Code& c, const std::vector<int32_t>& gp, const std:
         Q.layer_deg[l] = d;
         Q.max_deg = std::max(Q.max_deg, d);
     }
-    Q.layer_edges.assign(static_cast<size_t>(nl) * Q.max_deg, 0);
+    Q.edge_tab.assign(static_cast<size_t>(nl) * Q.max_deg * 2, 0);
+    Q.layer_off.assign(nl, 0);
+    Q.csr_of.assign(c.E, 0);
+    int off = 0;
     for (int l = 0; l < nl; ++l) {
         const int r0 = l * Z, d = Q.layer_deg[l];
         std::vector<std::pair<int, int>> bs;
@@ -249,7 +252,14 @@ void compile_qc_layout(const Code& c, const std::vector<int32_t>& gp, const std:
             for (int k = 0; k < d; ++k)
                 if (c.col_idx[c.row_ptr[row] + k] != want[k]) return;
         }
-        for (int k = 0; k < d; ++k) Q.layer_edges[static_cast<size_t>(l) * Q.max_deg + k] = (bs[k].first << 16) | bs[k].second;
+        // edges ordered by block column = by VN index within every row, i.e. CSR order
+        Q.layer_off[l] = off;
+        for (int k = 0; k < d; ++k) {
+            Q.edge_tab[(static_cast<size_t>(l) * Q.max_deg + k) * 2] = bs[k].first * Z + bs[k].second;
+            Q.edge_tab[(static_cast<size_t>(l) * Q.max_deg + k) * 2 + 1] = Z - bs[k].second;
+            for (int cc = 0; cc < Z; ++cc) Q.csr_of[off + k * Z + cc] = c.row_ptr[r0 + cc] + k;
+        }
+        off += d * Z;
     }
     // groups as lists of whole layers
     int window = -1;

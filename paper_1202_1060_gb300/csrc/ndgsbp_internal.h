@@ -73,8 +73,20 @@ struct QcLayout {
     int window = 0;           // layers per group (all groups the same size)
     int max_deg = 0;
     std::vector<int32_t> layer_deg;     // [n_layers]
-    std::vector<int32_t> layer_edges;   // [n_layers][max_deg] packed (block column << 16 | shift)
+    std::vector<int32_t> layer_off;     // [n_layers] first stored message of the layer
+    std::vector<int32_t> edge_tab;      // [n_layers][max_deg][2]: (b Z + s, Z - s), edges by block column
     std::vector<int32_t> group_layers;  // [G][window] layer ids in group order
+    std::vector<int32_t> csr_of;        // [E] CSR position of message layer_off[l] + k Z + c
+};
+
+// Device copy of a QcLayout.
+struct DeviceQc {
+    void* blob = nullptr;
+    const int32_t* edge_tab = nullptr;
+    const int32_t* layer_deg = nullptr;
+    const int32_t* layer_off = nullptr;
+    const int32_t* group_layers = nullptr;
+    const int32_t* csr_of = nullptr;
 };
 
 struct Groups {
@@ -89,7 +101,7 @@ struct Groups {
     mutable std::unique_ptr<Layout> flood;        // built on first FLOOD use
     mutable QcLayout flood_qc;
     mutable std::map<int, DeviceLayout> dev_grouped, dev_flood;   // per CUDA device
-    mutable std::map<int, void*> dev_qc, dev_flood_qc;
+    mutable std::map<int, DeviceQc> dev_qc, dev_flood_qc;
     ~Groups();
 };
 

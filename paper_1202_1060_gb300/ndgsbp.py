@@ -25,7 +25,7 @@ F32, F16, BF16, F64 = 0, 1, 2, 3
 UNIT_CN, UNIT_LAYER = 0, 1
 GROUPS_CYCLIC, GROUPS_NATURAL = 1, 2
 SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
-VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC = 0, 1, 2, 3
+VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1, 2, 3, 4
 STAT_FRAMES, STAT_FRAME_ERRORS, STAT_BIT_ERRORS, STAT_UNDETECTED = 0, 1, 2, 3
 STAT_ITERATIONS, STAT_UNSATISFIED, STATS_LEN = 4, 5, 8
 

@@ -214,20 +214,51 @@ def test_frame_alone_equals_frame_in_batch(env):
     assert (sub["post"][::-1] == full["post"]).all()
 
 
-@pytest.mark.parametrize("name,kind", [("gallager36_n1008", "ndgsbp"), ("qc_n2304_r12", "layers_cyclic"),
-                                       ("qc_n2304_r12", "flood")])
-def test_variants_and_block_sizes_agree_bitwise(env, name, kind):
+VARIANT_CASES = [("gallager36_n1008", "ndgsbp", False), ("qc_n2304_r12", "layers_cyclic", True),
+                 ("qc_n2304_r12", "layers_linear", True), ("qc_n2304_r12", "flood", False),
+                 ("qc_n576_r12", "flood", True), ("qc_n2304_r34", "layers_cyclic", True),
+                 ("qc_n1152_r23", "layers_cyclic", True)]
+
+
+@pytest.mark.parametrize("name,kind,qc", VARIANT_CASES)
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_variants_and_block_sizes_agree_bitwise(env, name, kind, qc, msg):
+    """Every kernel variant and launch shape computes the same arithmetic in the same order:
+    the table-driven kernel with messages in shared or global memory, any block size, and the
+    layered QC kernel give bit-identical posteriors."""
     nd, torch = env
     c = I.code_by_name(name)
-    llr = I.channel_llr(c.N, 64, 1.25, I.design_rate(c), seed=77)
-    code, g = _groups(nd, c, kind)
-    base = _run(nd, torch, g, c, llr, max_iter=20, variant=nd.VARIANT_SMEM)
+    mdt = nd.F32 if msg == "f32" else nd.F16
+    sched = nd.SCHEDULE_FLOOD if kind == "flood" else nd.SCHEDULE_GROUPS
+    llr = I.channel_llr(c.N, 64, 1.25 if c.M * 2 == c.N else 3.0, I.design_rate(c), seed=77)
+    code, g = _groups(nd, c, "layers_cyclic" if (kind == "flood" and c.Z) else kind)
+    kw0 = dict(max_iter=20, msg_dtype=mdt, schedule=sched)
+    base = _run(nd, torch, g, c, llr, variant=nd.VARIANT_SMEM, **kw0)
     assert base["plan"]["variant"] == nd.VARIANT_SMEM
-    for kw in (dict(variant=nd.VARIANT_GLOBAL), dict(variant=nd.VARIANT_SMEM, block_threads=64),
-               dict(variant=nd.VARIANT_GLOBAL, block_threads=128, ctas_per_sm=1)):
-        other = _run(nd, torch, g, c, llr, max_iter=20, **kw)
+    others = [dict(variant=nd.VARIANT_GLOBAL), dict(variant=nd.VARIANT_SMEM, block_threads=64),
+              dict(variant=nd.VARIANT_GLOBAL, block_threads=128, ctas_per_sm=1)]
+    if qc:
+        others += [dict(variant=nd.VARIANT_QC), dict(variant=nd.VARIANT_QC_GLOBAL)]
+    for kw in others:
+        other = _run(nd, torch, g, c, llr, **kw0, **kw)
+        if kw["variant"] in (nd.VARIANT_QC, nd.VARIANT_QC_GLOBAL):
+            assert other["plan"]["variant"] == kw["variant"]
         assert (other["post"] == base["post"]).all(), kw
         assert (other["iters"] == base["iters"]).all()
+        assert (other["bits"] == base["bits"]).all()
+    auto = _run(nd, torch, g, c, llr, **kw0)
+    assert (auto["post"] == base["post"]).all()
+    if qc:
+        assert auto["plan"]["variant"] == nd.VARIANT_QC
+
+
+def test_qc_variant_rejected_when_not_layered(env):
+    nd, torch = env
+    c = I.code_by_name("gallager36_n1008")
+    code, g = _groups(nd, c, "ndgsbp")
+    with pytest.raises(nd.NdgsbpError) as e:
+        g.plan(nd.params_default(variant=nd.VARIANT_QC), 10)
+    assert e.value.status == nd.ERR_UNSUPPORTED
 
 
 def test_llr_dtypes(env, oracle_mod):
