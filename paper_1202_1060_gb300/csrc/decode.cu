@@ -387,7 +387,7 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     bool msg_smem = p_bytes + m_bytes + t_bytes <= budget;
     if (p->variant == NDGSBP_VARIANT_QC_GLOBAL) msg_smem = false;
     const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
-    QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem);
+    QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, qc_degrees_specialised(Q, maxdc));
     if (!fn) return NDGSBP_OK;
     int per_sm = 0;
     int64_t grid = 0;

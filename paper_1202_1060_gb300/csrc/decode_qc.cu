@@ -21,7 +21,71 @@ namespace ndgsbp {
 
 __device__ __forceinline__ int qc_vn(int2 e, int c, int Z) { return e.x + c - (c >= e.y ? Z : 0); }
 
-template <typename MsgT, bool MSG_SMEM, int MAXDC>
+// Phase A for the CN of this thread in a layer of exactly D edges: VN->CN messages from the
+// posterior, Eq. (1), new messages stored; the VN indices and message changes stay in registers
+// for phase B.
+template <int D, int MAXDC, typename MsgT>
+__device__ __forceinline__ void qc_phase_a(const int2* __restrict__ et, int c, int Z, const float* __restrict__ P,
+                                           MsgT* __restrict__ m, float lim, int (&vv)[MAXDC], float (&dl)[MAXDC]) {
+    static_assert(D <= MAXDC, "degree above the bound");
+    float t[D], old[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        vv[k] = qc_vn(et[k], c, Z);
+        old[k] = to_f(m[k * Z]);
+        t[k] = P[vv[k]] - old[k];
+    }
+    check_node_update<D>(t, D, lim, [&](int k, float val) {
+        const MsgT q = from_f<MsgT>(val);
+        m[k * Z] = q;
+        dl[k] = to_f(q) - old[k];
+    });
+}
+
+template <int D, int MAXDC>
+__device__ __forceinline__ void qc_phase_b(float* __restrict__ P, const int (&vv)[MAXDC], const float (&dl)[MAXDC]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) P[vv[k]] += dl[k];
+}
+
+template <int D>
+__device__ __forceinline__ unsigned qc_parity(const int2* __restrict__ et, int c, int Z, const float* __restrict__ P) {
+    unsigned p = 0u;
+#pragma unroll
+    for (int k = 0; k < D; ++k) p ^= (P[qc_vn(et[k], c, Z)] < 0.f) ? 1u : 0u;
+    return p;
+}
+
+// Degree-generic versions (any d <= MAXDC), used for degrees outside the specialised set.
+template <int MAXDC, typename MsgT>
+__device__ __forceinline__ void qc_phase_a_any(const int2* __restrict__ et, int c, int Z, int d, const float* __restrict__ P,
+                                               MsgT* __restrict__ m, float lim, int (&vv)[MAXDC], float (&dl)[MAXDC]) {
+    float t[MAXDC], old[MAXDC];
+#pragma unroll
+    for (int k = 0; k < MAXDC; ++k) {
+        if (k < d) {
+            vv[k] = qc_vn(et[k], c, Z);
+            old[k] = to_f(m[k * Z]);
+            t[k] = P[vv[k]] - old[k];
+        }
+    }
+    check_node_update<MAXDC>(t, d, lim, [&](int k, float val) {
+        const MsgT q = from_f<MsgT>(val);
+        m[k * Z] = q;
+        dl[k] = to_f(q) - old[k];
+    });
+}
+
+// Warp-uniform dispatch on the layer degree (a warp covers one layer when 32 divides Z).
+#define NDGSBP_DEGREE_CASES(MAXDC, X) \
+    if (MAXDC == 8) { X(5) X(6) X(7) X(8) } else if (MAXDC == 16) { X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) }
+
+// SPEC instances run fully unrolled code for the layer's exact degree, chosen per layer by a
+// warp-uniform dispatch; they serve codes whose layer degrees all lie in (MAXDC/2, MAXDC] (one
+// or two row degrees just below the bound, the usual QC case).  Other instances run the
+// degree-generic predicated code.  Keeping the two apart keeps the register footprint of the
+// specialised code small (a shared fallback path raises it for every case).
+template <typename MsgT, bool MSG_SMEM, int MAXDC, bool SPEC>
 __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const QcArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_frame;
@@ -54,6 +118,7 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const
     const int j = tid / Z;
     const int c = tid - j * Z;
     const bool active = j < W;
+    const float lim = r.llr_max;
     if (tid == 0) s_err = 0u;
     for (;;) {
         const long long f = next_frame(r, &s_frame);   // barrier: also orders the table loads
@@ -66,34 +131,35 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const
         for (;; ++it) {
             for (int g = 0; g < a.G; ++g) {
                 float dl[MAXDC];
+                int vv[MAXDC];
                 int d = 0;
-                const int2* et = tab;
                 if (active) {
                     const int l = glay[g * W + j];
                     d = ldeg[l];
-                    et = tab + l * md;
+                    const int2* et = tab + l * md;
                     MsgT* m = msg + loff[l] + c;
-                    float t[MAXDC], old[MAXDC];
-#pragma unroll
-                    for (int k = 0; k < MAXDC; ++k) {
-                        if (k < d) {
-                            const int v = qc_vn(et[k], c, Z);
-                            old[k] = to_f(m[k * Z]);
-                            t[k] = P[v] - old[k];
-                        }
+                    if constexpr (SPEC) {
+#define NDGSBP_CASE_A(D) \
+    if (d == D) qc_phase_a<(D <= MAXDC ? D : MAXDC), MAXDC, MsgT>(et, c, Z, P, m, lim, vv, dl);
+                        NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_A)
+#undef NDGSBP_CASE_A
+                    } else {
+                        qc_phase_a_any<MAXDC, MsgT>(et, c, Z, d, P, m, lim, vv, dl);
                     }
-                    check_node_update<MAXDC>(t, d, r.llr_max, [&](int k, float val) {
-                        const MsgT q = from_f<MsgT>(val);
-                        m[k * Z] = q;
-                        dl[k] = to_f(q) - old[k];
-                    });
                 }
                 __syncthreads();
                 for (int jj = 0; jj < W; ++jj) {
                     if (active && j == jj) {
+                        if constexpr (SPEC) {
+#define NDGSBP_CASE_B(D) \
+    if (d == D) qc_phase_b<(D <= MAXDC ? D : MAXDC), MAXDC>(P, vv, dl);
+                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_B)
+#undef NDGSBP_CASE_B
+                        } else {
 #pragma unroll
-                        for (int k = 0; k < MAXDC; ++k)
-                            if (k < d) P[qc_vn(et[k], c, Z)] += dl[k];
+                            for (int k = 0; k < MAXDC; ++k)
+                                if (k < d) P[vv[k]] += dl[k];
+                        }
                     }
                     __syncthreads();
                 }
@@ -102,13 +168,20 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const
             if (r.early_stop || last) {
                 unsigned bad = 0u;
                 if (active) {
-                    for (int l = j; l < nl && !bad; l += W) {
+                    for (int l = j; l < nl; l += W) {
                         const int d = ldeg[l];
                         const int2* et = tab + l * md;
                         unsigned p = 0u;
+                        if constexpr (SPEC) {
+#define NDGSBP_CASE_S(D) \
+    if (d == D) p = qc_parity<(D <= MAXDC ? D : MAXDC)>(et, c, Z, P);
+                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_S)
+#undef NDGSBP_CASE_S
+                        } else {
 #pragma unroll
-                        for (int k = 0; k < MAXDC; ++k)
-                            if (k < d) p ^= (P[qc_vn(et[k], c, Z)] < 0.f) ? 1u : 0u;
+                            for (int k = 0; k < MAXDC; ++k)
+                                if (k < d) p ^= (P[qc_vn(et[k], c, Z)] < 0.f) ? 1u : 0u;
+                        }
                         bad |= p;
                     }
                 }
@@ -124,21 +197,34 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const
     }
 }
 
+template <typename MsgT, int MAXDC>
+static QcKernelFn pick_qc_storage(bool msg_smem, bool spec) {
+    if (spec) return msg_smem ? qc_decode_kernel<MsgT, true, MAXDC, true> : qc_decode_kernel<MsgT, false, MAXDC, true>;
+    return msg_smem ? qc_decode_kernel<MsgT, true, MAXDC, false> : qc_decode_kernel<MsgT, false, MAXDC, false>;
+}
+
 template <typename MsgT>
-static QcKernelFn pick_qc_degree(int maxdc, bool msg_smem) {
+static QcKernelFn pick_qc_degree(int maxdc, bool msg_smem, bool spec) {
     switch (maxdc) {
-        case 8: return msg_smem ? qc_decode_kernel<MsgT, true, 8> : qc_decode_kernel<MsgT, false, 8>;
-        case 16: return msg_smem ? qc_decode_kernel<MsgT, true, 16> : qc_decode_kernel<MsgT, false, 16>;
-        case 32: return msg_smem ? qc_decode_kernel<MsgT, true, 32> : qc_decode_kernel<MsgT, false, 32>;
+        case 8: return pick_qc_storage<MsgT, 8>(msg_smem, spec);
+        case 16: return pick_qc_storage<MsgT, 16>(msg_smem, spec);
+        case 32: return msg_smem ? qc_decode_kernel<MsgT, true, 32, false> : qc_decode_kernel<MsgT, false, 32, false>;
         default: return nullptr;
     }
 }
 
-QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem) {
+bool qc_degrees_specialised(const QcLayout& Q, int maxdc) {
+    if (maxdc > 16) return false;
+    for (int d : Q.layer_deg)
+        if (d <= maxdc / 2 || d > maxdc) return false;
+    return true;
+}
+
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec) {
     switch (msg_dtype) {
-        case NDGSBP_F32: return pick_qc_degree<float>(maxdc, msg_smem);
-        case NDGSBP_F16: return pick_qc_degree<__half>(maxdc, msg_smem);
-        case NDGSBP_BF16: return pick_qc_degree<__nv_bfloat16>(maxdc, msg_smem);
+        case NDGSBP_F32: return pick_qc_degree<float>(maxdc, msg_smem, spec);
+        case NDGSBP_F16: return pick_qc_degree<__half>(maxdc, msg_smem, spec);
+        case NDGSBP_BF16: return pick_qc_degree<__nv_bfloat16>(maxdc, msg_smem, spec);
         default: return nullptr;
     }
 }

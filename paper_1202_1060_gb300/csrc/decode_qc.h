@@ -19,7 +19,8 @@ struct QcArgs {
 
 typedef void (*QcKernelFn)(const QcArgs);
 
-QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem);
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec);
+bool qc_degrees_specialised(const QcLayout& Q, int maxdc);
 size_t qc_table_bytes(const QcLayout& Q);
 void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs);
 
