@@ -231,6 +231,31 @@ ndgsbp_status ndgsbp_decode_ex(const ndgsbp_groups* groups, const ndgsbp_params*
                                int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
                                const ndgsbp_extras* extras, void* stream);
 
+/* ---- Decoding without allocating (the paper has no counterpart) ---------------------------
+ * ndgsbp_decode_static is ndgsbp_decode without a workspace: it allocates no device memory.  It
+ * is for callers that cannot allocate while they decode -- a real-time receive loop that may
+ * not call cudaMalloc (the call can synchronise the device and its latency is unbounded), or a
+ * process whose device memory is already handed out by another allocator, so that a new
+ * allocation would fail.  The kernels' scratch (the frame counter, and the per-CTA message slots
+ * of the global-memory variants) lives in one static device array of
+ * NDGSBP_STATIC_SCRATCH_BYTES bytes inside this library, which every GPU that loads the library
+ * holds until the process exits.
+ *   - The first call on a device looks up the array's device address (a one-time set-up per
+ *     device); make that first call before any stream capture.
+ *   - The grouping's tables must already be on the device: call ndgsbp_decode_plan with the same
+ *     parameters, on that device, during set-up (that call uploads them).  Otherwise INVALID.
+ *   - A launch that needs more scratch than the array holds is rejected with WORKSPACE (lower
+ *     ctas_per_sm, keep messages in shared memory, or use ndgsbp_decode with a workspace).
+ *   - Every call shares the one array and clears its counter on `stream`; calls whose work
+ *     overlaps on the GPU (other streams, other threads) race on it and corrupt each other's
+ *     results, so issue them one after another on one stream.
+ * Arguments, outputs and the remaining errors are those of ndgsbp_decode. */
+#define NDGSBP_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+ndgsbp_status ndgsbp_decode_static(const ndgsbp_groups* groups, const ndgsbp_params* params,
+                                   const void* d_llr, int32_t llr_dtype, int64_t n_frames,
+                                   uint32_t* d_hard_bits, int32_t* d_iters, uint8_t* d_syndrome_ok,
+                                   float* d_posterior, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

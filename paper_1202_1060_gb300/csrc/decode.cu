@@ -263,7 +263,8 @@ static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     return NDGSBP_OK;
 }
 
-static ndgsbp_status device_layout(const Groups& g, bool flood, const Layout*& L, const DeviceLayout*& D) {
+static ndgsbp_status device_layout(const Groups& g, bool flood, const Layout*& L, const DeviceLayout*& D,
+                                   bool allow_upload = true) {
     L = flood ? &flood_layout(g) : &g.grouped;
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -271,6 +272,9 @@ static ndgsbp_status device_layout(const Groups& g, bool flood, const Layout*& L
     auto& cache = flood ? g.dev_flood : g.dev_grouped;
     auto it = cache.find(dev);
     if (it == cache.end()) {
+        if (!allow_upload)
+            return fail(NDGSBP_ERR_INVALID, "grouping tables are not on device %d yet: call ndgsbp_decode_plan "
+                                            "with the same parameters on this device first", dev);
         DeviceLayout dl;
         ndgsbp_status st = upload_layout(*L, dl);
         if (st) return st;
@@ -280,7 +284,8 @@ static ndgsbp_status device_layout(const Groups& g, bool flood, const Layout*& L
     return NDGSBP_OK;
 }
 
-static ndgsbp_status device_qc(const Groups& g, bool flood, const QcLayout*& Q, const DeviceQc*& D) {
+static ndgsbp_status device_qc(const Groups& g, bool flood, const QcLayout*& Q, const DeviceQc*& D,
+                               bool allow_upload = true) {
     Q = flood ? &flood_qc_layout(g) : &g.qc;
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -288,6 +293,9 @@ static ndgsbp_status device_qc(const Groups& g, bool flood, const QcLayout*& Q, 
     auto& cache = flood ? g.dev_flood_qc : g.dev_qc;
     auto it = cache.find(dev);
     if (it == cache.end()) {
+        if (!allow_upload)
+            return fail(NDGSBP_ERR_INVALID, "grouping tables are not on device %d yet: call ndgsbp_decode_plan "
+                                            "with the same parameters on this device first", dev);
         DeviceQc dq;
         ndgsbp_status st = upload_qc(*Q, dq);
         if (st) return st;
@@ -370,7 +378,7 @@ static ndgsbp_status finish_grid(const void* fn, int threads, size_t smem, const
 
 // Layered QC kernel plan, when the grouping is made of whole layers and a window fits a CTA.
 static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
-                                  const DeviceInfo& di, Plan& plan, bool* ok) {
+                                  const DeviceInfo& di, Plan& plan, bool* ok, bool allow_upload = true) {
     *ok = false;
     const QcLayout& Q = flood ? flood_qc_layout(g) : g.qc;
     if (!Q.ok) return NDGSBP_OK;
@@ -393,7 +401,7 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     int64_t grid = 0;
     ndgsbp_status st = finish_grid(reinterpret_cast<const void*>(fn), threads, smem, p, n_frames, di, per_sm, grid);
     if (st) return st;
-    st = device_qc(g, flood, plan.Q, plan.DQ);
+    st = device_qc(g, flood, plan.Q, plan.DQ, allow_upload);
     if (st) return st;
     plan.qc = true;
     plan.qfn = fn;
@@ -414,7 +422,8 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     return NDGSBP_OK;
 }
 
-static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, Plan& plan) {
+static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, Plan& plan,
+                               bool allow_upload = true) {
     ndgsbp_status st = validate_params(p);
     if (st) return st;
     const bool flood = p->schedule == NDGSBP_SCHEDULE_FLOOD;
@@ -424,14 +433,14 @@ static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t 
     const bool want_qc = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL;
     if (p->variant == NDGSBP_VARIANT_AUTO || want_qc) {
         bool ok = false;
-        st = make_qc_plan(g, p, n_frames, flood, di, plan, &ok);
+        st = make_qc_plan(g, p, n_frames, flood, di, plan, &ok, allow_upload);
         if (st) return st;
         if (ok) return NDGSBP_OK;
         if (want_qc)
             return fail(NDGSBP_ERR_UNSUPPORTED, "QC variant needs a QC code grouped in whole layers with a window "
                                                 "that fits one CTA");
     }
-    st = device_layout(g, flood, plan.L, plan.D);
+    st = device_layout(g, flood, plan.L, plan.D, allow_upload);
     if (st) return st;
     const Layout& L = *plan.L;
     const int maxdc = degree_bound(L.max_deg);
@@ -513,6 +522,76 @@ static void fill_run(RunArgs& r, const Groups& g, const ndgsbp_params* params, c
         r.retire_ns = reinterpret_cast<unsigned long long*>(extras->d_retire_ns);
         r.msgs_out = extras->d_messages;
     }
+}
+
+
+// ---- decoding with the library's own scratch --------------------------------------------
+// Scratch of ndgsbp_decode_static: one array per device, held by every GPU that loads the
+// library until the process exits.  Host code may not use its name as a device address (it is
+// only a host-side stand-in); static_scratch_address() asks the runtime for the real one.
+static __device__ __align__(256) unsigned char g_static_scratch[NDGSBP_STATIC_SCRATCH_BYTES];
+
+static std::mutex g_static_mu;
+static std::map<int, void*> g_static_addr;   // device -> device address of g_static_scratch
+
+// Set-up, once per device, with that device current.
+static ndgsbp_status static_scratch_address(void** out) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    auto it = g_static_addr.find(dev);
+    if (it == g_static_addr.end()) {
+        void* p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+        it = g_static_addr.emplace(dev, p).first;
+    }
+    *out = it->second;
+    return NDGSBP_OK;
+}
+
+// Launch a plan with `ws` as its scratch (counter already cleared on the stream).
+static ndgsbp_status launch_with_scratch(const Groups& g, const Plan& plan, const ndgsbp_params* params,
+                                         const void* d_llr, int32_t llr_dtype, int64_t n_frames,
+                                         unsigned char* ws, uint32_t* d_hard_bits, int32_t* d_iters,
+                                         uint8_t* d_syndrome_ok, float* d_posterior, cudaStream_t s) {
+    if (plan.qc) {
+        QcArgs a;
+        std::memset(&a, 0, sizeof(a));
+        fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior,
+                 nullptr);
+        fill_qc_args(a, *plan.Q, *plan.DQ, plan.msg_smem ? nullptr : ws + kHeaderBytes);
+        plan.qfn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
+    } else {
+        const Layout& L = *plan.L;
+        const DeviceLayout& D = *plan.D;
+        DecodeArgs a;
+        std::memset(&a, 0, sizeof(a));
+        fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior,
+                 nullptr);
+        a.M = L.M;
+        a.Epad = L.Epad;
+        a.G = L.G;
+        a.max_gd = L.max_gd;
+        a.slot_deg = D.slot_deg;
+        a.tile_base = D.tile_base;
+        a.edge_vn = D.edge_vn;
+        a.edge_csr = D.edge_csr;
+        a.grp_ptr = D.grp_ptr;
+        a.ge_slot = D.ge_slot;
+        a.ge_dpos = D.ge_dpos;
+        a.grp_colbase = D.grp_colbase;
+        a.grp_ncol = D.grp_ncol;
+        a.gcol = D.gcol;
+        size_t off = kHeaderBytes;
+        if (!plan.msg_smem) {
+            a.ws_msgs = ws + off;
+            off += align256(static_cast<size_t>(plan.pub.grid) * L.Epad * msg_size(params->msg_dtype));
+        }
+        if (!plan.delta_smem) a.ws_delta = reinterpret_cast<float*>(ws + off);
+        plan.fn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return NDGSBP_OK;
 }
 
 }  // namespace ndgsbp
@@ -612,6 +691,37 @@ ndgsbp_status ndgsbp_decode(const ndgsbp_groups* groups, const ndgsbp_params* pa
                             void* stream) {
     return ndgsbp_decode_ex(groups, params, d_llr, llr_dtype, n_frames, d_workspace, workspace_bytes,
                             d_hard_bits, d_iters, d_syndrome_ok, d_posterior, nullptr, stream);
+}
+
+ndgsbp_status ndgsbp_decode_static(const ndgsbp_groups* groups, const ndgsbp_params* params,
+                                   const void* d_llr, int32_t llr_dtype, int64_t n_frames,
+                                   uint32_t* d_hard_bits, int32_t* d_iters, uint8_t* d_syndrome_ok,
+                                   float* d_posterior, void* stream) {
+    clear_error();
+    if (!groups) return fail(NDGSBP_ERR_INVALID, "decode_static: null groups handle");
+    if (n_frames < 0) return fail(NDGSBP_ERR_INVALID, "decode_static: n_frames < 0");
+    if (llr_dtype != NDGSBP_F32 && llr_dtype != NDGSBP_F64 && llr_dtype != NDGSBP_F16 && llr_dtype != NDGSBP_BF16)
+        return fail(NDGSBP_ERR_INVALID, "decode_static: unknown llr_dtype %d", llr_dtype);
+    if (n_frames > 0 && (!d_llr || !d_hard_bits))
+        return fail(NDGSBP_ERR_INVALID, "decode_static: d_llr and d_hard_bits are required");
+    const Groups& g = groups->g;
+    Plan plan;
+    ndgsbp_status st = make_plan(g, params, n_frames, plan, /*allow_upload=*/false);
+    if (st) return st;
+    if (n_frames == 0) return NDGSBP_OK;
+    if (plan.pub.workspace_bytes > static_cast<int64_t>(NDGSBP_STATIC_SCRATCH_BYTES))
+        return fail(NDGSBP_ERR_WORKSPACE,
+                    "decode_static: this launch needs %lld bytes of scratch but the static array holds %u; "
+                    "lower ctas_per_sm, let the messages stay in shared memory, or use ndgsbp_decode",
+                    static_cast<long long>(plan.pub.workspace_bytes), NDGSBP_STATIC_SCRATCH_BYTES);
+    void* ws = nullptr;
+    st = static_scratch_address(&ws);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the frame counter must start at zero; message and delta slots are written before read
+    CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), s));
+    return launch_with_scratch(g, plan, params, d_llr, llr_dtype, n_frames, static_cast<unsigned char*>(ws),
+                               d_hard_bits, d_iters, d_syndrome_ok, d_posterior, s);
 }
 
 }  // extern "C"

@@ -83,7 +83,9 @@ _SIGS = {
                              _P, _P, _P, _P, _P]),
     "ndgsbp_decode_ex": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, ctypes.c_size_t,
                                 _P, _P, _P, _P, ctypes.POINTER(Extras), _P]),
+    "ndgsbp_decode_static": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, _P, _P, _P, _P]),
 }
+STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
 def _bind(lib, sigs):
@@ -296,6 +298,15 @@ def decode_plain(groups: Groups, params: Params, llr, workspace, hard_bits, iter
                               _dptr(workspace), workspace.numel() * workspace.element_size(),
                               _dptr(hard_bits), _dptr(iters), _dptr(syndrome_ok), _dptr(posterior),
                               _stream(stream)))
+
+
+def decode_static(groups: Groups, params: Params, llr, hard_bits, iters=None, syndrome_ok=None,
+                  posterior=None, stream=None):
+    """ndgsbp_decode_static: decode without a workspace (the library's static scratch array).
+    The grouping must have been planned on this device first (Groups.plan)."""
+    _check(_lib.ndgsbp_decode_static(groups.handle, ctypes.byref(params), _dptr(llr), dtype_code(llr),
+                                     llr.shape[0], _dptr(hard_bits), _dptr(iters), _dptr(syndrome_ok),
+                                     _dptr(posterior), _stream(stream)))
 
 
 def unpack_bits(words, N: int):
