@@ -38,7 +38,8 @@ GROUP_SEED = 2304
 CHANNEL_SEED = 0x5EED0000
 RATE = 0.5
 MUFU_PER_EDGE_UPDATE = 3          # exp2, reciprocal, log2 per edge of Eq. (1)
-MUFU_PER_CLK_PER_SM = 16          # multi-function unit results per clock per SM
+MUFU_PER_CLK_PER_SM = 32          # MUFU results per clock per SM sustained on GB300 (one warp
+                                  # instruction per clock per SM, the XU-pipe peak ncu normalises to)
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "decode_qc_n2304_traffic.json")
 
 
@@ -314,7 +315,9 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = MUFU_PER_CLK_PER_SM * sms * peak_clock_mhz * 1e6 / 1e12
-    kname = "qc_decode_kernel" if plan.variant in (nd.VARIANT_QC, nd.VARIANT_QC_GLOBAL) else "decode_kernel"
+    kname = {nd.VARIANT_QC: "qc_decode_kernel", nd.VARIANT_QC_GLOBAL: "qc_decode_kernel",
+             nd.VARIANT_QC_PAIR: "qc_pair_kernel", nd.VARIANT_QC_PAIR_GLOBAL: "qc_pair_kernel"}.get(plan.variant,
+                                                                                            "decode_kernel")
     traffic, traffic_rec = profiled_traffic(kname)
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
@@ -361,6 +364,7 @@ def run_ours(args):
                         "what": "service = frame retire - frame start; batch = frame retire - launch start "
                                 "(last timed decode launch, 65,536 frames at 2.5 dB)"},
             "fer": fer, "ber": ber, "mean_iterations": iter_sum / max(frames_done, 1),
+            "mean_iterations_per_point": (st[:, nd.STAT_ITERATIONS] / np.maximum(st[:, nd.STAT_FRAMES], 1)).tolist(),
             "coded_gbit_s": frames_total * c.N / elapsed_max / 1e9,
             "clocks": clk, "gpu_launches": 2 * len(EBN0) * args.steps,
             "plan": plan.as_dict(), "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,

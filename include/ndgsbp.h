@@ -65,6 +65,8 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_VARIANT_GLOBAL 2  /* edge messages in per-CTA global-memory slots */
 #define NDGSBP_VARIANT_QC 3      /* layered QC kernel: circulant index arithmetic, no tables */
 #define NDGSBP_VARIANT_QC_GLOBAL 4 /* layered QC kernel with messages in global-memory slots */
+#define NDGSBP_VARIANT_QC_PAIR 5   /* layered QC kernel, two CNs per thread, packed FP32 arithmetic */
+#define NDGSBP_VARIANT_QC_PAIR_GLOBAL 6 /* the pair kernel with messages in global-memory slots */
 
 /* stats counters accumulated by ndgsbp_decode_ex (uint64 each) */
 #define NDGSBP_STAT_FRAMES 0
@@ -92,7 +94,7 @@ typedef struct ndgsbp_params {
 
 /* Launch plan the library picked for a decode (filled by ndgsbp_decode_plan). */
 typedef struct ndgsbp_plan {
-    int32_t variant;        /* NDGSBP_VARIANT_SMEM / GLOBAL / QC / QC_GLOBAL */
+    int32_t variant;        /* the NDGSBP_VARIANT_* kernel that runs (never AUTO) */
     int32_t block_threads;
     int32_t grid;           /* persistent CTAs */
     int32_t ctas_per_sm;

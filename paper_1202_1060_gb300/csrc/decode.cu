@@ -249,7 +249,7 @@ static ndgsbp_status upload_layout(const Layout& L, DeviceLayout& D) {
 static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     BlobBuilder b;
     const size_t o_tab = b.add(Q.edge_tab), o_deg = b.add(Q.layer_deg), o_off = b.add(Q.layer_off);
-    const size_t o_gl = b.add(Q.group_layers), o_csr = b.add(Q.csr_of);
+    const size_t o_gl = b.add(Q.group_layers), o_csr = b.add(Q.csr_of), o_str = b.add(Q.layer_stride);
     void* blob = nullptr;
     ndgsbp_status st = b.upload(&blob);
     if (st) return st;
@@ -257,6 +257,7 @@ static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     D.blob = blob;
     D.edge_tab = reinterpret_cast<const int32_t*>(p + o_tab);
     D.layer_deg = reinterpret_cast<const int32_t*>(p + o_deg);
+    D.layer_stride = reinterpret_cast<const int32_t*>(p + o_str);
     D.layer_off = reinterpret_cast<const int32_t*>(p + o_off);
     D.group_layers = reinterpret_cast<const int32_t*>(p + o_gl);
     D.csr_of = reinterpret_cast<const int32_t*>(p + o_csr);
@@ -348,7 +349,7 @@ static ndgsbp_status validate_params(const ndgsbp_params* p) {
     if (p->block_threads < 0 || p->block_threads > 1024 || p->block_threads % 32)
         return fail(NDGSBP_ERR_INVALID, "block_threads must be 0 or a multiple of 32 up to 1024");
     if (p->ctas_per_sm < 0) return fail(NDGSBP_ERR_INVALID, "ctas_per_sm must be >= 0");
-    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_GLOBAL)
+    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_PAIR_GLOBAL)
         return fail(NDGSBP_ERR_INVALID, "unknown variant %d", p->variant);
     return NDGSBP_OK;
 }
@@ -377,6 +378,7 @@ static ndgsbp_status finish_grid(const void* fn, int threads, size_t smem, const
 }
 
 // Layered QC kernel plan, when the grouping is made of whole layers and a window fits a CTA.
+// QC / QC_GLOBAL (and AUTO) run the single-CN kernel, QC_PAIR / QC_PAIR_GLOBAL the pair kernel.
 static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
                                   const DeviceInfo& di, Plan& plan, bool* ok, bool allow_upload = true) {
     *ok = false;
@@ -384,18 +386,32 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     if (!Q.ok) return NDGSBP_OK;
     const int maxdc = degree_bound(Q.max_deg);
     if (!maxdc) return NDGSBP_OK;
-    const int active = Q.window * Q.Z;
+    const bool spec = qc_degrees_specialised(Q, maxdc);
+    const bool want_single = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL;
+    const bool want_pair = p->variant == NDGSBP_VARIANT_QC_PAIR || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL;
+    const bool force_global = p->variant == NDGSBP_VARIANT_QC_GLOBAL || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL;
+    const int active_pair = Q.window * (Q.Z / 2);
+    const bool pair_ok = spec && Q.Z % 2 == 0 && (p->block_threads ? p->block_threads : (active_pair + 31) / 32 * 32) <=
+                                                      qc_pair_max_threads(maxdc);
+    // AUTO keeps the single-CN kernel: on GB300 it is the faster of the two for the codes
+    // measured (the pair kernel halves the FP instructions but also the resident warps).
+    bool pair = false;
+    if (want_pair) {
+        if (!pair_ok) return NDGSBP_OK;
+        pair = true;
+    }
+    (void)want_single;
+    const int active = pair ? active_pair : Q.window * Q.Z;
     const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
-    if (threads < active || threads > max_threads_for(maxdc)) return NDGSBP_OK;
+    if (threads < active || threads > (pair ? qc_pair_max_threads(maxdc) : max_threads_for(maxdc))) return NDGSBP_OK;
     const size_t budget = static_cast<size_t>(di.smem_optin) - 64;
     const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 4);
-    const size_t m_bytes = align16(static_cast<size_t>(g.code->E) * msg_size(p->msg_dtype));
+    const size_t m_bytes = align16(static_cast<size_t>(Q.msg_slots) * msg_size(p->msg_dtype));
     const size_t t_bytes = qc_table_bytes(Q);
     if (p_bytes + t_bytes > budget) return NDGSBP_OK;
-    bool msg_smem = p_bytes + m_bytes + t_bytes <= budget;
-    if (p->variant == NDGSBP_VARIANT_QC_GLOBAL) msg_smem = false;
+    const bool msg_smem = !force_global && p_bytes + m_bytes + t_bytes <= budget;
     const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
-    QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, qc_degrees_specialised(Q, maxdc));
+    QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair);
     if (!fn) return NDGSBP_OK;
     int per_sm = 0;
     int64_t grid = 0;
@@ -407,7 +423,8 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     plan.qfn = fn;
     plan.msg_smem = msg_smem;
     ndgsbp_plan& o = plan.pub;
-    o.variant = msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL;
+    o.variant = pair ? (msg_smem ? NDGSBP_VARIANT_QC_PAIR : NDGSBP_VARIANT_QC_PAIR_GLOBAL)
+                     : (msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL);
     o.block_threads = threads;
     o.grid = static_cast<int32_t>(grid);
     o.ctas_per_sm = per_sm;
@@ -415,8 +432,8 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     o.delta_in_smem = 0;
     o.smem_bytes = static_cast<int64_t>(smem);
     o.workspace_bytes = static_cast<int64_t>(
-        kHeaderBytes + (msg_smem ? 0 : align256(static_cast<size_t>(grid) * g.code->E * msg_size(p->msg_dtype))));
-    o.stored_edges = g.code->E;
+        kHeaderBytes + (msg_smem ? 0 : align256(static_cast<size_t>(grid) * Q.msg_slots * msg_size(p->msg_dtype))));
+    o.stored_edges = Q.msg_slots;
     o.edge_updates_per_iter = flood ? g.code->E : g.edge_updates;
     *ok = true;
     return NDGSBP_OK;
@@ -430,7 +447,7 @@ static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t 
     DeviceInfo di;
     st = device_info(di);
     if (st) return st;
-    const bool want_qc = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL;
+    const bool want_qc = p->variant >= NDGSBP_VARIANT_QC;
     if (p->variant == NDGSBP_VARIANT_AUTO || want_qc) {
         bool ok = false;
         st = make_qc_plan(g, p, n_frames, flood, di, plan, &ok, allow_upload);

@@ -1,150 +1,194 @@
-// Layered QC decode kernel for sm_103a.
+// Layered QC decode kernels for sm_103a.
 //
-// For QC codes grouped in whole layers (windows of `window` consecutive-in-schedule layers of
-// Z CNs each), the VN of edge k of CN c in layer l is b_k Z + (c + s_k) mod Z, with (b_k, s_k)
-// the block column and circulant shift of the layer's k-th base entry.  The kernel computes
-// those indices instead of reading per-edge tables: each layer contributes one (b Z + s, Z - s)
-// pair per edge, held in shared memory and read as a broadcast.
+// For QC codes grouped in whole layers (windows of `window` layers of Z CNs each), the VN of
+// edge k of CN c in layer l is b_k Z + (c + s_k) mod Z, with (b_k, s_k) the block column and
+// circulant shift of the layer's k-th base entry.  The kernels compute those indices instead of
+// reading per-edge tables: each layer contributes one (4 (b Z + s), Z - s) pair per edge, held
+// in shared memory and read as a broadcast, and the index is kept as a byte offset into the
+// posterior.  The messages of CN c of layer l sit at layer_off[l] + c S_l + k with an odd
+// stride S_l >= d_l, so 32 consecutive CNs touch 32 distinct banks and k is a compile-time
+// offset.
 //
-// Thread t of the CTA owns window position j = t / Z and CN c = t mod Z for every group, so a
-// warp covers consecutive CNs of one layer: posterior reads P[b Z + (c + s) mod Z] and message
-// accesses msg[layer_off + k Z + c] are consecutive words (conflict-free).  Phase A (Eq. (1) on
-// every CN of the group) keeps each edge's message change in registers; phase B
-// applies the changes layer position by layer position (a layer holds each VN at most once),
-// which is the same fixed order as the colour order of the general kernel, so the two kernels
-// produce identical results.
+// qc_decode_kernel: thread t owns window position j = t / Z and CN c = t mod Z in every group.
+// qc_pair_kernel:   thread t owns position j = t / (Z/2) and the two CNs c and c + Z/2; all the
+//                   arithmetic of Eq. (1) runs on float2 pairs (packed FP32 instructions, each
+//                   lane rounded exactly as the scalar operation), so the two kernels give
+//                   identical results while the pair kernel issues about half the FP work.
+// Both run phase A (Eq. (1) on every CN of the group; VN offsets and message changes kept in
+// registers) and phase B (changes added layer position by layer position, the same fixed order
+// as the colour order of the table-driven kernel, whose results they therefore reproduce).
+// Layers get fully unrolled code for their exact degree when every layer degree lies in
+// (MAXDC/2, MAXDC] (the usual QC case); other codes use the degree-generic instances.
 #include <cstring>
 
 #include "decode_qc.h"
 
 namespace ndgsbp {
 
-__device__ __forceinline__ int qc_vn(int2 e, int c, int Z) { return e.x + c - (c >= e.y ? Z : 0); }
+// Byte offset of the VN of table entry e for CN c (c4 = 4 c, Z4 = 4 Z).
+__device__ __forceinline__ int qc_vb(int2 e, int c, int c4, int Z4) { return e.x + c4 - (c >= e.y ? Z4 : 0); }
 
-// Phase A for the CN of this thread in a layer of exactly D edges: VN->CN messages from the
-// posterior, Eq. (1), new messages stored; the VN indices and message changes stay in registers
-// for phase B.
+__device__ __forceinline__ float& at_byte(float* P, int vb) {
+    return *reinterpret_cast<float*>(reinterpret_cast<char*>(P) + vb);
+}
+
+// ---- single-CN kernel ---------------------------------------------------------------------
 template <int D, int MAXDC, typename MsgT>
-__device__ __forceinline__ void qc_phase_a(const int2* __restrict__ et, int c, int Z, const float* __restrict__ P,
-                                           MsgT* __restrict__ m, float lim, int (&vv)[MAXDC], float (&dl)[MAXDC]) {
+__device__ __forceinline__ void qc_phase_a(const int2* __restrict__ et, int c, int c4, int Z4, float* __restrict__ P,
+                                           MsgT* __restrict__ m, float lim, int (&vb)[MAXDC], float (&dl)[MAXDC]) {
     static_assert(D <= MAXDC, "degree above the bound");
     float t[D], old[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        vv[k] = qc_vn(et[k], c, Z);
-        old[k] = to_f(m[k * Z]);
-        t[k] = P[vv[k]] - old[k];
+        vb[k] = qc_vb(et[k], c, c4, Z4);
+        old[k] = to_f(m[k]);
+        t[k] = at_byte(P, vb[k]) - old[k];
     }
     check_node_update<D>(t, D, lim, [&](int k, float val) {
         const MsgT q = from_f<MsgT>(val);
-        m[k * Z] = q;
+        m[k] = q;
+        dl[k] = to_f(q) - old[k];
+    });
+}
+
+template <int MAXDC, typename MsgT>
+__device__ __forceinline__ void qc_phase_a_any(const int2* __restrict__ et, int c, int c4, int Z4, int d,
+                                               float* __restrict__ P, MsgT* __restrict__ m, float lim,
+                                               int (&vb)[MAXDC], float (&dl)[MAXDC]) {
+    float t[MAXDC], old[MAXDC];
+#pragma unroll
+    for (int k = 0; k < MAXDC; ++k) {
+        if (k < d) {
+            vb[k] = qc_vb(et[k], c, c4, Z4);
+            old[k] = to_f(m[k]);
+            t[k] = at_byte(P, vb[k]) - old[k];
+        }
+    }
+    check_node_update<MAXDC>(t, d, lim, [&](int k, float val) {
+        const MsgT q = from_f<MsgT>(val);
+        m[k] = q;
         dl[k] = to_f(q) - old[k];
     });
 }
 
 template <int D, int MAXDC>
-__device__ __forceinline__ void qc_phase_b(float* __restrict__ P, const int (&vv)[MAXDC], const float (&dl)[MAXDC]) {
+__device__ __forceinline__ void qc_phase_b(float* __restrict__ P, const int (&vb)[MAXDC], const float (&dl)[MAXDC]) {
 #pragma unroll
-    for (int k = 0; k < D; ++k) P[vv[k]] += dl[k];
+    for (int k = 0; k < D; ++k) at_byte(P, vb[k]) += dl[k];
 }
 
 template <int D>
-__device__ __forceinline__ unsigned qc_parity(const int2* __restrict__ et, int c, int Z, const float* __restrict__ P) {
+__device__ __forceinline__ unsigned qc_parity(const int2* __restrict__ et, int c, int c4, int Z4, float* __restrict__ P) {
     unsigned p = 0u;
 #pragma unroll
-    for (int k = 0; k < D; ++k) p ^= (P[qc_vn(et[k], c, Z)] < 0.f) ? 1u : 0u;
+    for (int k = 0; k < D; ++k) p ^= (at_byte(P, qc_vb(et[k], c, c4, Z4)) < 0.f) ? 1u : 0u;
     return p;
 }
 
-// Degree-generic versions (any d <= MAXDC), used for degrees outside the specialised set.
-template <int MAXDC, typename MsgT>
-__device__ __forceinline__ void qc_phase_a_any(const int2* __restrict__ et, int c, int Z, int d, const float* __restrict__ P,
-                                               MsgT* __restrict__ m, float lim, int (&vv)[MAXDC], float (&dl)[MAXDC]) {
-    float t[MAXDC], old[MAXDC];
-#pragma unroll
-    for (int k = 0; k < MAXDC; ++k) {
-        if (k < d) {
-            vv[k] = qc_vn(et[k], c, Z);
-            old[k] = to_f(m[k * Z]);
-            t[k] = P[vv[k]] - old[k];
-        }
-    }
-    check_node_update<MAXDC>(t, d, lim, [&](int k, float val) {
-        const MsgT q = from_f<MsgT>(val);
-        m[k * Z] = q;
-        dl[k] = to_f(q) - old[k];
-    });
-}
-
-// Warp-uniform dispatch on the layer degree (a warp covers one layer when 32 divides Z).
+// Warp-uniform dispatch on the layer degree (a warp covers one layer when 32 divides the CNs a
+// layer spreads over).
 #define NDGSBP_DEGREE_CASES(MAXDC, X) \
     if (MAXDC == 8) { X(5) X(6) X(7) X(8) } else if (MAXDC == 16) { X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) }
+#define NDGSBP_DD(D) ((D) <= MAXDC ? (D) : MAXDC)
 
-// SPEC instances run fully unrolled code for the layer's exact degree, chosen per layer by a
-// warp-uniform dispatch; they serve codes whose layer degrees all lie in (MAXDC/2, MAXDC] (one
-// or two row degrees just below the bound, the usual QC case).  Other instances run the
-// degree-generic predicated code.  Keeping the two apart keeps the register footprint of the
-// specialised code small (a shared fallback path raises it for every case).
+// Shared-memory tables of a QC launch (loaded once per CTA).
+struct QcSmem {
+    float* P;
+    unsigned char* msg;   // used when messages are in shared memory
+    int2* tab;
+    int* ldeg;
+    int* lstride;
+    int* loff;
+    int* glay;
+};
+
+template <typename MsgT, bool MSG_SMEM>
+__device__ __forceinline__ QcSmem qc_smem_layout(unsigned char* smem, const QcArgs& a) {
+    QcSmem s;
+    const RunArgs& r = a.r;
+    s.P = reinterpret_cast<float*>(smem);
+    size_t off = (static_cast<size_t>(r.N) * 4 + 15) & ~static_cast<size_t>(15);
+    s.msg = smem + off;
+    if (MSG_SMEM) off += (static_cast<size_t>(a.msg_slots) * sizeof(MsgT) + 15) & ~static_cast<size_t>(15);
+    s.tab = reinterpret_cast<int2*>(smem + off);
+    off += (static_cast<size_t>(a.nl) * a.maxdeg * 8 + 15) & ~static_cast<size_t>(15);
+    s.ldeg = reinterpret_cast<int*>(smem + off);
+    off += (static_cast<size_t>(a.nl) * 4 + 15) & ~static_cast<size_t>(15);
+    s.lstride = reinterpret_cast<int*>(smem + off);
+    off += (static_cast<size_t>(a.nl) * 4 + 15) & ~static_cast<size_t>(15);
+    s.loff = reinterpret_cast<int*>(smem + off);
+    off += (static_cast<size_t>(a.nl) * 4 + 15) & ~static_cast<size_t>(15);
+    s.glay = reinterpret_cast<int*>(smem + off);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < a.nl * a.maxdeg; i += nt) s.tab[i] = a.edge_tab[i];
+    for (int i = tid; i < a.nl; i += nt) {
+        s.ldeg[i] = a.layer_deg[i];
+        s.lstride[i] = a.layer_stride[i];
+        s.loff[i] = a.layer_off[i];
+    }
+    for (int i = tid; i < a.G * a.window; i += nt) s.glay[i] = a.group_layers[i];
+    return s;
+}
+
+template <typename MsgT>
+__device__ __forceinline__ void qc_frame_begin(const QcArgs& a, const QcSmem& s, MsgT* msg, long long f) {
+    const RunArgs& r = a.r;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (r.start_ns && tid == 0) r.start_ns[f] = global_timer_ns();
+    for (int n = tid; n < r.N; n += nt) s.P[n] = load_llr(r.llr, r.llr_dtype, f * r.N + n);
+    for (int e = tid; e < a.msg_slots; e += nt) msg[e] = from_f<MsgT>(0.f);
+}
+
+template <typename MsgT>
+__device__ __forceinline__ void qc_frame_messages_out(const QcArgs& a, const MsgT* msg, long long f) {
+    const RunArgs& r = a.r;
+    if (!r.msgs_out) return;
+    for (int e = threadIdx.x; e < a.msg_slots; e += blockDim.x) {
+        const int csr = __ldg(a.csr_of + e);
+        if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]);
+    }
+}
+
 template <typename MsgT, bool MSG_SMEM, int MAXDC, bool SPEC>
 __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const QcArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_frame;
     __shared__ unsigned s_err;
     const RunArgs& r = a.r;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int Z = a.Z, W = a.window, nl = a.nl, md = a.maxdeg;
-    float* P = reinterpret_cast<float*>(smem);
-    size_t off = (static_cast<size_t>(r.N) * 4 + 15) & ~static_cast<size_t>(15);
-    MsgT* msg;
-    if (MSG_SMEM) {
-        msg = reinterpret_cast<MsgT*>(smem + off);
-        off += (static_cast<size_t>(r.E) * sizeof(MsgT) + 15) & ~static_cast<size_t>(15);
-    } else {
-        msg = static_cast<MsgT*>(a.ws_msgs) + static_cast<size_t>(blockIdx.x) * r.E;
-    }
-    int2* tab = reinterpret_cast<int2*>(smem + off);
-    off += (static_cast<size_t>(nl) * md * 8 + 15) & ~static_cast<size_t>(15);
-    int* ldeg = reinterpret_cast<int*>(smem + off);
-    off += (static_cast<size_t>(nl) * 4 + 15) & ~static_cast<size_t>(15);
-    int* loff = reinterpret_cast<int*>(smem + off);
-    off += (static_cast<size_t>(nl) * 4 + 15) & ~static_cast<size_t>(15);
-    int* glay = reinterpret_cast<int*>(smem + off);
-    for (int i = tid; i < nl * md; i += nt) tab[i] = a.edge_tab[i];
-    for (int i = tid; i < nl; i += nt) {
-        ldeg[i] = a.layer_deg[i];
-        loff[i] = a.layer_off[i];
-    }
-    for (int i = tid; i < a.G * W; i += nt) glay[i] = a.group_layers[i];
+    const int tid = threadIdx.x;
+    const int Z = a.Z, W = a.window, nl = a.nl, md = a.maxdeg, Z4 = 4 * a.Z;
+    const QcSmem s = qc_smem_layout<MsgT, MSG_SMEM>(smem, a);
+    float* P = s.P;
+    MsgT* msg = MSG_SMEM ? reinterpret_cast<MsgT*>(s.msg)
+                         : static_cast<MsgT*>(a.ws_msgs) + static_cast<size_t>(blockIdx.x) * a.msg_slots;
     const int j = tid / Z;
-    const int c = tid - j * Z;
+    const int c = tid - j * Z, c4 = 4 * c;
     const bool active = j < W;
     const float lim = r.llr_max;
     if (tid == 0) s_err = 0u;
     for (;;) {
         const long long f = next_frame(r, &s_frame);   // barrier: also orders the table loads
         if (f >= r.n_frames) break;
-        if (r.start_ns && tid == 0) r.start_ns[f] = global_timer_ns();
-        for (int n = tid; n < r.N; n += nt) P[n] = load_llr(r.llr, r.llr_dtype, f * r.N + n);
-        for (int e = tid; e < r.E; e += nt) msg[e] = from_f<MsgT>(0.f);
+        qc_frame_begin(a, s, msg, f);
         __syncthreads();
         int it = 1, unsat = 1;
         for (;; ++it) {
             for (int g = 0; g < a.G; ++g) {
                 float dl[MAXDC];
-                int vv[MAXDC];
+                int vb[MAXDC];
                 int d = 0;
                 if (active) {
-                    const int l = glay[g * W + j];
-                    d = ldeg[l];
-                    const int2* et = tab + l * md;
-                    MsgT* m = msg + loff[l] + c;
+                    const int l = s.glay[g * W + j];
+                    d = s.ldeg[l];
+                    const int2* et = s.tab + l * md;
+                    MsgT* m = msg + s.loff[l] + c * s.lstride[l];
                     if constexpr (SPEC) {
 #define NDGSBP_CASE_A(D) \
-    if (d == D) qc_phase_a<(D <= MAXDC ? D : MAXDC), MAXDC, MsgT>(et, c, Z, P, m, lim, vv, dl);
+    if (d == D) qc_phase_a<NDGSBP_DD(D), MAXDC, MsgT>(et, c, c4, Z4, P, m, lim, vb, dl);
                         NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_A)
 #undef NDGSBP_CASE_A
                     } else {
-                        qc_phase_a_any<MAXDC, MsgT>(et, c, Z, d, P, m, lim, vv, dl);
+                        qc_phase_a_any<MAXDC, MsgT>(et, c, c4, Z4, d, P, m, lim, vb, dl);
                     }
                 }
                 __syncthreads();
@@ -152,13 +196,13 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const
                     if (active && j == jj) {
                         if constexpr (SPEC) {
 #define NDGSBP_CASE_B(D) \
-    if (d == D) qc_phase_b<(D <= MAXDC ? D : MAXDC), MAXDC>(P, vv, dl);
+    if (d == D) qc_phase_b<NDGSBP_DD(D), MAXDC>(P, vb, dl);
                             NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_B)
 #undef NDGSBP_CASE_B
                         } else {
 #pragma unroll
                             for (int k = 0; k < MAXDC; ++k)
-                                if (k < d) P[vv[k]] += dl[k];
+                                if (k < d) at_byte(P, vb[k]) += dl[k];
                         }
                     }
                     __syncthreads();
@@ -169,18 +213,18 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const
                 unsigned bad = 0u;
                 if (active) {
                     for (int l = j; l < nl; l += W) {
-                        const int d = ldeg[l];
-                        const int2* et = tab + l * md;
+                        const int d = s.ldeg[l];
+                        const int2* et = s.tab + l * md;
                         unsigned p = 0u;
                         if constexpr (SPEC) {
 #define NDGSBP_CASE_S(D) \
-    if (d == D) p = qc_parity<(D <= MAXDC ? D : MAXDC)>(et, c, Z, P);
+    if (d == D) p = qc_parity<NDGSBP_DD(D)>(et, c, c4, Z4, P);
                             NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_S)
 #undef NDGSBP_CASE_S
                         } else {
 #pragma unroll
                             for (int k = 0; k < MAXDC; ++k)
-                                if (k < d) p ^= (P[qc_vn(et[k], c, Z)] < 0.f) ? 1u : 0u;
+                                if (k < d) p ^= (at_byte(P, qc_vb(et[k], c, c4, Z4)) < 0.f) ? 1u : 0u;
                         }
                         bad |= p;
                     }
@@ -190,25 +234,195 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const
             }
             if (last) break;
         }
-        if (r.msgs_out)
-            for (int e = tid; e < r.E; e += nt) r.msgs_out[f * r.E + __ldg(a.csr_of + e)] = to_f(msg[e]);
+        qc_frame_messages_out(a, msg, f);
         write_frame_outputs(r, P, f, it, unsat, &s_err);
         __syncthreads();
     }
 }
 
+// ---- pair kernel --------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// check_node_update on two CNs at once: the same operations, lane by lane, as float2 packed
+// FP32 instructions (so each lane's result equals the scalar routine's bit for bit).
+template <int D, typename Emit>
+__device__ __forceinline__ void check_node_update2(const float2 (&t)[D], float lim, Emit emit) {
+    float2 xu[D], pn[D], pe[D];
+    unsigned sb0 = 0u, sb1 = 0u;
+    float2 cn = f2(1.f), ce = f2(0.f);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        sb0 |= (__float_as_uint(t[k].x) >> 31) << k;
+        sb1 |= (__float_as_uint(t[k].y) >> 31) << k;
+        const float2 x = __fmul2_rn(make_float2(fminf(fabsf(t[k].x), lim), fminf(fabsf(t[k].y), lim)),
+                                    f2(-1.4426950408889634f));
+        const float2 u = make_float2(ex2_approx(x.x), ex2_approx(x.y));   // exp(-|t|)
+        const float2 n = __ffma2_rn(f2(-0.5f), u, f2(0.5f));             // (1 - u) / 2
+        xu[k] = u;
+        pn[k] = cn;
+        pe[k] = ce;
+        ce = __ffma2_rn(ce, __fadd2_rn(n, u), __fmul2_rn(cn, u));
+        cn = __fmul2_rn(cn, n);
+    }
+    const unsigned par0 = __popc(sb0) & 1u, par1 = __popc(sb1) & 1u;
+    float2 sn = f2(1.f), se = f2(0.f);
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) {
+        const float2 u = xu[k];
+        const float2 n = __ffma2_rn(f2(-0.5f), u, f2(0.5f));
+        const float2 en = __fmul2_rn(pn[k], sn);
+        const float2 ee = __ffma2_rn(pe[k], __fadd2_rn(sn, se), __fmul2_rn(pn[k], se));
+        const float2 w = __ffma2_rn(__fmul2_rn(en, make_float2(rcp_approx(ee.x), rcp_approx(ee.y))), f2(2.f), f2(1.f));
+        const float2 lg = __fmul2_rn(f2(0.69314718055994531f), make_float2(lg2_approx(w.x), lg2_approx(w.y)));
+        const float m0 = fminf(lg.x, lim), m1 = fminf(lg.y, lim);
+        const unsigned g0 = ((par0 ^ (sb0 >> k)) & 1u) << 31, g1 = ((par1 ^ (sb1 >> k)) & 1u) << 31;
+        emit(k, make_float2(__uint_as_float(__float_as_uint(m0) | g0), __uint_as_float(__float_as_uint(m1) | g1)));
+        se = __ffma2_rn(se, __fadd2_rn(n, u), __fmul2_rn(sn, u));
+        sn = __fmul2_rn(sn, n);
+    }
+}
+
+template <int D, int MAXDC, typename MsgT>
+__device__ __forceinline__ void qc2_phase_a(const int2* __restrict__ et, int c0, int c1, int Z4, float* __restrict__ P,
+                                            MsgT* __restrict__ m0, MsgT* __restrict__ m1, float lim, int (&vb0)[MAXDC],
+                                            int (&vb1)[MAXDC], float2 (&dl)[MAXDC]) {
+    static_assert(D <= MAXDC, "degree above the bound");
+    float2 t[D], old[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const int2 e = et[k];
+        vb0[k] = qc_vb(e, c0, 4 * c0, Z4);
+        vb1[k] = qc_vb(e, c1, 4 * c1, Z4);
+        old[k] = make_float2(to_f(m0[k]), to_f(m1[k]));
+        // P - old with one rounding, as the scalar kernel's subtraction
+        t[k] = __ffma2_rn(old[k], f2(-1.f), make_float2(at_byte(P, vb0[k]), at_byte(P, vb1[k])));
+    }
+    check_node_update2<D>(t, lim, [&](int k, float2 val) {
+        const MsgT q0 = from_f<MsgT>(val.x), q1 = from_f<MsgT>(val.y);
+        m0[k] = q0;
+        m1[k] = q1;
+        dl[k] = __ffma2_rn(old[k], f2(-1.f), make_float2(to_f(q0), to_f(q1)));
+    });
+}
+
+template <int D, int MAXDC>
+__device__ __forceinline__ void qc2_phase_b(float* __restrict__ P, const int (&vb0)[MAXDC], const int (&vb1)[MAXDC],
+                                            const float2 (&dl)[MAXDC]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        at_byte(P, vb0[k]) += dl[k].x;
+        at_byte(P, vb1[k]) += dl[k].y;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ unsigned qc2_parity(const int2* __restrict__ et, int c0, int c1, int Z4, float* __restrict__ P) {
+    unsigned p0 = 0u, p1 = 0u;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const int2 e = et[k];
+        p0 ^= (at_byte(P, qc_vb(e, c0, 4 * c0, Z4)) < 0.f) ? 1u : 0u;
+        p1 ^= (at_byte(P, qc_vb(e, c1, 4 * c1, Z4)) < 0.f) ? 1u : 0u;
+    }
+    return p0 | p1;
+}
+
+__host__ __device__ constexpr int pair_max_threads(int maxdc) { return maxdc <= 8 ? 512 : 256; }
+
+template <typename MsgT, bool MSG_SMEM, int MAXDC>
+__global__ void __launch_bounds__(pair_max_threads(MAXDC)) qc_pair_kernel(const QcArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_frame;
+    __shared__ unsigned s_err;
+    const RunArgs& r = a.r;
+    const int tid = threadIdx.x;
+    const int Z = a.Z, Zh = a.Z >> 1, W = a.window, nl = a.nl, md = a.maxdeg, Z4 = 4 * a.Z;
+    const QcSmem s = qc_smem_layout<MsgT, MSG_SMEM>(smem, a);
+    float* P = s.P;
+    MsgT* msg = MSG_SMEM ? reinterpret_cast<MsgT*>(s.msg)
+                         : static_cast<MsgT*>(a.ws_msgs) + static_cast<size_t>(blockIdx.x) * a.msg_slots;
+    const int j = tid / Zh;
+    const int c0 = tid - j * Zh, c1 = c0 + Zh;
+    const bool active = j < W;
+    const float lim = r.llr_max;
+    (void)Z;
+    if (tid == 0) s_err = 0u;
+    for (;;) {
+        const long long f = next_frame(r, &s_frame);
+        if (f >= r.n_frames) break;
+        qc_frame_begin(a, s, msg, f);
+        __syncthreads();
+        int it = 1, unsat = 1;
+        for (;; ++it) {
+            for (int g = 0; g < a.G; ++g) {
+                float2 dl[MAXDC];
+                int vb0[MAXDC], vb1[MAXDC];
+                int d = 0;
+                if (active) {
+                    const int l = s.glay[g * W + j];
+                    d = s.ldeg[l];
+                    const int S = s.lstride[l];
+                    const int2* et = s.tab + l * md;
+                    MsgT* m0 = msg + s.loff[l] + c0 * S;
+                    MsgT* m1 = m0 + Zh * S;
+#define NDGSBP_CASE_A2(D) \
+    if (d == D) qc2_phase_a<NDGSBP_DD(D), MAXDC, MsgT>(et, c0, c1, Z4, P, m0, m1, lim, vb0, vb1, dl);
+                    NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_A2)
+#undef NDGSBP_CASE_A2
+                }
+                __syncthreads();
+                for (int jj = 0; jj < W; ++jj) {
+                    if (active && j == jj) {
+#define NDGSBP_CASE_B2(D) \
+    if (d == D) qc2_phase_b<NDGSBP_DD(D), MAXDC>(P, vb0, vb1, dl);
+                        NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_B2)
+#undef NDGSBP_CASE_B2
+                    }
+                    __syncthreads();
+                }
+            }
+            const bool last = it >= r.max_iter;
+            if (r.early_stop || last) {
+                unsigned bad = 0u;
+                if (active) {
+                    for (int l = j; l < nl; l += W) {
+                        const int d = s.ldeg[l];
+                        const int2* et = s.tab + l * md;
+                        unsigned p = 0u;
+#define NDGSBP_CASE_S2(D) \
+    if (d == D) p = qc2_parity<NDGSBP_DD(D)>(et, c0, c1, Z4, P);
+                        NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_S2)
+#undef NDGSBP_CASE_S2
+                        bad |= p;
+                    }
+                }
+                unsat = __syncthreads_or(bad);
+                if (!unsat && r.early_stop) break;
+            }
+            if (last) break;
+        }
+        qc_frame_messages_out(a, msg, f);
+        write_frame_outputs(r, P, f, it, unsat, &s_err);
+        __syncthreads();
+    }
+}
+
+// ---- kernel selection ---------------------------------------------------------------------
 template <typename MsgT, int MAXDC>
-static QcKernelFn pick_qc_storage(bool msg_smem, bool spec) {
+static QcKernelFn pick_qc_storage(bool msg_smem, bool spec, bool pair) {
+    if (pair) return msg_smem ? qc_pair_kernel<MsgT, true, MAXDC> : qc_pair_kernel<MsgT, false, MAXDC>;
     if (spec) return msg_smem ? qc_decode_kernel<MsgT, true, MAXDC, true> : qc_decode_kernel<MsgT, false, MAXDC, true>;
     return msg_smem ? qc_decode_kernel<MsgT, true, MAXDC, false> : qc_decode_kernel<MsgT, false, MAXDC, false>;
 }
 
 template <typename MsgT>
-static QcKernelFn pick_qc_degree(int maxdc, bool msg_smem, bool spec) {
+static QcKernelFn pick_qc_degree(int maxdc, bool msg_smem, bool spec, bool pair) {
     switch (maxdc) {
-        case 8: return pick_qc_storage<MsgT, 8>(msg_smem, spec);
-        case 16: return pick_qc_storage<MsgT, 16>(msg_smem, spec);
-        case 32: return msg_smem ? qc_decode_kernel<MsgT, true, 32, false> : qc_decode_kernel<MsgT, false, 32, false>;
+        case 8: return pick_qc_storage<MsgT, 8>(msg_smem, spec, pair);
+        case 16: return pick_qc_storage<MsgT, 16>(msg_smem, spec, pair);
+        case 32:
+            if (spec || pair) return nullptr;
+            return msg_smem ? qc_decode_kernel<MsgT, true, 32, false> : qc_decode_kernel<MsgT, false, 32, false>;
         default: return nullptr;
     }
 }
@@ -220,11 +434,13 @@ bool qc_degrees_specialised(const QcLayout& Q, int maxdc) {
     return true;
 }
 
-QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec) {
+int qc_pair_max_threads(int maxdc) { return pair_max_threads(maxdc); }
+
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair) {
     switch (msg_dtype) {
-        case NDGSBP_F32: return pick_qc_degree<float>(maxdc, msg_smem, spec);
-        case NDGSBP_F16: return pick_qc_degree<__half>(maxdc, msg_smem, spec);
-        case NDGSBP_BF16: return pick_qc_degree<__nv_bfloat16>(maxdc, msg_smem, spec);
+        case NDGSBP_F32: return pick_qc_degree<float>(maxdc, msg_smem, spec, pair);
+        case NDGSBP_F16: return pick_qc_degree<__half>(maxdc, msg_smem, spec, pair);
+        case NDGSBP_BF16: return pick_qc_degree<__nv_bfloat16>(maxdc, msg_smem, spec, pair);
         default: return nullptr;
     }
 }
@@ -233,7 +449,7 @@ static size_t a16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
 size_t qc_table_bytes(const QcLayout& Q) {
     const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;
-    return a16(static_cast<size_t>(Q.n_layers) * Q.max_deg * 8) + 2 * a16(static_cast<size_t>(Q.n_layers) * 4) +
+    return a16(static_cast<size_t>(Q.n_layers) * Q.max_deg * 8) + 3 * a16(static_cast<size_t>(Q.n_layers) * 4) +
            a16(G * Q.window * 4);
 }
 
@@ -243,8 +459,10 @@ void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs
     a.window = Q.window;
     a.G = static_cast<int>(Q.group_layers.size() / Q.window);
     a.maxdeg = Q.max_deg;
+    a.msg_slots = Q.msg_slots;
     a.edge_tab = reinterpret_cast<const int2*>(D.edge_tab);
     a.layer_deg = D.layer_deg;
+    a.layer_stride = D.layer_stride;
     a.layer_off = D.layer_off;
     a.group_layers = D.group_layers;
     a.csr_of = D.csr_of;

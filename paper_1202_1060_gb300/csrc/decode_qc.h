@@ -8,19 +8,21 @@ namespace ndgsbp {
 
 struct QcArgs {
     RunArgs r;
-    int Z, nl, G, window, maxdeg;
-    const int2* edge_tab;         // [nl][maxdeg]: (b Z + s, Z - s) of edge k of the layer
+    int Z, nl, G, window, maxdeg, msg_slots;
+    const int2* edge_tab;         // [nl][maxdeg]: (4 (b Z + s), Z - s) of edge k of the layer
     const int32_t* layer_deg;     // [nl]
+    const int32_t* layer_stride;  // [nl] messages per CN (odd)
     const int32_t* layer_off;     // [nl] first message of the layer
     const int32_t* group_layers;  // [G][window]
-    const int32_t* csr_of;        // [E] CSR position of each stored message
+    const int32_t* csr_of;        // [msg_slots] CSR position of each stored message, -1 = padding
     void* ws_msgs;                // per-CTA message slots when messages are not in shared memory
 };
 
 typedef void (*QcKernelFn)(const QcArgs);
 
-QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec);
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair);
 bool qc_degrees_specialised(const QcLayout& Q, int maxdc);
+int qc_pair_max_threads(int maxdc);
 size_t qc_table_bytes(const QcLayout& Q);
 void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs);
 

@@ -231,8 +231,8 @@ void compile_qc_layout(const Code& c, const std::vector<int32_t>& gp, const std:
     }
     Q.edge_tab.assign(static_cast<size_t>(nl) * Q.max_deg * 2, 0);
     Q.layer_off.assign(nl, 0);
-    Q.csr_of.assign(c.E, 0);
-    int off = 0;
+    Q.layer_stride.assign(nl, 0);
+    std::vector<std::vector<std::pair<int, int>>> circ(nl);
     for (int l = 0; l < nl; ++l) {
         const int r0 = l * Z, d = Q.layer_deg[l];
         std::vector<std::pair<int, int>> bs;
@@ -252,14 +252,29 @@ void compile_qc_layout(const Code& c, const std::vector<int32_t>& gp, const std:
             for (int k = 0; k < d; ++k)
                 if (c.col_idx[c.row_ptr[row] + k] != want[k]) return;
         }
-        // edges ordered by block column = by VN index within every row, i.e. CSR order
+        circ[l] = bs;
+    }
+    // messages of CN c of layer l at layer_off[l] + c S_l + k with an odd stride S_l >= d_l:
+    // 32 consecutive CNs then touch 32 distinct banks, and k is a compile-time offset
+    int off = 0;
+    for (int l = 0; l < nl; ++l) {
+        const int d = Q.layer_deg[l];
+        Q.layer_stride[l] = d | 1;
         Q.layer_off[l] = off;
+        off += Q.layer_stride[l] * Z;
+    }
+    Q.msg_slots = off;
+    Q.csr_of.assign(off, -1);
+    for (int l = 0; l < nl; ++l) {
+        const int r0 = l * Z, d = Q.layer_deg[l];
+        const auto& bs = circ[l];
+        // edges ordered by block column = by VN index within every row, i.e. CSR order
         for (int k = 0; k < d; ++k) {
-            Q.edge_tab[(static_cast<size_t>(l) * Q.max_deg + k) * 2] = bs[k].first * Z + bs[k].second;
+            Q.edge_tab[(static_cast<size_t>(l) * Q.max_deg + k) * 2] = 4 * (bs[k].first * Z + bs[k].second);
             Q.edge_tab[(static_cast<size_t>(l) * Q.max_deg + k) * 2 + 1] = Z - bs[k].second;
-            for (int cc = 0; cc < Z; ++cc) Q.csr_of[off + k * Z + cc] = c.row_ptr[r0 + cc] + k;
+            for (int cc = 0; cc < Z; ++cc)
+                Q.csr_of[Q.layer_off[l] + cc * Q.layer_stride[l] + k] = c.row_ptr[r0 + cc] + k;
         }
-        off += d * Z;
     }
     // groups as lists of whole layers
     int window = -1;

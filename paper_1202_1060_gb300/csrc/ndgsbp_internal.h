@@ -72,11 +72,13 @@ struct QcLayout {
     int Z = 0, n_layers = 0, nb = 0;
     int window = 0;           // layers per group (all groups the same size)
     int max_deg = 0;
+    int msg_slots = 0;                  // stored messages per frame (with stride padding)
     std::vector<int32_t> layer_deg;     // [n_layers]
+    std::vector<int32_t> layer_stride;  // [n_layers] messages per CN: the degree rounded up to odd
     std::vector<int32_t> layer_off;     // [n_layers] first stored message of the layer
-    std::vector<int32_t> edge_tab;      // [n_layers][max_deg][2]: (b Z + s, Z - s), edges by block column
+    std::vector<int32_t> edge_tab;      // [n_layers][max_deg][2]: (4 (b Z + s), Z - s), edges by block column
     std::vector<int32_t> group_layers;  // [G][window] layer ids in group order
-    std::vector<int32_t> csr_of;        // [E] CSR position of message layer_off[l] + k Z + c
+    std::vector<int32_t> csr_of;        // [msg_slots] CSR position of message layer_off[l] + c S_l + k, -1 = pad
 };
 
 // Device copy of a QcLayout.
@@ -84,6 +86,7 @@ struct DeviceQc {
     void* blob = nullptr;
     const int32_t* edge_tab = nullptr;
     const int32_t* layer_deg = nullptr;
+    const int32_t* layer_stride = nullptr;
     const int32_t* layer_off = nullptr;
     const int32_t* group_layers = nullptr;
     const int32_t* csr_of = nullptr;

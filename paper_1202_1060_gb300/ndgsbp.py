@@ -26,6 +26,7 @@ UNIT_CN, UNIT_LAYER = 0, 1
 GROUPS_CYCLIC, GROUPS_NATURAL = 1, 2
 SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
 VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1, 2, 3, 4
+VARIANT_QC_PAIR, VARIANT_QC_PAIR_GLOBAL = 5, 6
 STAT_FRAMES, STAT_FRAME_ERRORS, STAT_BIT_ERRORS, STAT_UNDETECTED = 0, 1, 2, 3
 STAT_ITERATIONS, STAT_UNSATISFIED, STATS_LEN = 4, 5, 8
 

@@ -238,10 +238,11 @@ def test_variants_and_block_sizes_agree_bitwise(env, name, kind, qc, msg):
     others = [dict(variant=nd.VARIANT_GLOBAL), dict(variant=nd.VARIANT_SMEM, block_threads=64),
               dict(variant=nd.VARIANT_GLOBAL, block_threads=128, ctas_per_sm=1)]
     if qc:
-        others += [dict(variant=nd.VARIANT_QC), dict(variant=nd.VARIANT_QC_GLOBAL)]
+        others += [dict(variant=nd.VARIANT_QC), dict(variant=nd.VARIANT_QC_GLOBAL),
+                   dict(variant=nd.VARIANT_QC_PAIR), dict(variant=nd.VARIANT_QC_PAIR_GLOBAL)]
     for kw in others:
         other = _run(nd, torch, g, c, llr, **kw0, **kw)
-        if kw["variant"] in (nd.VARIANT_QC, nd.VARIANT_QC_GLOBAL):
+        if kw["variant"] >= nd.VARIANT_QC:
             assert other["plan"]["variant"] == kw["variant"]
         assert (other["post"] == base["post"]).all(), kw
         assert (other["iters"] == base["iters"]).all()
