@@ -67,6 +67,7 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_VARIANT_QC_GLOBAL 4 /* layered QC kernel with messages in global-memory slots */
 #define NDGSBP_VARIANT_QC_PAIR 5   /* layered QC kernel, two CNs per thread, packed FP32 arithmetic */
 #define NDGSBP_VARIANT_QC_PAIR_GLOBAL 6 /* the pair kernel with messages in global-memory slots */
+#define NDGSBP_VARIANT_TILE 7      /* tile kernel: any QC window, degree <= 32, several frames per CTA */
 
 /* stats counters accumulated by ndgsbp_decode_ex (uint64 each) */
 #define NDGSBP_STAT_FRAMES 0
@@ -90,6 +91,8 @@ typedef struct ndgsbp_params {
     int32_t variant;        /* NDGSBP_VARIANT_* */
     int32_t block_threads;  /* 0 = chosen by the library; else a multiple of 32, <= 1024 */
     int32_t ctas_per_sm;    /* 0 = as many as fit; else an upper bound */
+    int32_t frames_per_cta; /* TILE variant: frame slots per CTA, 0 = library choice, <= 16 */
+    int32_t lanes_per_cn;   /* TILE variant: threads per CN (1, 2 or 4), 0 = library choice */
 } ndgsbp_params;
 
 /* Launch plan the library picked for a decode (filled by ndgsbp_decode_plan). */
@@ -232,6 +235,94 @@ ndgsbp_status ndgsbp_decode_ex(const ndgsbp_groups* groups, const ndgsbp_params*
                                void* d_workspace, size_t workspace_bytes, uint32_t* d_hard_bits,
                                int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
                                const ndgsbp_extras* extras, void* stream);
+
+/* ---- Ragged batches: several codes in one persistent launch --------------------------------
+ * One code's part of a ragged batch: its grouping (a QC code grouped in whole layers), its
+ * channel LLRs [n_frames][N] and its outputs, laid out as for ndgsbp_decode.  d_stats,
+ * d_start_ns and d_retire_ns are optional (see ndgsbp_extras). */
+typedef struct ndgsbp_batch {
+    const ndgsbp_groups* groups;
+    const void* d_llr;
+    int32_t llr_dtype;
+    int64_t n_frames;
+    uint32_t* d_hard_bits;
+    int32_t* d_iters;
+    uint8_t* d_syndrome_ok;
+    float* d_posterior;
+    uint64_t* d_stats;
+    uint64_t* d_start_ns;
+    uint64_t* d_retire_ns;
+    int32_t frames_per_cta;  /* 0 = library choice */
+    int32_t lanes_per_cn;    /* 0 = library choice */
+} ndgsbp_batch;
+
+typedef struct ndgsbp_ragged ndgsbp_ragged;
+
+/* Plan one persistent tile-kernel launch over n_batches <= 8 batches of different codes: each
+ * code keeps its own schedule (Sec. II-C Steps 2-4 with its groups) and per-frame early stop;
+ * CTAs take tiles of frames of any code from one list (largest codes first) and refill frame
+ * slots as frames retire.  params gives max_iter, msg_dtype, llr_max, early_stop and
+ * block_threads (shared by every code).  The batches' buffers are recorded in the handle: later
+ * launches reuse them, so refill their contents rather than moving them.  Allocates the tile
+ * list and the launch's workspace (owned by the handle; call before any stream capture).
+ * Errors: INVALID, UNSUPPORTED (a code that is not QC in whole layers, degree > 32), CUDA, NOMEM. */
+ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batches,
+                                   const ndgsbp_params* params, ndgsbp_ragged** out);
+/* Launch plan (variant TILE; grid, block, shared bytes) and number of tiles. */
+ndgsbp_status ndgsbp_ragged_info(const ndgsbp_ragged* ragged, ndgsbp_plan* plan, int32_t* n_tiles);
+/* Enqueue the launch on stream: a counter reset and one kernel. */
+ndgsbp_status ndgsbp_ragged_launch(ndgsbp_ragged* ragged, void* stream);
+/* The same launch through a CUDA graph: the first call on a stream captures the reset and the
+ * kernel into a graph and instantiates it, later calls replay it (one cudaGraphLaunch). */
+ndgsbp_status ndgsbp_ragged_graph_launch(ndgsbp_ragged* ragged, void* stream);
+ndgsbp_status ndgsbp_ragged_destroy(ndgsbp_ragged* ragged);
+
+/* ---- Serving: continuous batching of decode requests ---------------------------------------
+ * A server owns, per code, a pool of frame slots in device memory (channel LLRs, posterior,
+ * messages, outputs) sized so that all pools fit hbm_budget_bytes (split in proportion to
+ * weights; NULL = equal shares).  A host thread of the library admits the frames of queued
+ * requests into free slots in arrival order, runs epoch launches of the tile kernel in which
+ * every running frame advances by at most epoch_iters iterations (its state stays in device
+ * memory between epochs), and retires frames whose syndrome is zero (Step 4 b) or that reached
+ * params->max_iter, freeing their slots for the next frames at once.  A request completes when
+ * all its frames have retired.  Every frame is decoded exactly as by ndgsbp_decode with the
+ * TILE variant, whatever else is in flight.
+ * Errors: INVALID, BUDGET (a pool would get no slot), UNSUPPORTED (a code the tile kernel does
+ * not take), CUDA, NOMEM. */
+typedef struct ndgsbp_server ndgsbp_server;
+
+typedef struct ndgsbp_server_stats {
+    int64_t requests_submitted, requests_completed;
+    int64_t frames_completed, frame_errors_unsatisfied;
+    int64_t epochs;
+    int64_t iterations;          /* frame-iterations run */
+    double busy_seconds;         /* host time with at least one frame on the device */
+    int64_t slots_total, slots_in_use;
+} ndgsbp_server_stats;
+
+ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_codes,
+                                   const double* weights, const ndgsbp_params* params,
+                                   size_t hbm_budget_bytes, int32_t epoch_iters,
+                                   ndgsbp_server** out);
+/* Queue a request of n_frames frames of code `code` (index into the create-time list):
+ * host_llr [n_frames][N] FP32 is read during admission and must stay valid until the request
+ * completes; the outputs (laid out as for ndgsbp_decode, host memory, host_iters and
+ * host_syndrome_ok may be NULL) are written before completion is reported.  *ticket identifies
+ * the request.  Thread-safe. */
+ndgsbp_status ndgsbp_server_submit(ndgsbp_server* server, int32_t code, const float* host_llr,
+                                   int64_t n_frames, uint32_t* host_hard_bits, int32_t* host_iters,
+                                   uint8_t* host_syndrome_ok, int64_t* ticket);
+/* *done = 1 once the request completed; *latency_ms = completion - submission (host clock).
+ * Completion is reported once: after poll reported done (or wait returned OK) the ticket is
+ * released and later calls with it return INVALID. */
+ndgsbp_status ndgsbp_server_poll(ndgsbp_server* server, int64_t ticket, int32_t* done,
+                                 double* latency_ms);
+/* Block until the request completes or timeout_ms passes (TIMEOUT). */
+ndgsbp_status ndgsbp_server_wait(ndgsbp_server* server, int64_t ticket, int32_t timeout_ms,
+                                 double* latency_ms);
+ndgsbp_status ndgsbp_server_stats_get(ndgsbp_server* server, ndgsbp_server_stats* stats);
+/* Stops the worker (finishing the epoch in flight) and frees the pools. */
+ndgsbp_status ndgsbp_server_destroy(ndgsbp_server* server);
 
 /* ---- Decoding without allocating (the paper has no counterpart) ---------------------------
  * ndgsbp_decode_static is ndgsbp_decode without a workspace: it allocates no device memory.  It

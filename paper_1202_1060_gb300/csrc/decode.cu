@@ -21,6 +21,7 @@
 #include <cstring>
 
 #include "decode_qc.h"
+#include "decode_tile.h"
 #include "device_common.cuh"
 #include "ndgsbp_internal.h"
 
@@ -306,6 +307,10 @@ static ndgsbp_status device_qc(const Groups& g, bool flood, const QcLayout*& Q, 
     return NDGSBP_OK;
 }
 
+ndgsbp_status device_qc_tables(const Groups& g, const QcLayout*& Q, const DeviceQc*& D) {
+    return device_qc(g, false, Q, D);
+}
+
 void release_device_layouts(Groups& g) {
     int cur = 0;
     if (cudaGetDevice(&cur) != cudaSuccess) return;
@@ -329,8 +334,12 @@ Groups::~Groups() { release_device_layouts(*this); }
 struct Plan {
     ndgsbp_plan pub;
     bool qc = false;
+    bool tile = false;
     KernelFn fn = nullptr;
     QcKernelFn qfn = nullptr;
+    TileKernelFn tfn = nullptr;
+    int tile_tpc = 1, tile_le = 1, tile_slots = 1, tile_slot_bytes = 0, tile_p_bytes = 0, tile_m_bytes = 0;
+    int tile_delta_stride = 1, tile_frames = 1, tile_table_bytes = 0, n_tiles = 0;
     bool msg_smem = false, delta_smem = false;
     const Layout* L = nullptr;
     const DeviceLayout* D = nullptr;
@@ -349,7 +358,11 @@ static ndgsbp_status validate_params(const ndgsbp_params* p) {
     if (p->block_threads < 0 || p->block_threads > 1024 || p->block_threads % 32)
         return fail(NDGSBP_ERR_INVALID, "block_threads must be 0 or a multiple of 32 up to 1024");
     if (p->ctas_per_sm < 0) return fail(NDGSBP_ERR_INVALID, "ctas_per_sm must be >= 0");
-    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_PAIR_GLOBAL)
+    if (p->frames_per_cta < 0 || p->frames_per_cta > 16)
+        return fail(NDGSBP_ERR_INVALID, "frames_per_cta must be in [0, 16]");
+    if (p->lanes_per_cn != 0 && p->lanes_per_cn != 1 && p->lanes_per_cn != 2 && p->lanes_per_cn != 4)
+        return fail(NDGSBP_ERR_INVALID, "lanes_per_cn must be 0, 1, 2 or 4");
+    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_TILE)
         return fail(NDGSBP_ERR_INVALID, "unknown variant %d", p->variant);
     return NDGSBP_OK;
 }
@@ -439,6 +452,72 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     return NDGSBP_OK;
 }
 
+// Tile kernel plan: any QC grouping in whole layers, row degree <= 32.
+static ndgsbp_status make_tile_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
+                                    const DeviceInfo& di, Plan& plan, bool* ok, bool allow_upload = true) {
+    *ok = false;
+    const QcLayout& Q = flood ? flood_qc_layout(g) : g.qc;
+    if (!Q.ok) return NDGSBP_OK;
+    const int tpc = p->lanes_per_cn ? p->lanes_per_cn : tile_lanes_per_cn(Q.max_deg);
+    if (!tpc) return NDGSBP_OK;
+    const int le = (Q.max_deg + tpc - 1) / tpc;
+    if (le > 8) return fail(NDGSBP_ERR_UNSUPPORTED, "lanes_per_cn %d leaves %d edges per lane (at most 8)", tpc, le);
+    const int ds = Q.max_deg | 1;
+    const int per_slot = Q.window * Q.Z * tpc;
+    int threads = p->block_threads ? p->block_threads : std::min(512, std::max(128, (per_slot + 31) / 32 * 32));
+    const size_t budget = static_cast<size_t>(di.smem_optin) - 256;
+    const size_t table = tile_table_bytes(Q);
+    const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 4);
+    const size_t m_bytes = align16(static_cast<size_t>(Q.msg_slots) * msg_size(p->msg_dtype));
+    const size_t d_bytes = align16(static_cast<size_t>(Q.window) * Q.Z * ds * 4);
+    const bool msg_smem = p->variant != NDGSBP_VARIANT_GLOBAL && table + p_bytes + m_bytes + d_bytes <= budget;
+    const size_t slot_bytes = p_bytes + (msg_smem ? m_bytes : 0) + d_bytes;
+    if (table + slot_bytes > budget) return NDGSBP_OK;
+    const int max_slots = static_cast<int>(std::min<size_t>(16, (budget - table) / slot_bytes));
+    int slots = p->frames_per_cta ? p->frames_per_cta : std::max(1, std::min(16, threads / per_slot));
+    slots = std::min(slots, max_slots);
+    const size_t smem = table + static_cast<size_t>(slots) * slot_bytes;
+    TileKernelFn fn = pick_tile_kernel(p->msg_dtype);
+    if (!fn) return NDGSBP_OK;
+    int per_sm = 0;
+    int64_t grid = 0;
+    ndgsbp_status st = finish_grid(reinterpret_cast<const void*>(fn), threads, smem, p, n_frames, di, per_sm, grid);
+    if (st) return st;
+    const int tile_frames = slots * 4;
+    const int64_t n_tiles = std::max<int64_t>(1, (n_frames + tile_frames - 1) / tile_frames);
+    grid = std::min<int64_t>(grid, n_tiles);
+    st = device_qc(g, flood, plan.Q, plan.DQ, allow_upload);
+    if (st) return st;
+    plan.tile = true;
+    plan.tfn = fn;
+    plan.msg_smem = msg_smem;
+    plan.tile_tpc = tpc;
+    plan.tile_le = le;
+    plan.tile_slots = slots;
+    plan.tile_slot_bytes = static_cast<int>(slot_bytes);
+    plan.tile_p_bytes = static_cast<int>(p_bytes);
+    plan.tile_m_bytes = msg_smem ? static_cast<int>(m_bytes) : 0;
+    plan.tile_delta_stride = ds;
+    plan.tile_frames = tile_frames;
+    plan.tile_table_bytes = static_cast<int>(table);
+    plan.n_tiles = static_cast<int>(n_tiles);
+    ndgsbp_plan& o = plan.pub;
+    o.variant = NDGSBP_VARIANT_TILE;
+    o.block_threads = threads;
+    o.grid = static_cast<int32_t>(grid);
+    o.ctas_per_sm = per_sm;
+    o.max_row_degree = Q.max_deg;
+    o.delta_in_smem = 1;
+    o.smem_bytes = static_cast<int64_t>(smem);
+    o.workspace_bytes = static_cast<int64_t>(
+        kHeaderBytes +
+        (msg_smem ? 0 : align256(static_cast<size_t>(grid) * slots * Q.msg_slots * msg_size(p->msg_dtype))));
+    o.stored_edges = Q.msg_slots;
+    o.edge_updates_per_iter = flood ? g.code->E : g.edge_updates;
+    *ok = true;
+    return NDGSBP_OK;
+}
+
 static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, Plan& plan,
                                bool allow_upload = true) {
     ndgsbp_status st = validate_params(p);
@@ -447,6 +526,13 @@ static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t 
     DeviceInfo di;
     st = device_info(di);
     if (st) return st;
+    if (p->variant == NDGSBP_VARIANT_TILE) {
+        bool ok = false;
+        st = make_tile_plan(g, p, n_frames, flood, di, plan, &ok, allow_upload);
+        if (st) return st;
+        if (ok) return NDGSBP_OK;
+        return fail(NDGSBP_ERR_UNSUPPORTED, "TILE variant needs a QC code grouped in whole layers, row degree <= 32");
+    }
     const bool want_qc = p->variant >= NDGSBP_VARIANT_QC;
     if (p->variant == NDGSBP_VARIANT_AUTO || want_qc) {
         bool ok = false;
@@ -456,6 +542,10 @@ static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t 
         if (want_qc)
             return fail(NDGSBP_ERR_UNSUPPORTED, "QC variant needs a QC code grouped in whole layers with a window "
                                                 "that fits one CTA");
+        // QC code whose window does not fit one CTA with one CN per thread: tile kernel
+        st = make_tile_plan(g, p, n_frames, flood, di, plan, &ok, allow_upload);
+        if (st) return st;
+        if (ok) return NDGSBP_OK;
     }
     st = device_layout(g, flood, plan.L, plan.D, allow_upload);
     if (st) return st;
@@ -566,16 +656,53 @@ static ndgsbp_status static_scratch_address(void** out) {
     return NDGSBP_OK;
 }
 
-// Launch a plan with `ws` as its scratch (counter already cleared on the stream).
-static ndgsbp_status launch_with_scratch(const Groups& g, const Plan& plan, const ndgsbp_params* params,
-                                         const void* d_llr, int32_t llr_dtype, int64_t n_frames,
-                                         unsigned char* ws, uint32_t* d_hard_bits, int32_t* d_iters,
-                                         uint8_t* d_syndrome_ok, float* d_posterior, cudaStream_t s) {
-    if (plan.qc) {
+// Launch a plan with `ws` as its scratch (its counter already cleared on the stream).
+static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp_params* params, const void* d_llr,
+                                 int32_t llr_dtype, int64_t n_frames, unsigned char* ws, uint32_t* d_hard_bits,
+                                 int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
+                                 const ndgsbp_extras* extras, cudaStream_t s) {
+    if (plan.tile) {
+        TileArgs a;
+        std::memset(&a, 0, sizeof(a));
+        TileCode& C = a.codes[0];
+        fill_run(C.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior,
+                 extras);
+        const QcLayout& Q = *plan.Q;
+        const DeviceQc& D = *plan.DQ;
+        C.N = g.code->N;
+        C.E = static_cast<int>(g.code->E);
+        C.Z = Q.Z;
+        C.nl = Q.n_layers;
+        C.G = static_cast<int>(Q.group_layers.size() / Q.window);
+        C.window = Q.window;
+        C.maxdeg = Q.max_deg;
+        C.msg_slots = Q.msg_slots;
+        C.tpc = plan.tile_tpc;
+        C.le = plan.tile_le;
+        C.slots = plan.tile_slots;
+        C.slot_bytes = plan.tile_slot_bytes;
+        C.p_bytes = plan.tile_p_bytes;
+        C.m_bytes = plan.tile_m_bytes;
+        C.delta_stride = plan.tile_delta_stride;
+        C.edge_tab = reinterpret_cast<const int2*>(D.edge_tab);
+        C.layer_deg = D.layer_deg;
+        C.layer_stride = D.layer_stride;
+        C.layer_off = D.layer_off;
+        C.group_layers = D.group_layers;
+        C.csr_of = D.csr_of;
+        C.ws_msgs = plan.msg_smem ? nullptr : ws + kHeaderBytes;
+        a.n_codes = 1;
+        a.tiles = nullptr;
+        a.n_tiles = plan.n_tiles;
+        a.tile_frames = plan.tile_frames;
+        a.tile_counter = reinterpret_cast<unsigned long long*>(ws);
+        a.table_bytes = plan.tile_table_bytes;
+        plan.tfn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
+    } else if (plan.qc) {
         QcArgs a;
         std::memset(&a, 0, sizeof(a));
         fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior,
-                 nullptr);
+                 extras);
         fill_qc_args(a, *plan.Q, *plan.DQ, plan.msg_smem ? nullptr : ws + kHeaderBytes);
         plan.qfn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
     } else {
@@ -584,7 +711,7 @@ static ndgsbp_status launch_with_scratch(const Groups& g, const Plan& plan, cons
         DecodeArgs a;
         std::memset(&a, 0, sizeof(a));
         fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior,
-                 nullptr);
+                 extras);
         a.M = L.M;
         a.Epad = L.Epad;
         a.G = L.G;
@@ -663,42 +790,8 @@ ndgsbp_status ndgsbp_decode_ex(const ndgsbp_groups* groups, const ndgsbp_params*
     auto* ws = static_cast<unsigned char*>(d_workspace);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), s));
-    if (plan.qc) {
-        QcArgs a;
-        std::memset(&a, 0, sizeof(a));
-        fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior, extras);
-        fill_qc_args(a, *plan.Q, *plan.DQ, plan.msg_smem ? nullptr : ws + kHeaderBytes);
-        plan.qfn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
-    } else {
-        const Layout& L = *plan.L;
-        const DeviceLayout& D = *plan.D;
-        DecodeArgs a;
-        std::memset(&a, 0, sizeof(a));
-        fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior, extras);
-        a.M = L.M;
-        a.Epad = L.Epad;
-        a.G = L.G;
-        a.max_gd = L.max_gd;
-        a.slot_deg = D.slot_deg;
-        a.tile_base = D.tile_base;
-        a.edge_vn = D.edge_vn;
-        a.edge_csr = D.edge_csr;
-        a.grp_ptr = D.grp_ptr;
-        a.ge_slot = D.ge_slot;
-        a.ge_dpos = D.ge_dpos;
-        a.grp_colbase = D.grp_colbase;
-        a.grp_ncol = D.grp_ncol;
-        a.gcol = D.gcol;
-        size_t off = kHeaderBytes;
-        if (!plan.msg_smem) {
-            a.ws_msgs = ws + off;
-            off += align256(static_cast<size_t>(plan.pub.grid) * L.Epad * msg_size(params->msg_dtype));
-        }
-        if (!plan.delta_smem) a.ws_delta = reinterpret_cast<float*>(ws + off);
-        plan.fn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
-    }
-    CUDA_TRY(cudaGetLastError());
-    return NDGSBP_OK;
+    return launch_plan(g, plan, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok,
+                       d_posterior, extras, s);
 }
 
 ndgsbp_status ndgsbp_decode(const ndgsbp_groups* groups, const ndgsbp_params* params,
@@ -737,8 +830,8 @@ ndgsbp_status ndgsbp_decode_static(const ndgsbp_groups* groups, const ndgsbp_par
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the frame counter must start at zero; message and delta slots are written before read
     CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), s));
-    return launch_with_scratch(g, plan, params, d_llr, llr_dtype, n_frames, static_cast<unsigned char*>(ws),
-                               d_hard_bits, d_iters, d_syndrome_ok, d_posterior, s);
+    return launch_plan(g, plan, params, d_llr, llr_dtype, n_frames, static_cast<unsigned char*>(ws), d_hard_bits,
+                       d_iters, d_syndrome_ok, d_posterior, nullptr, s);
 }
 
 }  // extern "C"

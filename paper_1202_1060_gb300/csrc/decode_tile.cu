@@ -1,0 +1,409 @@
+// Tile decode kernel for sm_103a: layered QC codes of any window size and row degree up to 32,
+// several frames per CTA, and any mix of codes in one launch.
+//
+// Work comes in tiles (code, first frame, frame count) handed out by an atomic counter; a CTA
+// decodes a tile's frames in `slots` frame slots at once and refills a slot from the tile as
+// soon as its frame retires (Step 4 b), so early-stopping frames free their slot immediately.
+// All slots of a CTA step through the same group schedule.
+//
+// A CN of degree d is spread over tpc lanes (consecutive threads of one warp), lane p holding
+// edges [p le, min(d, (p+1) le)) with le <= 8.  Each lane forms the tanh product of its own edges
+// in the positive-pair form (N, E) of Eq. (1) (see check_node_update), the lanes exchange their
+// totals with two shuffles, and every lane seeds its suffix pass with the product of the other
+// lanes' totals, so the exclusion "all edges but k" costs nothing extra per edge.  With tpc = 1
+// the operations are those of the other kernels, in the same order.
+//
+// A group's CNs are processed in rounds over the block; the message changes go to a per-slot
+// delta buffer in shared memory, and phase B adds them to the posterior layer position by
+// layer position (the fixed order of the other kernels).  Posteriors, messages (when they fit)
+// and deltas of every slot live in shared memory, after the code's tables.
+#include <cstring>
+
+#include "decode_tile.h"
+
+namespace ndgsbp {
+
+constexpr int kLane = 8;        // largest number of edges a lane holds
+constexpr int kMaxSlots = 16;   // largest number of frame slots per CTA
+
+__device__ __forceinline__ int tile_vb(int2 e, int c, int Z4) { return e.x + 4 * c - (c >= e.y ? Z4 : 0); }
+
+__device__ __forceinline__ float& at_b(float* P, int vb) {
+    return *reinterpret_cast<float*>(reinterpret_cast<char*>(P) + vb);
+}
+
+// Forward pass over the lane's L edges: prefix pairs, lane total (cn, ce), sign bits.
+template <int L>
+__device__ __forceinline__ void lane_forward(const float (&t)[kLane], float lim, float (&xu)[kLane], float (&pn)[kLane],
+                                             float (&pe)[kLane], float& cn, float& ce, unsigned& sbits) {
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        sbits |= (__float_as_uint(t[k]) >> 31) << k;
+        const float x = fminf(fabsf(t[k]), lim);
+        const float u = ex2_approx(x * -1.4426950408889634f);
+        const float n = fmaf(-0.5f, u, 0.5f);
+        xu[k] = u;
+        pn[k] = cn;
+        pe[k] = ce;
+        ce = fmaf(ce, n + u, cn * u);
+        cn = cn * n;
+    }
+}
+
+// Backward pass: the suffix starts from (sn, se), the product over the other lanes' edges.
+template <int L, typename Emit>
+__device__ __forceinline__ void lane_backward(const float (&xu)[kLane], const float (&pn)[kLane], const float (&pe)[kLane],
+                                              float sn, float se, unsigned sbits, unsigned par, float lim, Emit emit) {
+#pragma unroll
+    for (int k = L - 1; k >= 0; --k) {
+        const float u = xu[k];
+        const float n = fmaf(-0.5f, u, 0.5f);
+        const float en = pn[k] * sn;
+        const float ee = fmaf(pe[k], sn + se, pn[k] * se);
+        const float w = fmaf(en * rcp_approx(ee), 2.f, 1.f);
+        const float mag = fminf(0.69314718055994531f * lg2_approx(w), lim);
+        const unsigned sgn = ((par ^ (sbits >> k)) & 1u) << 31;
+        emit(k, __uint_as_float(__float_as_uint(mag) | sgn));
+        se = fmaf(se, n + u, sn * u);
+        sn = sn * n;
+    }
+}
+
+#define NDGSBP_LANE_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
+
+// Shared state of a CTA (static part).
+struct TileShared {
+    long long frame[kMaxSlots];
+    int iter[kMaxSlots];
+    int epoch[kMaxSlots];
+    unsigned unsat[kMaxSlots];
+    unsigned err;
+    int tile, code, cur_code, next, end, active;
+};
+
+template <typename MsgT, bool SERVE>
+__device__ __forceinline__ MsgT* slot_msgs(const TileCode& C, unsigned char* slot_base, int s, long long f) {
+    if (C.m_bytes) return reinterpret_cast<MsgT*>(slot_base + C.p_bytes);
+    if (SERVE) return static_cast<MsgT*>(C.state_msgs) + static_cast<size_t>(f) * C.msg_slots;
+    return static_cast<MsgT*>(C.ws_msgs) + (static_cast<size_t>(blockIdx.x) * C.slots + s) * C.msg_slots;
+}
+
+// Next frame of the tile for a slot (tid 0 only); in serving mode only pool slots that hold a
+// new or running frame are taken.
+template <bool SERVE>
+__device__ __forceinline__ long long claim_frame(TileShared& sh, const TileCode& C) {
+    if (SERVE) {
+        while (sh.next < sh.end) {
+            const int fl = C.state_flag[sh.next];
+            if (fl == kSlotNew || fl == kSlotRunning) return sh.next++;
+            ++sh.next;
+        }
+        return -1;
+    }
+    return sh.next < sh.end ? sh.next++ : -1;
+}
+
+// Load frame f into slot s (all threads): a fresh frame starts from P = L, messages 0; in
+// serving mode a running frame resumes from its saved state.
+template <typename MsgT, bool SERVE>
+__device__ __forceinline__ void load_frame(const TileCode& C, unsigned char* base, int s, long long f, int saved_iter) {
+    const RunArgs& r = C.r;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float* P = reinterpret_cast<float*>(base);
+    MsgT* msg = slot_msgs<MsgT, SERVE>(C, base, s, f);
+    if (SERVE && saved_iter > 0) {
+        const float* sp = C.state_P + static_cast<size_t>(f) * r.N;
+        for (int n = tid; n < r.N; n += nt) P[n] = sp[n];
+        if (C.m_bytes) {
+            const MsgT* sm = static_cast<const MsgT*>(C.state_msgs) + static_cast<size_t>(f) * C.msg_slots;
+            for (int e = tid; e < C.msg_slots; e += nt) msg[e] = sm[e];
+        }
+        return;
+    }
+    if (r.start_ns && tid == 0) r.start_ns[f] = global_timer_ns();
+    for (int n = tid; n < r.N; n += nt) P[n] = load_llr(r.llr, r.llr_dtype, f * r.N + n);
+    for (int e = tid; e < C.msg_slots; e += nt) msg[e] = from_f<MsgT>(0.f);
+}
+
+// Serving mode: save a running frame's state at the end of its share of the launch.
+template <typename MsgT>
+__device__ __forceinline__ void save_frame(const TileCode& C, unsigned char* base, long long f) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float* P = reinterpret_cast<const float*>(base);
+    float* sp = C.state_P + static_cast<size_t>(f) * C.N;
+    for (int n = tid; n < C.N; n += nt) sp[n] = P[n];
+    if (C.m_bytes) {
+        const MsgT* msg = reinterpret_cast<const MsgT*>(base + C.p_bytes);
+        MsgT* sm = static_cast<MsgT*>(C.state_msgs) + static_cast<size_t>(f) * C.msg_slots;
+        for (int e = tid; e < C.msg_slots; e += nt) sm[e] = msg[e];
+    }
+}
+
+template <typename MsgT, bool SERVE>
+__global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ TileShared sh;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // tables of the current code at the start of shared memory, frame slots after them
+    int2* tab = reinterpret_cast<int2*>(smem);
+    unsigned char* slots_base = smem + a.table_bytes;
+    if (tid == 0) {
+        sh.cur_code = -1;
+        sh.err = 0u;
+    }
+    for (;;) {
+        if (tid == 0) sh.tile = static_cast<int>(atomicAdd(a.tile_counter, 1ull));
+        __syncthreads();
+        const int ti = sh.tile;
+        if (ti >= a.n_tiles) break;
+        int4 tile;
+        if (a.tiles) {
+            tile = a.tiles[ti];
+        } else {
+            const long long first = static_cast<long long>(ti) * a.tile_frames;
+            tile = make_int4(0, static_cast<int>(first),
+                             static_cast<int>(min(static_cast<long long>(a.tile_frames), a.codes[0].r.n_frames - first)), 0);
+        }
+        const TileCode& C = a.codes[tile.x];
+        const RunArgs& r = C.r;
+        const int Z = C.Z, Z4 = 4 * C.Z, W = C.window, nl = C.nl, md = C.maxdeg, tpc = C.tpc, le = C.le;
+        const int tsh = tpc == 1 ? 0 : (tpc == 2 ? 1 : 2);
+        // code tables: (4 (b Z + s), Z - s) per edge, degrees, strides, offsets, group layers
+        int* ldeg = reinterpret_cast<int*>(tab + nl * md);
+        int* lstride = ldeg + nl;
+        int* loff = lstride + nl;
+        int* glay = loff + nl;
+        if (sh.cur_code != tile.x) {
+            for (int i = tid; i < nl * md; i += nt) tab[i] = C.edge_tab[i];
+            for (int i = tid; i < nl; i += nt) {
+                ldeg[i] = C.layer_deg[i];
+                lstride[i] = C.layer_stride[i];
+                loff[i] = C.layer_off[i];
+            }
+            for (int i = tid; i < C.G * W; i += nt) glay[i] = C.group_layers[i];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            sh.cur_code = tile.x;
+            sh.next = tile.y;
+            sh.end = tile.y + tile.z;
+            for (int s = 0; s < C.slots; ++s) {
+                const long long f = claim_frame<SERVE>(sh, C);
+                sh.frame[s] = f;
+                sh.iter[s] = (SERVE && f >= 0) ? (C.state_flag[f] == kSlotNew ? 0 : C.state_iter[f]) : 0;
+                sh.epoch[s] = 0;
+                if (SERVE && f >= 0) C.state_flag[f] = kSlotRunning;
+            }
+        }
+        __syncthreads();
+        // initialisation of every filled slot: P_n = L_n, L_{m->n} = 0 (or the saved state)
+        for (int s = 0; s < C.slots; ++s) {
+            const long long f = sh.frame[s];
+            if (f < 0) continue;
+            load_frame<MsgT, SERVE>(C, slots_base + static_cast<size_t>(s) * C.slot_bytes, s, f, sh.iter[s]);
+        }
+        __syncthreads();
+        const int per_slot = W * Z * tpc;           // CN-lanes of one group in one slot
+        const int work = C.slots * per_slot;
+        const int rounds = (work + nt - 1) / nt;
+        const float lim = r.llr_max;
+        const unsigned gmask = tpc == 1 ? 0u : ((1u << tpc) - 1u) << ((tid & 31) & ~(tpc - 1));
+        for (;;) {
+            for (int g = 0; g < C.G; ++g) {
+                // ---- phase A: Eq. (1) on every CN of the group in every filled slot ----------
+                for (int rr = 0; rr < rounds; ++rr) {
+                    const int i = rr * nt + tid;
+                    const int s = i / per_slot;
+                    const bool live = i < work && sh.frame[s] >= 0;
+                    const int w = i - s * per_slot;
+                    const int cnl = w >> tsh, p = w & (tpc - 1);
+                    const int j = cnl / Z, c = cnl - j * Z;
+                    int L = 0;
+                    float t[kLane], old[kLane], xu[kLane], pn[kLane], pe[kLane];
+                    float cn = 1.f, ce = 0.f;
+                    unsigned sbits = 0u;
+                    float* P = nullptr;
+                    MsgT* m = nullptr;
+                    float* dl = nullptr;
+                    int k0 = 0;
+                    if (live) {
+                        unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
+                        P = reinterpret_cast<float*>(base);
+                        const int l = glay[g * W + j];
+                        const int d = ldeg[l];
+                        k0 = p * le;
+                        L = min(max(d - k0, 0), le);
+                        m = slot_msgs<MsgT, SERVE>(C, base, s, sh.frame[s]) + loff[l] + c * lstride[l] + k0;
+                        dl = reinterpret_cast<float*>(base + C.p_bytes + C.m_bytes) + cnl * C.delta_stride + k0;
+                        const int2* et = tab + l * md + k0;
+#pragma unroll
+                        for (int k = 0; k < kLane; ++k) {
+                            if (k < L) {
+                                old[k] = to_f(m[k]);
+                                t[k] = at_b(P, tile_vb(et[k], c, Z4)) - old[k];
+                            }
+                        }
+                        switch (L) {
+#define NDGSBP_FWD(LL) \
+    case LL: lane_forward<LL>(t, lim, xu, pn, pe, cn, ce, sbits); break;
+                            NDGSBP_LANE_CASES(NDGSBP_FWD)
+#undef NDGSBP_FWD
+                            default: break;
+                        }
+                    }
+                    // product over the other lanes of the CN, and the total sign parity
+                    float on = 1.f, oe = 0.f;
+                    unsigned par = __popc(sbits) & 1u;
+                    if (tpc > 1) {
+                        const float xn = __shfl_xor_sync(gmask, cn, 1), xe = __shfl_xor_sync(gmask, ce, 1);
+                        par ^= __shfl_xor_sync(gmask, par, 1);
+                        if (tpc == 2) {
+                            on = xn;
+                            oe = xe;
+                        } else {
+                            const float pn2 = cn * xn, pe2 = fmaf(ce, xn + xe, cn * xe);   // this pair's total
+                            const float yn = __shfl_xor_sync(gmask, pn2, 2), ye = __shfl_xor_sync(gmask, pe2, 2);
+                            par ^= __shfl_xor_sync(gmask, par, 2);
+                            on = xn * yn;
+                            oe = fmaf(xe, yn + ye, xn * ye);
+                        }
+                    }
+                    if (live) {
+                        auto emit = [&](int k, float val) {
+                            const MsgT q = from_f<MsgT>(val);
+                            m[k] = q;
+                            dl[k] = to_f(q) - old[k];
+                        };
+                        switch (L) {
+#define NDGSBP_BWD(LL) \
+    case LL: lane_backward<LL>(xu, pn, pe, on, oe, sbits, par, lim, emit); break;
+                            NDGSBP_LANE_CASES(NDGSBP_BWD)
+#undef NDGSBP_BWD
+                            default: break;
+                        }
+                    }
+                }
+                __syncthreads();
+                // ---- phase B: posterior += changes, layer position by layer position -----------
+                const int per_pos = Z * tpc;
+                const int pwork = C.slots * per_pos;
+                for (int jj = 0; jj < W; ++jj) {
+                    for (int i = tid; i < pwork; i += nt) {
+                        const int s = i / per_pos;
+                        if (sh.frame[s] < 0) continue;
+                        const int w = i - s * per_pos;
+                        const int c = w >> tsh, p = w & (tpc - 1);
+                        const int cnl = jj * Z + c;
+                        const int l = glay[g * W + jj];
+                        const int k0 = p * le;
+                        const int L = min(max(ldeg[l] - k0, 0), le);
+                        unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
+                        float* P = reinterpret_cast<float*>(base);
+                        const float* dl = reinterpret_cast<const float*>(base + C.p_bytes + C.m_bytes) +
+                                          cnl * C.delta_stride + k0;
+                        const int2* et = tab + l * md + k0;
+                        for (int k = 0; k < L; ++k) at_b(P, tile_vb(et[k], c, Z4)) += dl[k];
+                    }
+                    __syncthreads();
+                }
+            }
+            // ---- Step 4: syndrome of every slot that needs it -----------------------------------
+            if (tid < C.slots) {
+                sh.iter[tid] += (sh.frame[tid] >= 0) ? 1 : 0;
+                sh.epoch[tid] += (sh.frame[tid] >= 0) ? 1 : 0;
+                sh.unsat[tid] = 0u;
+            }
+            __syncthreads();
+            {
+                const int per_s = nl * Z * tpc;
+                const int swork = C.slots * per_s;
+                const int srounds = (swork + nt - 1) / nt;
+                for (int rr = 0; rr < srounds; ++rr) {
+                    const int i = rr * nt + tid;
+                    const int s = i / per_s;
+                    unsigned pbit = 0u;
+                    const bool live = i < swork && sh.frame[s] >= 0 && (r.early_stop || sh.iter[s] >= r.max_iter);
+                    const int w = i - s * per_s;
+                    const int cn_i = w >> tsh, p = w & (tpc - 1);
+                    if (live) {
+                        const int l = cn_i / Z, c = cn_i - l * Z;
+                        const int k0 = p * le;
+                        const int L = min(max(ldeg[l] - k0, 0), le);
+                        float* P = reinterpret_cast<float*>(slots_base + static_cast<size_t>(s) * C.slot_bytes);
+                        const int2* et = tab + l * md + k0;
+                        for (int k = 0; k < L; ++k) pbit ^= (at_b(P, tile_vb(et[k], c, Z4)) < 0.f) ? 1u : 0u;
+                    }
+                    if (tpc > 1) {
+                        pbit ^= __shfl_xor_sync(gmask, pbit, 1);
+                        if (tpc == 4) pbit ^= __shfl_xor_sync(gmask, pbit, 2);
+                    }
+                    if (live && p == 0 && pbit) sh.unsat[s] = 1u;
+                }
+            }
+            __syncthreads();
+            // ---- retire finished frames (or, serving, park them) and refill their slots ---------
+            for (int s = 0; s < C.slots; ++s) {
+                const long long f = sh.frame[s];
+                if (f < 0) continue;
+                const int it = sh.iter[s];
+                const bool done = (r.early_stop && !sh.unsat[s]) || it >= r.max_iter;
+                const bool park = SERVE && !done && sh.epoch[s] >= C.epoch_iters;
+                if (!done && !park) continue;
+                unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
+                float* P = reinterpret_cast<float*>(base);
+                if (done) {
+                    MsgT* msg = slot_msgs<MsgT, SERVE>(C, base, s, f);
+                    if (r.msgs_out)
+                        for (int e = tid; e < C.msg_slots; e += nt) {
+                            const int csr = __ldg(C.csr_of + e);
+                            if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]);
+                        }
+                    write_frame_outputs(r, P, f, it, sh.unsat[s] ? 1 : 0, &sh.err);
+                    if (SERVE && tid == 0) C.state_flag[f] = kSlotDone;
+                } else {
+                    save_frame<MsgT>(C, base, f);
+                    if (tid == 0) C.state_iter[f] = it;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    const long long nf = claim_frame<SERVE>(sh, C);
+                    sh.frame[s] = nf;
+                    sh.iter[s] = (SERVE && nf >= 0) ? (C.state_flag[nf] == kSlotNew ? 0 : C.state_iter[nf]) : 0;
+                    sh.epoch[s] = 0;
+                    if (SERVE && nf >= 0) C.state_flag[nf] = kSlotRunning;
+                }
+                __syncthreads();
+                const long long nf = sh.frame[s];
+                if (nf >= 0) load_frame<MsgT, SERVE>(C, base, s, nf, sh.iter[s]);
+                __syncthreads();
+            }
+            if (tid == 0) {
+                int any = 0;
+                for (int s = 0; s < C.slots; ++s) any |= sh.frame[s] >= 0;
+                sh.active = any;
+            }
+            __syncthreads();
+            if (!sh.active) break;
+        }
+    }
+}
+
+TileKernelFn pick_tile_kernel(int msg_dtype, bool serve) {
+    switch (msg_dtype) {
+        case NDGSBP_F32: return serve ? tile_decode_kernel<float, true> : tile_decode_kernel<float, false>;
+        case NDGSBP_F16: return serve ? tile_decode_kernel<__half, true> : tile_decode_kernel<__half, false>;
+        case NDGSBP_BF16:
+            return serve ? tile_decode_kernel<__nv_bfloat16, true> : tile_decode_kernel<__nv_bfloat16, false>;
+        default: return nullptr;
+    }
+}
+
+size_t tile_table_bytes(const QcLayout& Q) {
+    const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;
+    const size_t b = static_cast<size_t>(Q.n_layers) * Q.max_deg * 8 + 3 * static_cast<size_t>(Q.n_layers) * 4 + G * Q.window * 4;
+    return (b + 15) & ~static_cast<size_t>(15);
+}
+
+int tile_lanes_per_cn(int maxdeg) { return maxdeg <= 8 ? 1 : maxdeg <= 16 ? 2 : maxdeg <= 32 ? 4 : 0; }
+
+}  // namespace ndgsbp

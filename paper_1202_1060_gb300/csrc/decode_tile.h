@@ -1,0 +1,59 @@
+// Tile decode kernel interface (decode_tile.cu): QC codes of any window size and row degree
+// up to 32, several frames per CTA, and several codes in one launch (ragged batches).
+#pragma once
+
+#include "device_common.cuh"
+#include "ndgsbp_internal.h"
+
+namespace ndgsbp {
+
+// One code of a launch: its layered QC description, its batch, and how a CTA lays it out.
+struct TileCode {
+    int N, E, Z, nl, G, window, maxdeg, msg_slots;
+    int tpc;              // lanes per CN (1, 2 or 4)
+    int le;               // edges per lane, ceil(maxdeg / tpc) <= 8
+    int slots;            // frames a CTA holds at once
+    int slot_bytes;       // shared bytes per frame slot: posterior, messages, deltas
+    int p_bytes;          // posterior bytes at the start of a slot (16-aligned)
+    int m_bytes;          // message bytes after it (0 when messages live in global memory)
+    int delta_stride;     // deltas per CN in the slot's delta buffer (odd >= maxdeg)
+    const int2* edge_tab;
+    const int32_t* layer_deg;
+    const int32_t* layer_stride;
+    const int32_t* layer_off;
+    const int32_t* group_layers;
+    const int32_t* csr_of;
+    RunArgs r;            // this code's batch, parameters and outputs (r.counter unused)
+    void* ws_msgs;        // global message slots (blocks x slots x msg_slots) when m_bytes == 0
+    // serving: frames are slots of a pool whose decoding state persists between launches
+    int* state_flag;      // [pool] kSlotFree / kSlotNew / kSlotRunning / kSlotDone, or null
+    int* state_iter;      // [pool] iterations done so far
+    float* state_P;       // [pool][N] posteriors of running frames
+    void* state_msgs;     // [pool][msg_slots] messages of running frames
+    int epoch_iters;      // iterations a frame may run in one launch before its state is saved
+};
+
+constexpr int kSlotFree = 0, kSlotNew = 1, kSlotRunning = 2, kSlotDone = 3;
+
+constexpr int kTileMaxCodes = 8;
+
+// A launch: a list of tiles (code, first frame, frame count) handed out by an atomic counter.
+// With tiles == nullptr the tiles are implicit: code 0, tile t = frames [t tile_frames, ...).
+struct TileArgs {
+    TileCode codes[kTileMaxCodes];
+    int n_codes;
+    const int4* tiles;    // x = code, y = first frame, z = frames
+    int n_tiles;
+    int tile_frames;
+    unsigned long long* tile_counter;
+    int table_bytes;      // shared bytes reserved for the largest code's tables
+};
+
+typedef void (*TileKernelFn)(const TileArgs);
+
+TileKernelFn pick_tile_kernel(int msg_dtype, bool serve = false);
+size_t tile_table_bytes(const QcLayout& Q);
+// Lanes per CN for a code of the given largest degree (edges per lane at most 8), 0 if above 32.
+int tile_lanes_per_cn(int maxdeg);
+
+}  // namespace ndgsbp

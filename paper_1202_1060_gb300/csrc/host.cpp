@@ -377,6 +377,8 @@ void ndgsbp_params_default(ndgsbp_params* p) {
     p->variant = NDGSBP_VARIANT_AUTO;
     p->block_threads = 0;
     p->ctas_per_sm = 0;
+    p->frames_per_cta = 0;
+    p->lanes_per_cn = 0;
 }
 
 const char* ndgsbp_last_error(void) { return t_error.c_str(); }

@@ -1,0 +1,492 @@
+// Serving: continuous batching of decode requests over device-resident frame slots.
+//
+// Per code the server owns a pool of slots in device memory: channel LLRs, the decoding state
+// of a running frame (posterior, messages, iteration count, status) and its outputs.  A worker
+// thread repeats one epoch:
+//   1. admit: frames of queued requests (arrival order) take free slots of their code's pool;
+//      their LLRs are copied in and their slots marked new;
+//   2. run: one launch of the tile kernel in serving mode over every pool; each running frame
+//      advances by at most epoch_iters iterations, then retires (zero syndrome or max_iter,
+//      outputs written) or is parked with its state in device memory;
+//   3. harvest: statuses and outputs come back; retired frames free their slots and are copied
+//      into their requests' buffers; a request completes when all its frames have retired.
+// Frames of different requests and codes share every launch, and new requests join as soon
+// as slots free up.  Each frame is computed exactly as by the tile kernel in a plain decode.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "decode_tile.h"
+#include "ndgsbp_internal.h"
+
+namespace ndgsbp {
+ndgsbp_status device_qc_tables(const Groups& g, const QcLayout*& Q, const DeviceQc*& D);
+}
+
+using namespace ndgsbp;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+constexpr int kMaxPoolSlots = 16384;
+
+struct Request {
+    int64_t ticket = 0;
+    int code = 0;
+    int64_t n_frames = 0;
+    const float* llr = nullptr;
+    uint32_t* hard = nullptr;
+    int32_t* iters = nullptr;
+    uint8_t* ok = nullptr;
+    int64_t admitted = 0, retired = 0;
+    Clock::time_point t_submit, t_done;
+    bool done = false;
+};
+
+struct Pool {
+    const Groups* g = nullptr;
+    const QcLayout* Q = nullptr;
+    const DeviceQc* D = nullptr;
+    int N = 0, W = 0, slots = 0, tpc = 1, le = 1, ds = 1, cta_slots = 1;
+    size_t slot_bytes = 0, p_bytes = 0, m_bytes = 0;
+    // device
+    float* llr = nullptr;
+    uint32_t* hard = nullptr;
+    int32_t* iters = nullptr;
+    uint8_t* ok = nullptr;
+    int* flag = nullptr;
+    int* st_iter = nullptr;
+    float* st_P = nullptr;
+    void* st_msgs = nullptr;
+    // pinned host
+    float* h_stage = nullptr;     // LLRs of frames admitted this epoch, by slot
+    int* h_new = nullptr;         // kSlotNew for every slot (source of flag uploads)
+    int* h_flag = nullptr;
+    uint32_t* h_hard = nullptr;
+    int32_t* h_iters = nullptr;
+    uint8_t* h_ok = nullptr;
+    std::vector<int> free_slots;
+    std::vector<std::pair<Request*, int64_t>> owner;
+    std::vector<int> admitted_now;
+};
+
+}  // namespace
+
+struct ndgsbp_server {
+    std::vector<Pool> pools;
+    ndgsbp_params params{};
+    int epoch_iters = 1;
+    int device = 0;
+    TileArgs args{};
+    TileKernelFn fn = nullptr;
+    int grid = 0, threads = 0;
+    size_t smem = 0;
+    int4* d_tiles = nullptr;
+    unsigned long long* d_counter = nullptr;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::unordered_map<int64_t, std::unique_ptr<Request>> reqs;
+    int64_t next_ticket = 1;
+    int64_t in_flight = 0;   // frames holding a slot
+    bool stop = false;
+    ndgsbp_status failed = NDGSBP_OK;
+    std::string failure;
+    std::thread worker;
+    ndgsbp_server_stats stats{};
+
+    ~ndgsbp_server();
+    void run();
+    bool epoch();
+};
+
+ndgsbp_server::~ndgsbp_server() {
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        stop = true;
+    }
+    cv_work.notify_all();
+    if (worker.joinable()) worker.join();
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cudaSetDevice(device) == cudaSuccess) {
+        if (stream) cudaStreamSynchronize(stream);
+        for (Pool& p : pools) {
+            cudaFree(p.llr);
+            cudaFree(p.hard);
+            cudaFree(p.iters);
+            cudaFree(p.ok);
+            cudaFree(p.flag);
+            cudaFree(p.st_iter);
+            cudaFree(p.st_P);
+            cudaFree(p.st_msgs);
+            cudaFreeHost(p.h_stage);
+            cudaFreeHost(p.h_new);
+            cudaFreeHost(p.h_flag);
+            cudaFreeHost(p.h_hard);
+            cudaFreeHost(p.h_iters);
+            cudaFreeHost(p.h_ok);
+        }
+        cudaFree(d_tiles);
+        cudaFree(d_counter);
+        if (stream) cudaStreamDestroy(stream);
+        cudaSetDevice(cur);
+    }
+    cudaGetLastError();
+}
+
+#define SRV_CUDA(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t _e = (expr);                                                              \
+        if (_e != cudaSuccess) {                                                              \
+            std::lock_guard<std::mutex> lock(mu);                                             \
+            failed = NDGSBP_ERR_CUDA;                                                         \
+            failure = std::string(#expr) + ": " + cudaGetErrorString(_e);                     \
+            return false;                                                                     \
+        }                                                                                     \
+    } while (0)
+
+// One epoch; false on a CUDA error (recorded, the worker stops).
+bool ndgsbp_server::epoch() {
+    // 1. admission, in arrival order, frame by frame as slots are free
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (Pool& p : pools) p.admitted_now.clear();
+        for (auto it = queue.begin(); it != queue.end();) {
+            Request* r = *it;
+            Pool& p = pools[r->code];
+            while (r->admitted < r->n_frames && !p.free_slots.empty()) {
+                const int slot = p.free_slots.back();
+                p.free_slots.pop_back();
+                p.owner[slot] = {r, r->admitted};
+                std::memcpy(p.h_stage + static_cast<size_t>(slot) * p.N, r->llr + static_cast<size_t>(r->admitted) * p.N,
+                            sizeof(float) * p.N);
+                p.admitted_now.push_back(slot);
+                ++r->admitted;
+                ++in_flight;
+            }
+            it = (r->admitted == r->n_frames) ? queue.erase(it) : std::next(it);
+        }
+    }
+    for (Pool& p : pools) {
+        std::sort(p.admitted_now.begin(), p.admitted_now.end());
+        for (size_t i = 0; i < p.admitted_now.size();) {
+            size_t j = i + 1;
+            while (j < p.admitted_now.size() && p.admitted_now[j] == p.admitted_now[j - 1] + 1) ++j;
+            const int a = p.admitted_now[i], n = static_cast<int>(j - i);
+            SRV_CUDA(cudaMemcpyAsync(p.llr + static_cast<size_t>(a) * p.N, p.h_stage + static_cast<size_t>(a) * p.N,
+                                     sizeof(float) * p.N * n, cudaMemcpyHostToDevice, stream));
+            SRV_CUDA(cudaMemcpyAsync(p.flag + a, p.h_new + a, sizeof(int) * n, cudaMemcpyHostToDevice, stream));
+            i = j;
+        }
+    }
+    // 2. one serving launch over every pool
+    const auto t0 = Clock::now();
+    SRV_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), stream));
+    fn<<<grid, threads, smem, stream>>>(args);
+    SRV_CUDA(cudaGetLastError());
+    // 3. statuses and outputs back, then harvest
+    for (Pool& p : pools) {
+        SRV_CUDA(cudaMemcpyAsync(p.h_flag, p.flag, sizeof(int) * p.slots, cudaMemcpyDeviceToHost, stream));
+        SRV_CUDA(cudaMemcpyAsync(p.h_iters, p.iters, sizeof(int32_t) * p.slots, cudaMemcpyDeviceToHost, stream));
+        SRV_CUDA(cudaMemcpyAsync(p.h_ok, p.ok, p.slots, cudaMemcpyDeviceToHost, stream));
+        SRV_CUDA(cudaMemcpyAsync(p.h_hard, p.hard, sizeof(uint32_t) * p.W * p.slots, cudaMemcpyDeviceToHost, stream));
+    }
+    SRV_CUDA(cudaStreamSynchronize(stream));
+    const auto t1 = Clock::now();
+    std::vector<Request*> finished;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        stats.epochs += 1;
+        stats.busy_seconds += std::chrono::duration<double>(t1 - t0).count();
+        for (Pool& p : pools) {
+            for (int slot = 0; slot < p.slots; ++slot) {
+                Request* r = p.owner[slot].first;
+                if (!r || p.h_flag[slot] != kSlotDone) continue;
+                const int64_t f = p.owner[slot].second;
+                std::memcpy(r->hard + static_cast<size_t>(f) * p.W, p.h_hard + static_cast<size_t>(slot) * p.W,
+                            sizeof(uint32_t) * p.W);
+                if (r->iters) r->iters[f] = p.h_iters[slot];
+                if (r->ok) r->ok[f] = p.h_ok[slot];
+                stats.frames_completed += 1;
+                stats.iterations += p.h_iters[slot];
+                if (!p.h_ok[slot]) stats.frame_errors_unsatisfied += 1;
+                p.owner[slot] = {nullptr, 0};
+                p.free_slots.push_back(slot);
+                --in_flight;
+                if (++r->retired == r->n_frames) finished.push_back(r);
+            }
+        }
+        for (Request* r : finished) {
+            r->done = true;
+            r->t_done = Clock::now();
+            stats.requests_completed += 1;
+        }
+    }
+    if (!finished.empty()) cv_done.notify_all();
+    return true;
+}
+
+void ndgsbp_server::run() {
+    cudaSetDevice(device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lock(mu);
+            cv_work.wait(lock, [&] { return stop || !queue.empty() || in_flight > 0; });
+            if (stop) return;
+        }
+        if (!epoch()) {
+            cv_done.notify_all();
+            return;
+        }
+    }
+}
+
+static size_t a16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
+
+extern "C" {
+
+ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_codes, const double* weights,
+                                   const ndgsbp_params* params, size_t hbm_budget_bytes, int32_t epoch_iters,
+                                   ndgsbp_server** out) {
+    clear_error();
+    if (!codes || !params || !out || n_codes < 1 || n_codes > kTileMaxCodes || epoch_iters < 1)
+        return fail(NDGSBP_ERR_INVALID, "server_create: need 1..%d codes, params and epoch_iters >= 1", kTileMaxCodes);
+    if (params->max_iter < 1 || !(params->llr_max > 0.f && params->llr_max <= 30.f))
+        return fail(NDGSBP_ERR_INVALID, "server_create: bad max_iter or llr_max");
+    TileKernelFn fn = pick_tile_kernel(params->msg_dtype, /*serve=*/true);
+    if (!fn) return fail(NDGSBP_ERR_INVALID, "server_create: msg_dtype must be F32, F16 or BF16");
+    const int ms = params->msg_dtype == NDGSBP_F32 ? 4 : 2;
+    std::unique_ptr<ndgsbp_server> h(new (std::nothrow) ndgsbp_server);
+    if (!h) return fail(NDGSBP_ERR_NOMEM, "out of host memory");
+    int dev = 0, sms = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))
+        return fail(NDGSBP_ERR_CUDA, "server_create: no CUDA device");
+    h->device = dev;
+    h->params = *params;
+    h->epoch_iters = epoch_iters;
+    h->pools.resize(n_codes);
+    double wsum = 0.0;
+    for (int i = 0; i < n_codes; ++i) wsum += weights ? std::max(0.0, weights[i]) : 1.0;
+    if (!(wsum > 0.0)) return fail(NDGSBP_ERR_INVALID, "server_create: weights sum to zero");
+    const size_t budget = static_cast<size_t>(optin) - 256;
+    size_t table_max = 0;
+    int threads = params->block_threads;
+    for (int i = 0; i < n_codes; ++i) {
+        Pool& p = h->pools[i];
+        if (!codes[i]) return fail(NDGSBP_ERR_INVALID, "server_create: code %d is null", i);
+        p.g = &codes[i]->g;
+        if (!p.g->qc.ok) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d is not QC grouped in whole layers", i);
+        ndgsbp_status st = device_qc_tables(*p.g, p.Q, p.D);
+        if (st) return st;
+        p.tpc = tile_lanes_per_cn(p.Q->max_deg);
+        if (!p.tpc) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d has row degree above 32", i);
+        p.le = (p.Q->max_deg + p.tpc - 1) / p.tpc;
+        p.ds = p.Q->max_deg | 1;
+        p.N = p.g->code->N;
+        p.W = (p.N + 31) / 32;
+        table_max = std::max(table_max, tile_table_bytes(*p.Q));
+        if (!params->block_threads)
+            threads = std::max(threads, std::min(512, std::max(128, (p.Q->window * p.Q->Z * p.tpc + 31) / 32 * 32)));
+    }
+    size_t smem = table_max;
+    for (int i = 0; i < n_codes; ++i) {
+        Pool& p = h->pools[i];
+        p.p_bytes = a16(static_cast<size_t>(p.N) * 4);
+        const size_t m = a16(static_cast<size_t>(p.Q->msg_slots) * ms);
+        const size_t d = a16(static_cast<size_t>(p.Q->window) * p.Q->Z * p.ds * 4);
+        p.m_bytes = table_max + p.p_bytes + m + d <= budget ? m : 0;
+        p.slot_bytes = p.p_bytes + p.m_bytes + d;
+        if (table_max + p.slot_bytes > budget) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d too large", i);
+        const int per_slot = p.Q->window * p.Q->Z * p.tpc;
+        p.cta_slots = std::max(1, std::min<int>({16, threads / per_slot, static_cast<int>((budget - table_max) / p.slot_bytes)}));
+        smem = std::max(smem, table_max + p.cta_slots * p.slot_bytes);
+        // pool size from the budget share: LLR, posterior, messages, outputs and status per slot
+        const double share = (weights ? std::max(0.0, weights[i]) : 1.0) / wsum;
+        const size_t per = sizeof(float) * p.N * 2 + static_cast<size_t>(p.Q->msg_slots) * ms + sizeof(uint32_t) * p.W + 16;
+        p.slots = static_cast<int>(std::min<double>(kMaxPoolSlots, std::floor(share * hbm_budget_bytes / per)));
+        if (p.slots < 1) return fail(NDGSBP_ERR_BUDGET, "server_create: the budget leaves no slot for code %d", i);
+    }
+    if (threads <= 0 || threads > 1024 || threads % 32)
+        return fail(NDGSBP_ERR_INVALID, "server_create: block_threads must be a multiple of 32 up to 1024");
+    cudaError_t e = cudaSuccess;
+    auto dmalloc = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+        if (e == cudaSuccess) e = cudaMemset(*ptr, 0, bytes);
+    };
+    auto hmalloc = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaHostAlloc(ptr, bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) std::memset(*ptr, 0, bytes);
+    };
+    std::vector<int4> tiles;
+    for (int i = 0; i < n_codes; ++i) {
+        Pool& p = h->pools[i];
+        dmalloc(reinterpret_cast<void**>(&p.llr), sizeof(float) * p.N * static_cast<size_t>(p.slots));
+        dmalloc(reinterpret_cast<void**>(&p.hard), sizeof(uint32_t) * p.W * static_cast<size_t>(p.slots));
+        dmalloc(reinterpret_cast<void**>(&p.iters), sizeof(int32_t) * p.slots);
+        dmalloc(reinterpret_cast<void**>(&p.ok), p.slots);
+        dmalloc(reinterpret_cast<void**>(&p.flag), sizeof(int) * p.slots);
+        dmalloc(reinterpret_cast<void**>(&p.st_iter), sizeof(int) * p.slots);
+        dmalloc(reinterpret_cast<void**>(&p.st_P), sizeof(float) * p.N * static_cast<size_t>(p.slots));
+        dmalloc(&p.st_msgs, static_cast<size_t>(p.Q->msg_slots) * ms * p.slots);
+        hmalloc(reinterpret_cast<void**>(&p.h_stage), sizeof(float) * p.N * static_cast<size_t>(p.slots));
+        hmalloc(reinterpret_cast<void**>(&p.h_new), sizeof(int) * p.slots);
+        hmalloc(reinterpret_cast<void**>(&p.h_flag), sizeof(int) * p.slots);
+        hmalloc(reinterpret_cast<void**>(&p.h_hard), sizeof(uint32_t) * p.W * static_cast<size_t>(p.slots));
+        hmalloc(reinterpret_cast<void**>(&p.h_iters), sizeof(int32_t) * p.slots);
+        hmalloc(reinterpret_cast<void**>(&p.h_ok), p.slots);
+        if (e != cudaSuccess) return fail(NDGSBP_ERR_NOMEM, "server_create: %s", cudaGetErrorString(e));
+        for (int s = 0; s < p.slots; ++s) p.h_new[s] = kSlotNew;
+        p.owner.assign(p.slots, {nullptr, 0});
+        for (int s = p.slots - 1; s >= 0; --s) p.free_slots.push_back(s);
+        TileCode& C = h->args.codes[i];
+        C.N = p.N;
+        C.E = static_cast<int>(p.g->code->E);
+        C.Z = p.Q->Z;
+        C.nl = p.Q->n_layers;
+        C.G = static_cast<int>(p.Q->group_layers.size() / p.Q->window);
+        C.window = p.Q->window;
+        C.maxdeg = p.Q->max_deg;
+        C.msg_slots = p.Q->msg_slots;
+        C.tpc = p.tpc;
+        C.le = p.le;
+        C.slots = p.cta_slots;
+        C.slot_bytes = static_cast<int>(p.slot_bytes);
+        C.p_bytes = static_cast<int>(p.p_bytes);
+        C.m_bytes = static_cast<int>(p.m_bytes);
+        C.delta_stride = p.ds;
+        C.edge_tab = reinterpret_cast<const int2*>(p.D->edge_tab);
+        C.layer_deg = p.D->layer_deg;
+        C.layer_stride = p.D->layer_stride;
+        C.layer_off = p.D->layer_off;
+        C.group_layers = p.D->group_layers;
+        C.csr_of = p.D->csr_of;
+        C.state_flag = p.flag;
+        C.state_iter = p.st_iter;
+        C.state_P = p.st_P;
+        C.state_msgs = p.st_msgs;
+        C.epoch_iters = epoch_iters;
+        RunArgs& r = C.r;
+        r.N = p.N;
+        r.E = C.E;
+        r.W = p.W;
+        r.llr = p.llr;
+        r.llr_dtype = NDGSBP_F32;
+        r.n_frames = p.slots;
+        r.max_iter = params->max_iter;
+        r.llr_max = params->llr_max;
+        r.early_stop = params->early_stop ? 1 : 0;
+        r.hard_bits = p.hard;
+        r.iters = p.iters;
+        r.synd_ok = p.ok;
+        const int tf = p.cta_slots * 2;
+        for (int s = 0; s < p.slots; s += tf) tiles.push_back(make_int4(i, s, std::min(tf, p.slots - s), 0));
+        h->stats.slots_total += p.slots;
+    }
+    dmalloc(reinterpret_cast<void**>(&h->d_tiles), sizeof(int4) * tiles.size());
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
+    dmalloc(reinterpret_cast<void**>(&h->d_counter), 256);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), threads, smem);
+    if (e != cudaSuccess) return fail(NDGSBP_ERR_CUDA, "server_create: %s", cudaGetErrorString(e));
+    if (per_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: the launch does not fit on an SM");
+    if (params->ctas_per_sm > 0) per_sm = std::min(per_sm, params->ctas_per_sm);
+    h->args.n_codes = n_codes;
+    h->args.tiles = h->d_tiles;
+    h->args.n_tiles = static_cast<int>(tiles.size());
+    h->args.tile_counter = h->d_counter;
+    h->args.table_bytes = static_cast<int>(table_max);
+    h->fn = fn;
+    h->threads = threads;
+    h->smem = smem;
+    h->grid = std::max(1, std::min(per_sm * sms, h->args.n_tiles));
+    ndgsbp_server* raw = h.release();
+    raw->worker = std::thread([raw] { raw->run(); });
+    *out = raw;
+    return NDGSBP_OK;
+}
+
+ndgsbp_status ndgsbp_server_submit(ndgsbp_server* s, int32_t code, const float* host_llr, int64_t n_frames,
+                                   uint32_t* host_hard_bits, int32_t* host_iters, uint8_t* host_syndrome_ok,
+                                   int64_t* ticket) {
+    clear_error();
+    if (!s || !ticket || code < 0 || code >= static_cast<int32_t>(s->pools.size()) || n_frames < 1 || !host_llr ||
+        !host_hard_bits)
+        return fail(NDGSBP_ERR_INVALID, "server_submit: bad arguments");
+    auto r = std::make_unique<Request>();
+    r->code = code;
+    r->n_frames = n_frames;
+    r->llr = host_llr;
+    r->hard = host_hard_bits;
+    r->iters = host_iters;
+    r->ok = host_syndrome_ok;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->failed) return fail(s->failed, "server stopped: %s", s->failure.c_str());
+        r->ticket = s->next_ticket++;
+        *ticket = r->ticket;
+        s->queue.push_back(r.get());
+        s->reqs.emplace(r->ticket, std::move(r));
+        s->stats.requests_submitted += 1;
+    }
+    s->cv_work.notify_one();
+    return NDGSBP_OK;
+}
+
+ndgsbp_status ndgsbp_server_poll(ndgsbp_server* s, int64_t ticket, int32_t* done, double* latency_ms) {
+    if (!s) return fail(NDGSBP_ERR_INVALID, "server_poll: null server");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(NDGSBP_ERR_INVALID, "server_poll: unknown ticket %lld", static_cast<long long>(ticket));
+    if (s->failed) return fail(s->failed, "server stopped: %s", s->failure.c_str());
+    const bool fin = it->second->done;
+    if (done) *done = fin ? 1 : 0;
+    if (latency_ms && fin)
+        *latency_ms = std::chrono::duration<double, std::milli>(it->second->t_done - it->second->t_submit).count();
+    if (fin) s->reqs.erase(it);   // reported once: the ticket is released
+    return NDGSBP_OK;
+}
+
+ndgsbp_status ndgsbp_server_wait(ndgsbp_server* s, int64_t ticket, int32_t timeout_ms, double* latency_ms) {
+    if (!s) return fail(NDGSBP_ERR_INVALID, "server_wait: null server");
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(NDGSBP_ERR_INVALID, "server_wait: unknown ticket %lld", static_cast<long long>(ticket));
+    Request* r = it->second.get();
+    const bool ok = s->cv_done.wait_for(lock, std::chrono::milliseconds(std::max(0, timeout_ms)),
+                                        [&] { return r->done || s->failed; });
+    if (s->failed) return fail(s->failed, "server stopped: %s", s->failure.c_str());
+    if (!ok) return fail(NDGSBP_ERR_TIMEOUT, "server_wait: request %lld not done after %d ms",
+                         static_cast<long long>(ticket), timeout_ms);
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    s->reqs.erase(it);   // reported once: the ticket is released
+    return NDGSBP_OK;
+}
+
+ndgsbp_status ndgsbp_server_stats_get(ndgsbp_server* s, ndgsbp_server_stats* out) {
+    if (!s || !out) return fail(NDGSBP_ERR_INVALID, "server_stats: null pointer");
+    std::lock_guard<std::mutex> lock(s->mu);
+    *out = s->stats;
+    out->slots_in_use = s->in_flight;
+    return NDGSBP_OK;
+}
+
+ndgsbp_status ndgsbp_server_destroy(ndgsbp_server* s) {
+    delete s;
+    return NDGSBP_OK;
+}
+
+}  // extern "C"

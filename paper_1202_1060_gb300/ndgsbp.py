@@ -26,7 +26,7 @@ UNIT_CN, UNIT_LAYER = 0, 1
 GROUPS_CYCLIC, GROUPS_NATURAL = 1, 2
 SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
 VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1, 2, 3, 4
-VARIANT_QC_PAIR, VARIANT_QC_PAIR_GLOBAL = 5, 6
+VARIANT_QC_PAIR, VARIANT_QC_PAIR_GLOBAL, VARIANT_TILE = 5, 6, 7
 STAT_FRAMES, STAT_FRAME_ERRORS, STAT_BIT_ERRORS, STAT_UNDETECTED = 0, 1, 2, 3
 STAT_ITERATIONS, STAT_UNSATISFIED, STATS_LEN = 4, 5, 8
 
@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("msg_dtype", ctypes.c_int32), ("llr_max", ctypes.c_float),
                 ("early_stop", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("frames_per_cta", ctypes.c_int32), ("lanes_per_cn", ctypes.c_int32)]
 
 
 class Plan(ctypes.Structure):
@@ -60,6 +61,24 @@ class Extras(ctypes.Structure):
                 ("d_stats", ctypes.c_void_p), ("d_iter_hist", ctypes.c_void_p),
                 ("d_start_ns", ctypes.c_void_p), ("d_retire_ns", ctypes.c_void_p),
                 ("d_messages", ctypes.c_void_p)]
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_void_p), ("d_llr", ctypes.c_void_p), ("llr_dtype", ctypes.c_int32),
+                ("n_frames", ctypes.c_int64), ("d_hard_bits", ctypes.c_void_p), ("d_iters", ctypes.c_void_p),
+                ("d_syndrome_ok", ctypes.c_void_p), ("d_posterior", ctypes.c_void_p), ("d_stats", ctypes.c_void_p),
+                ("d_start_ns", ctypes.c_void_p), ("d_retire_ns", ctypes.c_void_p),
+                ("frames_per_cta", ctypes.c_int32), ("lanes_per_cn", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests_submitted", ctypes.c_int64), ("requests_completed", ctypes.c_int64),
+                ("frames_completed", ctypes.c_int64), ("frame_errors_unsatisfied", ctypes.c_int64),
+                ("epochs", ctypes.c_int64), ("iterations", ctypes.c_int64), ("busy_seconds", ctypes.c_double),
+                ("slots_total", ctypes.c_int64), ("slots_in_use", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _P, _I32, _I64, _U64, _D, _U32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
@@ -85,6 +104,18 @@ _SIGS = {
     "ndgsbp_decode_ex": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, ctypes.c_size_t,
                                 _P, _P, _P, _P, ctypes.POINTER(Extras), _P]),
     "ndgsbp_decode_static": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, _P, _P, _P, _P]),
+    "ndgsbp_ragged_create": (_I32, [_P, _I32, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
+    "ndgsbp_ragged_info": (_I32, [_P, ctypes.POINTER(Plan), _P]),
+    "ndgsbp_ragged_launch": (_I32, [_P, _P]),
+    "ndgsbp_ragged_graph_launch": (_I32, [_P, _P]),
+    "ndgsbp_ragged_destroy": (_I32, [_P]),
+    "ndgsbp_server_create": (_I32, [_P, _I32, _P, ctypes.POINTER(Params), ctypes.c_size_t, _I32,
+                                    ctypes.POINTER(_P)]),
+    "ndgsbp_server_submit": (_I32, [_P, _I32, _P, _I64, _P, _P, _P, ctypes.POINTER(_I64)]),
+    "ndgsbp_server_poll": (_I32, [_P, _I64, ctypes.POINTER(_I32), ctypes.POINTER(_D)]),
+    "ndgsbp_server_wait": (_I32, [_P, _I64, _I32, ctypes.POINTER(_D)]),
+    "ndgsbp_server_stats_get": (_I32, [_P, ctypes.POINTER(ServerStats)]),
+    "ndgsbp_server_destroy": (_I32, [_P]),
 }
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -308,6 +339,119 @@ def decode_static(groups: Groups, params: Params, llr, hard_bits, iters=None, sy
     _check(_lib.ndgsbp_decode_static(groups.handle, ctypes.byref(params), _dptr(llr), dtype_code(llr),
                                      llr.shape[0], _dptr(hard_bits), _dptr(iters), _dptr(syndrome_ok),
                                      _dptr(posterior), _stream(stream)))
+
+
+class Ragged:
+    """ndgsbp_ragged handle: one persistent launch over batches of several codes.  Each batch is
+    a dict with groups, llr (CUDA tensor [F, N]) and output tensors hard_bits, iters,
+    syndrome_ok, posterior, stats, start_ns, retire_ns (optional), frames_per_cta, lanes_per_cn."""
+
+    def __init__(self, batches, params: Params):
+        arr = (Batch * len(batches))()
+        self._keep = batches
+        for i, b in enumerate(batches):
+            llr = b["llr"]
+            arr[i] = Batch(groups=b["groups"].handle.value, d_llr=_addr(llr), llr_dtype=dtype_code(llr),
+                           n_frames=llr.shape[0], d_hard_bits=_addr(b["hard_bits"]), d_iters=_addr(b.get("iters")),
+                           d_syndrome_ok=_addr(b.get("syndrome_ok")), d_posterior=_addr(b.get("posterior")),
+                           d_stats=_addr(b.get("stats")), d_start_ns=_addr(b.get("start_ns")),
+                           d_retire_ns=_addr(b.get("retire_ns")), frames_per_cta=int(b.get("frames_per_cta", 0)),
+                           lanes_per_cn=int(b.get("lanes_per_cn", 0)))
+        h = ctypes.c_void_p()
+        _check(_lib.ndgsbp_ragged_create(arr, len(batches), ctypes.byref(params), ctypes.byref(h)))
+        self._h = h
+
+    def info(self):
+        pl = Plan()
+        n = ctypes.c_int32()
+        _check(_lib.ndgsbp_ragged_info(self._h, ctypes.byref(pl), ctypes.byref(n)))
+        return pl.as_dict(), n.value
+
+    def launch(self, stream=None):
+        _check(_lib.ndgsbp_ragged_launch(self._h, _stream(stream)))
+
+    def graph_launch(self, stream=None):
+        _check(_lib.ndgsbp_ragged_graph_launch(self._h, _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.ndgsbp_ragged_destroy(h)
+            self._h = None
+
+
+class Server:
+    """ndgsbp_server handle: continuous batching of decode requests over device-resident frame
+    slots.  codes is a list of Groups (QC codes grouped in whole layers); weights split
+    hbm_budget_bytes between their pools.  submit() takes host FP32 LLRs [F, N] and returns a
+    Request whose host outputs are filled when it completes."""
+
+    class Request:
+        def __init__(self, server, ticket, llr, hard, iters, ok, N):
+            self.server, self.ticket, self.N = server, ticket, N
+            self._llr, self.hard_words, self.iters, self.syndrome_ok = llr, hard, iters, ok
+            self.latency_ms = None
+
+        def done(self) -> bool:
+            if self.latency_ms is None:
+                d, lat = ctypes.c_int32(), ctypes.c_double()
+                _check(_lib.ndgsbp_server_poll(self.server._h, self.ticket, ctypes.byref(d), ctypes.byref(lat)))
+                if d.value:
+                    self._finish(lat.value)
+            return self.latency_ms is not None
+
+        def wait(self, timeout_ms: int = 60000) -> float:
+            """Block until done; returns the request latency in ms (host clock)."""
+            if self.latency_ms is None:
+                lat = ctypes.c_double()
+                _check(_lib.ndgsbp_server_wait(self.server._h, self.ticket, int(timeout_ms), ctypes.byref(lat)))
+                self._finish(lat.value)
+            return self.latency_ms
+
+        def _finish(self, lat):
+            self.latency_ms = lat
+            self.server._live.pop(self.ticket, None)
+
+        def hard_bits(self):
+            return unpack_bits(self.hard_words, self.N)
+
+    def __init__(self, codes, params: Params, hbm_budget_bytes: int, epoch_iters: int = 1, weights=None):
+        arr = (ctypes.c_void_p * len(codes))(*[g.handle.value for g in codes])
+        w = None if weights is None else np.ascontiguousarray(weights, np.float64)
+        h = ctypes.c_void_p()
+        self._codes = list(codes)
+        self._live = {}   # requests in flight: their host buffers stay alive until completion
+        _check(_lib.ndgsbp_server_create(arr, len(codes), _hptr(w), ctypes.byref(params), int(hbm_budget_bytes),
+                                         int(epoch_iters), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, code: int, llr) -> "Server.Request":
+        llr = np.ascontiguousarray(llr, np.float32)
+        F, N = llr.shape
+        hard = np.zeros((F, (N + 31) // 32), np.uint32)
+        iters = np.zeros(F, np.int32)
+        ok = np.zeros(F, np.uint8)
+        t = ctypes.c_int64()
+        _check(_lib.ndgsbp_server_submit(self._h, int(code), _hptr(llr), F, _hptr(hard), _hptr(iters), _hptr(ok),
+                                         ctypes.byref(t)))
+        req = Server.Request(self, t.value, llr, hard, iters, ok, N)
+        self._live[t.value] = req
+        return req
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.ndgsbp_server_stats_get(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.ndgsbp_server_destroy(h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        self.close()
 
 
 def unpack_bits(words, N: int):

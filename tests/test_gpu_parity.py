@@ -418,3 +418,50 @@ def test_full_size_qc2304_sampled(env, oracle_mod):
     synd_ok = ~(((allbits.astype(np.int64) @ H.T) % 2).any(axis=1))
     assert (synd_ok.astype(np.uint8) == ok.cpu().numpy()).all()
     assert it.min() >= 1 and it.max() <= 25
+
+
+# ----------------------------------------------------------------------------------------
+# tile kernel: lanes per CN, frames per CTA, large windows
+# ----------------------------------------------------------------------------------------
+TILE_CASES = [("qc_n2304_r12", "layers_cyclic", (1, 2), 1.25), ("qc_n576_r12", "flood", (1, 2, 4), 2.0),
+              ("qc_n2304_r34", "layers_cyclic", (2, 4), 3.0), ("qc_n1152_r23", "layers_cyclic", (2, 4), 2.5),
+              ("qc_n8192_r2732", "layers_cyclic", (4,), 3.5), ("qc_n16200_r23", "layers_cyclic", (2, 4), 2.0)]
+
+
+@pytest.mark.parametrize("name,kind,lanes,ebn0", TILE_CASES)
+def test_tile_kernel(env, oracle_mod, name, kind, lanes, ebn0):
+    """One lane per CN reproduces the other kernels bit for bit; 2 or 4 lanes per CN combine the
+    tanh product in another order and are held to the message tolerance against the oracle.
+    Any number of frames per CTA gives the same result as one."""
+    nd, torch = env
+    c = I.code_by_name(name)
+    F = 40 if c.N <= 2304 else 8
+    sched = nd.SCHEDULE_FLOOD if kind == "flood" else nd.SCHEDULE_GROUPS
+    code, g = _groups(nd, c, "layers_cyclic")
+    llr = I.channel_llr(c.N, F, ebn0, I.design_rate(c), seed=4242)
+    q = g.query()
+    if kind == "flood":
+        ref_k = oracle_mod.flood_decode(c, llr.astype(np.float32).astype(np.float64), 2, early_stop=False,
+                                        want_c2v=True)
+        ref_full = oracle_mod.flood_decode(c, llr.astype(np.float32).astype(np.float64), 30)
+    else:
+        ref_k = _oracle(oracle_mod, c, g, llr, max_iter=2, early_stop=False, want_c2v=True)
+        ref_full = _oracle(oracle_mod, c, g, llr, max_iter=30)
+    stable = ~(np.abs(ref_full.total) < NEAR_ZERO).any(axis=1) & (ref_full.synd_ok == 1)
+    for tpc in lanes:
+        kw = dict(variant=nd.VARIANT_TILE, lanes_per_cn=tpc, schedule=sched)
+        first = None
+        for fpc in (1, 3, 16):
+            r2 = _run(nd, torch, g, c, llr, want_msgs=True, max_iter=2, early_stop=0, frames_per_cta=fpc, **kw)
+            assert r2["plan"]["variant"] == nd.VARIANT_TILE
+            assert _msg_err(r2["msgs"], ref_k.c2v) <= MSG_TOL, (tpc, fpc)
+            full = _run(nd, torch, g, c, llr, max_iter=30, frames_per_cta=fpc, **kw)
+            assert (full["iters"][stable] == ref_full.iters[stable]).all(), (tpc, fpc)
+            assert (full["bits"][stable] == ref_full.hard[stable]).all()
+            if first is None:
+                first = full
+            else:
+                assert (full["post"] == first["post"]).all(), (tpc, fpc)
+        if tpc == 1:
+            base = _run(nd, torch, g, c, llr, max_iter=30, schedule=sched, variant=nd.VARIANT_SMEM)
+            assert (first["post"] == base["post"]).all()
