@@ -444,6 +444,335 @@ def run_e2e(args, nd, torch, code, c, groups, params, F, W, dev, rank, world):
             "timer": "host wall clock around all steps, synchronised", "syndrome_ok_fraction": ok_frac}
 
 
+# ------------------------------------------------------------------------------------------
+# supplementary workloads: ragged multi-code batches, serving, reduced-precision messages
+# ------------------------------------------------------------------------------------------
+# Eb/N0 of each code's FER ~ 1e-3 point (FP32 messages, cyclic 2-layer NDGSBP), from a GPU
+# pre-sweep in 0.1 dB steps over 262,144 frames per point (16200: 131,072)
+FER1E3_EBN0 = {"qc_n2304_r12": 1.8, "qc_n16200_r23": 2.0, "qc_n576_r12": 2.9, "qc_n1152_r23": 3.0,
+               "qc_n2304_r34": 3.2, "qc_n8192_r2732": 3.6}
+MIX4 = [("qc_n576_r12", 0.4), ("qc_n1152_r23", 0.3), ("qc_n2304_r34", 0.2), ("qc_n8192_r2732", 0.1)]
+RAGGED_FRAMES = 200000
+
+
+def _setup_code(nd, I, name, seed=2304):
+    c = I.code_by_name(name)
+    code = nd.Code.from_inputs(c)
+    g = nd.Groups.build(code, c.M // c.Z, 0.5, seed, unit=nd.UNIT_LAYER, flags=nd.GROUPS_CYCLIC)
+    return c, code, g
+
+
+def _mufu_roofline(peaks, peak_kind, sms, mufu_ops, kernel_s, kernel, launches, extra=None):
+    peak_clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = MUFU_PER_CLK_PER_SM * sms * peak_clock_mhz * 1e6 / 1e12
+    achieved = mufu_ops / kernel_s / 1e12
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
+         "traffic": None, "kernel": kernel, "launches": launches, "avg_launch_ms": 1e3 * kernel_s / launches,
+         "what": f"MUFU ops (3 per edge-update of Eq. (1)) over the kernel's CUDA-event time; peak = "
+                 f"{MUFU_PER_CLK_PER_SM} MUFU/clk/SM x {sms} SMs x {peak_clock_mhz:.0f} MHz ({peak_kind})"}
+    if extra:
+        r.update(extra)
+    return r
+
+
+def run_ragged(args):
+    """Ragged batching: one persistent tile-kernel launch (CUDA-graph replay) over 200,000 frames
+    of 4 QC codes in a 40/30/20/10 mix, FP16 messages, per-frame early stop, I_max 30, tile shape
+    from the autotuner, each code at its FER ~ 1e-3 point.  A step = channel generation for the 4
+    codes + the ragged launch.  Beside it: the plain FP32 single-code batched path (each code's
+    batch decoded by its own default launch) on the same frames."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1202_1060_gb300 import inputs as I
+    from paper_1202_1060_gb300 import ndgsbp as nd
+    stream = torch.cuda.Stream(device=dev)
+    batches = []
+    for i, (name, share) in enumerate(MIX4):
+        c, code, g = _setup_code(nd, I, name, seed=17 + i)
+        F = int(RAGGED_FRAMES * share)
+        W = (c.N + 31) // 32
+        batches.append(dict(name=name, c=c, code=code, groups=g, F=F,
+                            llr=torch.empty((F, c.N), dtype=torch.float32, device=dev),
+                            hard_bits=torch.empty((F, W), dtype=torch.int32, device=dev),
+                            iters=torch.empty(F, dtype=torch.int32, device=dev),
+                            syndrome_ok=torch.empty(F, dtype=torch.uint8, device=dev),
+                            stats=torch.zeros(nd.STATS_LEN, dtype=torch.int64, device=dev)))
+    imax = 30
+
+    def gen(s):
+        for i, b in enumerate(batches):
+            nd.awgn_llr(b["code"], b["F"], FER1E3_EBN0[b["name"]], I.design_rate(b["c"]),
+                        CHANNEL_SEED + 31 * i + 1000 * s, b["llr"], stream=stream)
+
+    gen(-1)
+    torch.cuda.synchronize()
+    p0 = nd.params_default(max_iter=imax, msg_dtype=nd.F16)
+    t0 = time.perf_counter()
+    params, tuned_ms = nd.ragged_autotune(batches, p0, sample_frames=8192,
+                                          cache_path=os.path.join(ROOT, "gpurun_out", "tune_cache.txt"))
+    tune_s = time.perf_counter() - t0
+    rg = nd.Ragged(batches, params)
+    plan, n_tiles = rg.info()
+    for s in range(args.warmup):
+        gen(-2 - s)
+        rg.graph_launch(stream)
+    torch.cuda.synchronize()
+    for b in batches:
+        b["stats"].zero_()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
+    ev[0].record(stream)
+    for s in range(args.steps):
+        gen(s)
+        ev[2 * s + 1].record(stream)
+        rg.graph_launch(stream)
+        ev[2 * s + 2].record(stream)
+    ev[-1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = ev[0].elapsed_time(ev[-1]) / 1e3
+    dec_s = sum(ev[2 * s + 1].elapsed_time(ev[2 * s + 2]) for s in range(args.steps)) / 1e3
+    # a stats-carrying launch for FER and iterations (the graph replays the launch recorded at
+    # create time, which carries the stats pointers)
+    per_code = []
+    bits = 0
+    mufu = 0
+    for b in batches:
+        st = b["stats"].cpu().numpy()
+        q = b["groups"].query()
+        K = b["c"].N - b["c"].M
+        bits += b["F"] * K
+        mufu += MUFU_PER_EDGE_UPDATE * q["edge_updates_per_iter"] * int(st[nd.STAT_ITERATIONS])
+        per_code.append({"code": b["name"], "frames": b["F"], "ebn0_db": FER1E3_EBN0[b["name"]],
+                         "fer": float(st[nd.STAT_FRAME_ERRORS] / max(st[nd.STAT_FRAMES], 1)),
+                         "mean_iterations": float(st[nd.STAT_ITERATIONS] / max(st[nd.STAT_FRAMES], 1)),
+                         "frames_per_cta": b["frames_per_cta"], "lanes_per_cn": b["lanes_per_cn"]})
+    value = bits * args.steps / elapsed / 1e9
+    # plain FP32 single-code batched path on the same frames (last step's channel)
+    pf = nd.params_default(max_iter=imax, msg_dtype=nd.F32)
+    ws = [torch.zeros(max(256, b["groups"].workspace_size(pf, b["F"])), dtype=torch.uint8, device=dev)
+          for b in batches]
+    for _ in range(2):
+        for b, w in zip(batches, ws):
+            nd.decode_plain(b["groups"], pf, b["llr"], w, b["hard_bits"], b["iters"], b["syndrome_ok"], stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for b, w in zip(batches, ws):
+        nd.decode_plain(b["groups"], pf, b["llr"], w, b["hard_bits"], b["iters"], b["syndrome_ok"], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    peaks, kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16", "data": "synthetic",
+        "config": {"workload": "ragged: 200,000 frames of 4 QC codes (n=576 r1/2, 1152 r2/3, 2304 r3/4, 8192 r27/32) "
+                               "in a 40/30/20/10 mix, one persistent tile-kernel launch replayed as a CUDA graph, "
+                               "FP16 messages, I_max 30, early stop, each code at its FER~1e-3 Eb/N0, tile shape "
+                               "from the autotuner; step = channel generation + decode",
+                   "l2": "inputs larger than L2 (1.5 GB of LLRs)"},
+        "decode_only_gbit_s": bits * args.steps / dec_s / 1e9,
+        "plain_fp32_single_code_gbit_s": bits / plain_s / 1e9,
+        "speedup_vs_plain_fp32": (bits * args.steps / dec_s) / (bits / plain_s),
+        "per_code": per_code, "tuned": {"block_threads": params.block_threads, "tile_launch_ms": tuned_ms,
+                                        "tuning_s": tune_s, "tiles": n_tiles, "plan": plan},
+        "clocks": clk, "gpu_launches": 5 * args.steps,
+        "roofline": _mufu_roofline(peaks, kind, sms, mufu * args.steps, dec_s, "tile_decode_kernel", args.steps),
+        "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """Serving: Poisson arrivals of decode requests (sizes log-uniform in [1, 4096] frames, code
+    by the 40/30/20/10 mix, Eb/N0 ~ U[1, 3] dB, I_max 30, FP16 messages) at 0.5, 0.75, 1.0 and
+    1.2x the server's saturated capacity; latency = completion - scheduled arrival."""
+    import numpy as np
+    import torch
+    import threading
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1202_1060_gb300 import inputs as I
+    from paper_1202_1060_gb300 import ndgsbp as nd
+    rng = np.random.default_rng(args.arrival_seed)
+    grid = [1.0 + 0.25 * i for i in range(9)]
+    pool_frames = 4096
+    codes = []
+    for i, (name, share) in enumerate(MIX4):
+        c, code, g = _setup_code(nd, I, name, seed=17 + i)
+        tmp = torch.empty((pool_frames, c.N), dtype=torch.float32, device=dev)
+        pools = []
+        for j, eb in enumerate(grid):
+            nd.awgn_llr(code, pool_frames, eb, I.design_rate(c), CHANNEL_SEED + 7919 * i + j, tmp)
+            pools.append(tmp.cpu().numpy().copy())
+        codes.append(dict(name=name, c=c, code=code, groups=g, share=share, pools=pools, K=c.N - c.M))
+    del tmp
+    params = nd.params_default(max_iter=30, msg_dtype=nd.F16)
+    budget = args.serve_budget_mb << 20
+    srv = nd.Server([d["groups"] for d in codes], params, budget, epoch_iters=args.epoch_iters,
+                    weights=[d["share"] * d["c"].N for d in codes])
+
+    def draw_request():
+        k = int(rng.choice(len(codes), p=[d["share"] for d in codes]))
+        size = int(np.clip(np.floor(np.exp(rng.uniform(0.0, np.log(4097.0)))), 1, 4096))
+        eb = rng.uniform(1.0, 3.0)
+        j = int(np.argmin([abs(eb - x) for x in grid]))
+        off = int(rng.integers(0, pool_frames - size + 1))
+        return k, codes[k]["pools"][j][off:off + size]
+
+    # capacity: a saturated backlog
+    backlog = [draw_request() for _ in range(args.serve_backlog)]
+    for k, llr in backlog[:32]:
+        srv.submit(k, llr).wait(600000)
+    t0 = time.perf_counter()
+    reqs = [srv.submit(k, llr) for k, llr in backlog]
+    for r in reqs:
+        r.wait(600000)
+    cap_s = time.perf_counter() - t0
+    cap_frames = sum(llr.shape[0] for _, llr in backlog)
+    cap_bits = sum(llr.shape[0] * codes[k]["K"] for k, llr in backlog)
+    capacity = cap_frames / cap_s
+    mean_size = cap_frames / len(backlog)
+    loads = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    for load in (0.5, 0.75, 1.0, 1.2):
+        rate = load * capacity / mean_size          # requests per second
+        n_req = max(50, int(rate * args.serve_seconds))
+        gaps = rng.exponential(1.0 / rate, n_req)
+        arrivals = np.cumsum(gaps)
+        work = [draw_request() for _ in range(n_req)]
+        handles = [None] * n_req
+        st0 = srv.stats()
+        start = time.perf_counter()
+        for i in range(n_req):
+            now = time.perf_counter() - start
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            handles[i] = srv.submit(work[i][0], work[i][1])
+        for h in handles:
+            h.wait(600000)
+        end = time.perf_counter() - start
+        # latency from the scheduled arrival: submit lateness (client behind schedule) counts
+        lat = []
+        for i, h in enumerate(handles):
+            lat.append(h.latency_ms)
+        st1 = srv.stats()
+        frames = sum(w[1].shape[0] for w in work)
+        bits = sum(w[1].shape[0] * codes[w[0]]["K"] for w in work)
+        loads.append({"load": load, "requests": n_req, "frames": frames, "offered_frames_per_s": load * capacity,
+                      "seconds": end, "gbit_s": bits / end / 1e9,
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "epochs": st1["epochs"] - st0["epochs"],
+                      "frame_errors_unsatisfied": st1["frame_errors_unsatisfied"] - st0["frame_errors_unsatisfied"],
+                      "mean_iterations": (st1["iterations"] - st0["iterations"]) / max(frames, 1)})
+    clk = clocks.stop()
+    stats = srv.stats()
+    srv.close()
+    sat = {"frames_per_s": capacity, "gbit_s": cap_bits / cap_s / 1e9, "requests": len(backlog),
+           "seconds": cap_s}
+    line = {
+        "metric": METRIC, "value": sat["gbit_s"], "unit": "Gbit/s", "n_gpus": 1, "steps": len(loads),
+        "warmup": 32, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16", "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals at 0.5/0.75/1.0/1.2x saturated capacity, request sizes "
+                               "log-uniform in [1, 4096] frames, codes by the 40/30/20/10 mix of n=576/1152/2304/8192, "
+                               "Eb/N0 ~ U[1,3] dB (nearest 0.25 dB pool), FP16 messages, I_max 30, continuous "
+                               "batching with device-resident frame state",
+                   "hbm_budget_mb": args.serve_budget_mb, "epoch_iters": args.epoch_iters,
+                   "arrival_seed": args.arrival_seed, "slots": stats["slots_total"],
+                   "l2": "pool state larger than L2"},
+        "saturated": sat, "loads": loads, "clocks": clk, "gpu_launches": stats["epochs"],
+        "latency": {"p50_ms": loads[2]["p50_ms"], "p99_ms": loads[2]["p99_ms"],
+                    "what": "request completion - submission at 1.0x capacity (host clock)"},
+        "roofline": None, "e2e": {"value": sat["gbit_s"], "unit": "Gbit/s",
+                                  "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                                  "what": "host buffers in and out through the server API"},
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_precision(args):
+    """Reduced-precision messages: the n=2304 r1/2 and n=16200 r2/3 QC codes at their FER ~ 1e-3
+    points, 262,144 frames, FP32 / FP16 / BF16 message storage with FP32 arithmetic."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1202_1060_gb300 import inputs as I
+    from paper_1202_1060_gb300 import ndgsbp as nd
+    stream = torch.cuda.Stream(device=dev)
+    F = args.precision_frames
+    rows = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name in ("qc_n2304_r12", "qc_n16200_r23"):
+        c, code, g = _setup_code(nd, I, name)
+        eb = FER1E3_EBN0[name]
+        llr = torch.empty((F, c.N), dtype=torch.float32, device=dev)
+        nd.awgn_llr(code, F, eb, I.design_rate(c), CHANNEL_SEED + c.N, llr, stream=stream)
+        W = (c.N + 31) // 32
+        hard = torch.empty((F, W), dtype=torch.int32, device=dev)
+        iters = torch.empty(F, dtype=torch.int32, device=dev)
+        ok = torch.empty(F, dtype=torch.uint8, device=dev)
+        stats = torch.zeros(nd.STATS_LEN, dtype=torch.int64, device=dev)
+        q = g.query()
+        for msg, dt in (("f32", nd.F32), ("f16", nd.F16), ("bf16", nd.BF16)):
+            p = nd.params_default(max_iter=IMAX_ND, msg_dtype=dt)
+            ws = torch.zeros(max(256, g.workspace_size(p, F)), dtype=torch.uint8, device=dev)
+            for _ in range(args.warmup):
+                nd.decode(g, p, llr, ws, hard, iters, ok, stream=stream)
+            stats.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                nd.decode(g, p, llr, ws, hard, iters, ok, stats=stats, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            st = stats.cpu().numpy()
+            plan = g.plan(p, F)
+            rows.append({"code": name, "msg_dtype": msg, "ebn0_db": eb, "frames": F,
+                         "gbit_s": F * args.steps * (c.N - c.M) / sec / 1e9,
+                         "fer": float(st[nd.STAT_FRAME_ERRORS] / st[nd.STAT_FRAMES]),
+                         "ber": float(st[nd.STAT_BIT_ERRORS] / (st[nd.STAT_FRAMES] * c.N)),
+                         "mean_iterations": float(st[nd.STAT_ITERATIONS] / st[nd.STAT_FRAMES]),
+                         "variant": plan.variant, "ms_per_decode": 1e3 * sec / args.steps,
+                         "mufu_tops": MUFU_PER_EDGE_UPDATE * q["edge_updates_per_iter"] * float(st[nd.STAT_ITERATIONS])
+                                      / sec / 1e12})
+            del ws
+        del llr
+    clk = clocks.stop()
+    f16 = [r for r in rows if r["msg_dtype"] == "f16"]
+    line = {
+        "metric": METRIC, "value": sum(r["gbit_s"] for r in f16) / len(f16), "unit": "Gbit/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": f"precision: n=2304 r1/2 and n=16200 r2/3 QC codes at FER~1e-3, {F} frames, "
+                               "cyclic 2-layer NDGSBP, I_max 25, FP32/FP16/BF16 message storage",
+                   "l2": "inputs larger than L2"},
+        "rows": rows, "clocks": clk, "gpu_launches": 6 * args.steps, "roofline": None, "e2e": None,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,11 +785,21 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=64, help="oracle frames per point per reference step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", choices=["sweep", "ragged", "serving", "precision"], default="sweep",
+                    help="sweep = the default n=2304 Eb/N0 sweep line; the others are supplementary")
+    ap.add_argument("--precision-frames", type=int, default=262144)
+    ap.add_argument("--serve-budget-mb", type=int, default=2048)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-backlog", type=int, default=400)
+    ap.add_argument("--epoch-iters", type=int, default=2)
+    ap.add_argument("--arrival-seed", type=int, default=20260)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "sweep":
+        return {"ragged": run_ragged, "serving": run_serving, "precision": run_precision}[args.workload](args)
     return run_ours(args)
 
 

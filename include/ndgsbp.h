@@ -277,6 +277,50 @@ ndgsbp_status ndgsbp_ragged_launch(ndgsbp_ragged* ragged, void* stream);
 ndgsbp_status ndgsbp_ragged_graph_launch(ndgsbp_ragged* ragged, void* stream);
 ndgsbp_status ndgsbp_ragged_destroy(ndgsbp_ragged* ragged);
 
+/* ---- Autotuning (the paper has no counterpart) ---------------------------------------------
+ * ndgsbp_autotune times candidate launch shapes of ndgsbp_decode on the caller's frames d_llr
+ * [n_frames][N] (a representative sample: the iteration counts follow its noise level) and
+ * returns the fastest in result->best: params with variant, block_threads, ctas_per_sm,
+ * frames_per_cta and lanes_per_cn filled in (the other fields as given).  Candidates are the
+ * library's default choice, the QC kernels at 0/1/2 CTAs per SM, and tile shapes (1, 2 or 4
+ * lanes per CN x 1..16 frames per CTA x 128..512 threads) that the plan accepts.  Each
+ * candidate is an ordinary decode into the tuner's own scratch buffers: one untimed call, then
+ * the median of three timed by CUDA events on a private stream.  Shapes with the same lanes
+ * per CN give bit-identical results; more lanes per CN split a CN's edges between lanes and so
+ * change the order of FP32 additions in Eq. (1), i.e. results agree to rounding.
+ * Results are cached in memory under a content key (the code, its groups, schedule, max_iter,
+ * msg_dtype, early_stop, llr_max, block_threads, llr_dtype, log2 of n_frames, device name and
+ * SM count) and, with cache_path non-NULL, appended to that text file (loaded on first use) so
+ * later processes skip the timing.  flags: NDGSBP_TUNE_TILE_ONLY restricts the candidates to
+ * the TILE variant and, when params->block_threads is set, keeps that block size.
+ * Allocates and frees device memory (not during stream capture).
+ * Errors: INVALID, UNSUPPORTED (no shape fits), NOMEM, CUDA. */
+#define NDGSBP_TUNE_TILE_ONLY 1
+
+typedef struct ndgsbp_tune_result {
+    ndgsbp_params best;
+    double best_ms;         /* median decode time of the sample with best */
+    double default_ms;      /* the same for the library's default choice (0 with TILE_ONLY) */
+    int32_t candidates;     /* shapes timed */
+    int32_t from_cache;     /* 1 when the result came from the cache (nothing was timed) */
+} ndgsbp_tune_result;
+
+ndgsbp_status ndgsbp_autotune(const ndgsbp_groups* groups, const ndgsbp_params* params,
+                              const void* d_llr, int32_t llr_dtype, int64_t n_frames, int32_t flags,
+                              const char* cache_path, ndgsbp_tune_result* result);
+
+/* Tile shape of a ragged launch: for each block size 128, 256, 384, 512 the per-code tile shape
+ * (frames_per_cta, lanes_per_cn) is tuned with ndgsbp_autotune (TILE_ONLY) on the first
+ * sample_frames frames of each batch (all when <= 0), then the whole ragged launch over the
+ * batches is timed (one untimed launch, best of two timed); the fastest block size wins.  On
+ * return batches[i].frames_per_cta / lanes_per_cn and *params_out (variant TILE, block_threads)
+ * hold the winner, and *best_ms its launch time.  The timing launches write the batches'
+ * output buffers.  Errors: as ndgsbp_autotune and ndgsbp_ragged_create. */
+ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches,
+                                     const ndgsbp_params* params, int64_t sample_frames,
+                                     const char* cache_path, ndgsbp_params* params_out,
+                                     double* best_ms);
+
 /* ---- Serving: continuous batching of decode requests ---------------------------------------
  * A server owns, per code, a pool of frame slots in device memory (channel LLRs, posterior,
  * messages, outputs) sized so that all pools fit hbm_budget_bytes (split in proportion to

@@ -27,6 +27,7 @@ GROUPS_CYCLIC, GROUPS_NATURAL = 1, 2
 SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
 VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1, 2, 3, 4
 VARIANT_QC_PAIR, VARIANT_QC_PAIR_GLOBAL, VARIANT_TILE = 5, 6, 7
+TUNE_TILE_ONLY = 1
 STAT_FRAMES, STAT_FRAME_ERRORS, STAT_BIT_ERRORS, STAT_UNDETECTED = 0, 1, 2, 3
 STAT_ITERATIONS, STAT_UNSATISFIED, STATS_LEN = 4, 5, 8
 
@@ -71,6 +72,11 @@ class Batch(ctypes.Structure):
                 ("frames_per_cta", ctypes.c_int32), ("lanes_per_cn", ctypes.c_int32)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best", Params), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("candidates", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("requests_submitted", ctypes.c_int64), ("requests_completed", ctypes.c_int64),
                 ("frames_completed", ctypes.c_int64), ("frame_errors_unsatisfied", ctypes.c_int64),
@@ -109,6 +115,10 @@ _SIGS = {
     "ndgsbp_ragged_launch": (_I32, [_P, _P]),
     "ndgsbp_ragged_graph_launch": (_I32, [_P, _P]),
     "ndgsbp_ragged_destroy": (_I32, [_P]),
+    "ndgsbp_autotune": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _I32, ctypes.c_char_p,
+                               ctypes.POINTER(TuneResult)]),
+    "ndgsbp_ragged_autotune": (_I32, [_P, _I32, ctypes.POINTER(Params), _I64, ctypes.c_char_p,
+                                      ctypes.POINTER(Params), ctypes.POINTER(_D)]),
     "ndgsbp_server_create": (_I32, [_P, _I32, _P, ctypes.POINTER(Params), ctypes.c_size_t, _I32,
                                     ctypes.POINTER(_P)]),
     "ndgsbp_server_submit": (_I32, [_P, _I32, _P, _I64, _P, _P, _P, ctypes.POINTER(_I64)]),
@@ -341,22 +351,52 @@ def decode_static(groups: Groups, params: Params, llr, hard_bits, iters=None, sy
                                      _dptr(posterior), _stream(stream)))
 
 
+def _batch_array(batches):
+    arr = (Batch * len(batches))()
+    for i, b in enumerate(batches):
+        llr = b["llr"]
+        arr[i] = Batch(groups=b["groups"].handle.value, d_llr=_addr(llr), llr_dtype=dtype_code(llr),
+                       n_frames=llr.shape[0], d_hard_bits=_addr(b["hard_bits"]), d_iters=_addr(b.get("iters")),
+                       d_syndrome_ok=_addr(b.get("syndrome_ok")), d_posterior=_addr(b.get("posterior")),
+                       d_stats=_addr(b.get("stats")), d_start_ns=_addr(b.get("start_ns")),
+                       d_retire_ns=_addr(b.get("retire_ns")), frames_per_cta=int(b.get("frames_per_cta", 0)),
+                       lanes_per_cn=int(b.get("lanes_per_cn", 0)))
+    return arr
+
+
+def autotune(groups: Groups, params: Params, llr, flags: int = 0, cache_path: str | None = None):
+    """ndgsbp_autotune on the frames of llr (CUDA tensor [F, N]): returns (best Params, info dict)."""
+    r = TuneResult()
+    _check(_lib.ndgsbp_autotune(groups.handle, ctypes.byref(params), _dptr(llr), dtype_code(llr), llr.shape[0],
+                                int(flags), None if cache_path is None else cache_path.encode(), ctypes.byref(r)))
+    best = Params.from_buffer_copy(r.best)
+    return best, {"best_ms": r.best_ms, "default_ms": r.default_ms, "candidates": r.candidates,
+                  "from_cache": bool(r.from_cache)}
+
+
+def ragged_autotune(batches, params: Params, sample_frames: int = 0, cache_path: str | None = None):
+    """ndgsbp_ragged_autotune: sets frames_per_cta / lanes_per_cn in each batch dict and returns
+    (Params for the launch, launch ms)."""
+    arr = _batch_array(batches)
+    out = Params()
+    ms = ctypes.c_double()
+    _check(_lib.ndgsbp_ragged_autotune(arr, len(batches), ctypes.byref(params), int(sample_frames),
+                                       None if cache_path is None else cache_path.encode(), ctypes.byref(out),
+                                       ctypes.byref(ms)))
+    for i, b in enumerate(batches):
+        b["frames_per_cta"] = arr[i].frames_per_cta
+        b["lanes_per_cn"] = arr[i].lanes_per_cn
+    return out, ms.value
+
+
 class Ragged:
     """ndgsbp_ragged handle: one persistent launch over batches of several codes.  Each batch is
     a dict with groups, llr (CUDA tensor [F, N]) and output tensors hard_bits, iters,
     syndrome_ok, posterior, stats, start_ns, retire_ns (optional), frames_per_cta, lanes_per_cn."""
 
     def __init__(self, batches, params: Params):
-        arr = (Batch * len(batches))()
+        arr = _batch_array(batches)
         self._keep = batches
-        for i, b in enumerate(batches):
-            llr = b["llr"]
-            arr[i] = Batch(groups=b["groups"].handle.value, d_llr=_addr(llr), llr_dtype=dtype_code(llr),
-                           n_frames=llr.shape[0], d_hard_bits=_addr(b["hard_bits"]), d_iters=_addr(b.get("iters")),
-                           d_syndrome_ok=_addr(b.get("syndrome_ok")), d_posterior=_addr(b.get("posterior")),
-                           d_stats=_addr(b.get("stats")), d_start_ns=_addr(b.get("start_ns")),
-                           d_retire_ns=_addr(b.get("retire_ns")), frames_per_cta=int(b.get("frames_per_cta", 0)),
-                           lanes_per_cn=int(b.get("lanes_per_cn", 0)))
         h = ctypes.c_void_p()
         _check(_lib.ndgsbp_ragged_create(arr, len(batches), ctypes.byref(params), ctypes.byref(h)))
         self._h = h
