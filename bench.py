@@ -40,7 +40,36 @@ RATE = 0.5
 MUFU_PER_EDGE_UPDATE = 3          # exp2, reciprocal, log2 per edge of Eq. (1)
 MUFU_PER_CLK_PER_SM = 32          # MUFU results per clock per SM sustained on GB300 (one warp
                                   # instruction per clock per SM, the XU-pipe peak ncu normalises to)
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "decode_qc_n2304_traffic.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "qc_decode_kernel_n2304_sweep.md")
+
+
+def channel_seed(point, step, rank, base=CHANNEL_SEED):
+    """Seed of one Eb/N0 point's channel LLRs in one step on one rank: frame-sharded replicas
+    draw disjoint Philox streams (the rank sits in the seed's upper bits)."""
+    return base + point + 1000 * step + (rank << 40)
+
+
+def max_over_ranks(x, device, world):
+    """The slowest rank's time: the whole job is done when the last rank is."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(t, world):
+    """Error and iteration counters summed over the ranks' shards (in place)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
+
+
+def whole_job_gbits(frames_per_rank, world, bits_per_frame, seconds):
+    """Whole-job throughput: the frames of all ranks over the slowest rank's time."""
+    return frames_per_rank * world * bits_per_frame / seconds / 1e9
 
 
 def workload_config(frames):
@@ -119,9 +148,13 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+KERNEL_SOURCES = ("decode_qc.cu", "decode_qc.h", "qc_device.cuh", "device_common.cuh")
+
+
 def kernel_source_hash():
+    """Hash of the sources of the n=2304 decode kernel (qc_decode_kernel)."""
     h = hashlib.sha256()
-    for fn in ("decode.cu", "decode_qc.cu"):
+    for fn in KERNEL_SOURCES:
         p = os.path.join(ROOT, "paper_1202_1060_gb300", "csrc", fn)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
@@ -129,15 +162,23 @@ def kernel_source_hash():
 
 
 def profiled_traffic(kernel_name):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    """DRAM bytes per full-size launch from the committed ncu summary (lines "key: value"), if it
+    was taken on the current kernel source; else None."""
+    rec = {}
     try:
         with open(PROFILE_TRAFFIC) as f:
-            rec = json.load(f)
-    except (OSError, ValueError):
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    rec[k.strip()] = v.strip().strip("`")
+    except OSError:
         return None, None
     if rec.get("source_hash") != kernel_source_hash() or rec.get("kernel") != kernel_name:
         return None, rec
-    return rec.get("dram_bytes_per_launch_full"), rec
+    try:
+        return float(rec["dram_bytes_per_launch_full"]), rec
+    except (KeyError, ValueError):
+        return None, rec
 
 
 # ------------------------------------------------------------------------------------------
@@ -249,7 +290,7 @@ def run_ours(args):
 
     def step(s, timing=None, latency=False):
         for i, eb in enumerate(EBN0):
-            seed = CHANNEL_SEED + i + 1000 * s + (rank << 40)
+            seed = channel_seed(i, s, rank)
             nd.awgn_llr(code, F, eb, RATE, seed, llr, stream=stream)
             if timing is not None:
                 timing.append(torch.cuda.Event(enable_timing=True))
@@ -288,12 +329,10 @@ def run_ours(args):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     clk = clocks.stop()
     dec_ms = [dec_events[2 * j].elapsed_time(dec_events[2 * j + 1]) for j in range(len(dec_events) // 2)]
-    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_max = float(t.item())
+    elapsed_max = max_over_ranks(elapsed, dev, world)
     frames_total = F * len(EBN0) * args.steps * world
-    value = frames_total * 1152 / elapsed_max / 1e9
+    value = whole_job_gbits(F * len(EBN0) * args.steps, world, 1152, elapsed_max)
+    sum_over_ranks(stats, world)
 
     st = stats.cpu().numpy()
     frames_done = int(st[:, nd.STAT_FRAMES].sum())
@@ -316,7 +355,9 @@ def run_ours(args):
     peak_clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = MUFU_PER_CLK_PER_SM * sms * peak_clock_mhz * 1e6 / 1e12
     kname = {nd.VARIANT_QC: "qc_decode_kernel", nd.VARIANT_QC_GLOBAL: "qc_decode_kernel",
-             nd.VARIANT_QC_PAIR: "qc_pair_kernel", nd.VARIANT_QC_PAIR_GLOBAL: "qc_pair_kernel"}.get(plan.variant,
+             nd.VARIANT_QC_PAIR: "qc_pair_kernel", nd.VARIANT_QC_PAIR_GLOBAL: "qc_pair_kernel",
+             nd.VARIANT_QC_FRAMES2: "qc_frames2_kernel", nd.VARIANT_QC_FRAMES2_GLOBAL: "qc_frames2_kernel",
+             nd.VARIANT_TILE: "tile_decode_kernel"}.get(plan.variant,
                                                                                             "decode_kernel")
     traffic, traffic_rec = profiled_traffic(kname)
     roofline = {
@@ -385,7 +426,7 @@ def run_e2e(args, nd, torch, code, c, groups, params, F, W, dev, rank, world):
     host_llr = []
     tmp = torch.empty((F, c.N), dtype=torch.float32, device=dev)
     for i, eb in enumerate(EBN0):
-        nd.awgn_llr(code, F, eb, RATE, CHANNEL_SEED + 77 + i + (rank << 40), tmp)
+        nd.awgn_llr(code, F, eb, RATE, channel_seed(i, 0, rank, base=CHANNEL_SEED + 77), tmp)
         h = torch.empty((F, c.N), dtype=torch.float32, pin_memory=True)
         h.copy_(tmp)
         host_llr.append(h)
@@ -430,11 +471,7 @@ def run_e2e(args, nd, torch, code, c, groups, params, F, W, dev, rank, world):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    dt = time.perf_counter() - t0
-    t = torch.tensor([dt], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dt = float(t.item())
+    dt = max_over_ranks(time.perf_counter() - t0, dev, world)
     frames = F * n_pts * args.steps * world
     h2d = n_pts * F * c.N * 4
     d2h = n_pts * F * (W * 4 + 4 + 1)
@@ -447,10 +484,14 @@ def run_e2e(args, nd, torch, code, c, groups, params, F, W, dev, rank, world):
 # ------------------------------------------------------------------------------------------
 # supplementary workloads: ragged multi-code batches, serving, reduced-precision messages
 # ------------------------------------------------------------------------------------------
-# Eb/N0 of each code's FER ~ 1e-3 point (FP32 messages, cyclic 2-layer NDGSBP), from a GPU
-# pre-sweep in 0.1 dB steps over 262,144 frames per point (16200: 131,072)
-FER1E3_EBN0 = {"qc_n2304_r12": 1.8, "qc_n16200_r23": 2.0, "qc_n576_r12": 2.9, "qc_n1152_r23": 3.0,
-               "qc_n2304_r34": 3.2, "qc_n8192_r2732": 3.6}
+# Eb/N0 of each code's FER ~ 1e-3 point (FP32 messages, cyclic 2-layer NDGSBP, I_max 25 for the
+# n=2304 r1/2 and n=16200 codes, 30 for the others), interpolated between the two points of a
+# GPU pre-sweep in 0.1 dB steps (262,144 frames per point, 131,072 for n=16200) that bracket
+# FER = 1e-3: 2304 r1/2 1.7/1.8 dB (1.4e-3/5.4e-4), 16200 1.8/1.9 (4.6e-3/1.2e-4), 576
+# 2.6/2.7 (1.2e-3/8.4e-4), 1152 2.7/2.8 (1.6e-3/8.2e-4), 2304 r3/4 2.8/2.9 (2.0e-3/6.4e-4),
+# 8192 3.3/3.4 (1.3e-3/1.6e-4)
+FER1E3_EBN0 = {"qc_n2304_r12": 1.75, "qc_n16200_r23": 1.85, "qc_n576_r12": 2.65, "qc_n1152_r23": 2.75,
+               "qc_n2304_r34": 2.85, "qc_n8192_r2732": 3.3}
 MIX4 = [("qc_n576_r12", 0.4), ("qc_n1152_r23", 0.3), ("qc_n2304_r34", 0.2), ("qc_n8192_r2732", 0.1)]
 RAGGED_FRAMES = 200000
 
@@ -582,7 +623,7 @@ def run_ragged(args):
         "decode_only_gbit_s": bits * args.steps / dec_s / 1e9,
         "plain_fp32_single_code_gbit_s": bits / plain_s / 1e9,
         "speedup_vs_plain_fp32": (bits * args.steps / dec_s) / (bits / plain_s),
-        "per_code": per_code, "tuned": {"block_threads": params.block_threads, "tile_launch_ms": tuned_ms,
+        "per_code": per_code, "tuned": {"block_threads": params.block_threads, "ctas_per_sm": params.ctas_per_sm, "tile_launch_ms": tuned_ms,
                                         "tuning_s": tune_s, "tiles": n_tiles, "plan": plan},
         "clocks": clk, "gpu_launches": 5 * args.steps,
         "roofline": _mufu_roofline(peaks, kind, sms, mufu * args.steps, dec_s, "tile_decode_kernel", args.steps),
@@ -635,11 +676,15 @@ def run_serving(args):
     backlog = [draw_request() for _ in range(args.serve_backlog)]
     for k, llr in backlog[:32]:
         srv.submit(k, llr).wait(600000)
+    st_a = srv.stats()
     t0 = time.perf_counter()
     reqs = [srv.submit(k, llr) for k, llr in backlog]
     for r in reqs:
         r.wait(600000)
     cap_s = time.perf_counter() - t0
+    st_b = srv.stats()
+    cap_split = {k: st_b[k] - st_a[k] for k in ("epochs", "admit_seconds", "device_seconds", "harvest_seconds",
+                                                "busy_seconds", "iterations", "frames_completed")}
     cap_frames = sum(llr.shape[0] for _, llr in backlog)
     cap_bits = sum(llr.shape[0] * codes[k]["K"] for k, llr in backlog)
     capacity = cap_frames / cap_s
@@ -680,8 +725,38 @@ def run_serving(args):
     clk = clocks.stop()
     stats = srv.stats()
     srv.close()
+    # the plain batched path on the same frames: each code's frames of the backlog in one
+    # device-resident batch, decoded by the default single-code launch (FP32 and FP16 messages)
+    plain = {}
+    for mname, mdt in (("f32", nd.F32), ("f16", nd.F16)):
+        pp = nd.params_default(max_iter=30, msg_dtype=mdt)
+        jobs = []
+        for k, d in enumerate(codes):
+            frames = [llr for kk, llr in backlog if kk == k]
+            if not frames:
+                continue
+            x = torch.from_numpy(np.concatenate(frames)).to(dev)
+            F = x.shape[0]
+            W = (d["c"].N + 31) // 32
+            jobs.append((d, x, torch.zeros(max(256, d["groups"].workspace_size(pp, F)), dtype=torch.uint8, device=dev),
+                         torch.empty((F, W), dtype=torch.int32, device=dev)))
+        for _ in range(2):
+            for d, x, w, hb in jobs:
+                nd.decode_plain(d["groups"], pp, x, w, hb)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for d, x, w, hb in jobs:
+            nd.decode_plain(d["groups"], pp, x, w, hb)
+        e1.record()
+        torch.cuda.synchronize()
+        plain[mname] = cap_bits / (e0.elapsed_time(e1) / 1e3) / 1e9
+        del jobs
     sat = {"frames_per_s": capacity, "gbit_s": cap_bits / cap_s / 1e9, "requests": len(backlog),
-           "seconds": cap_s}
+           "seconds": cap_s, "server_time_split": cap_split,
+           "plain_batched_gbit_s": plain,
+           "what": "saturated backlog through the server (host buffers in and out) vs the same frames decoded "
+                   "as device-resident per-code batches by the default single-code launch"}
     line = {
         "metric": METRIC, "value": sat["gbit_s"], "unit": "Gbit/s", "n_gpus": 1, "steps": len(loads),
         "warmup": 32, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -781,7 +856,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=FRAMES, help="frames per Eb/N0 point per GPU")
     ap.add_argument("--variant", type=int, default=0, help="decode variant (0 = library choice)")
-    ap.add_argument("--cpu-frames", type=int, default=512, help="oracle sample per Eb/N0 point")
+    ap.add_argument("--cpu-frames", type=int, default=4096, help="oracle sample per Eb/N0 point")
     ap.add_argument("--ref-frames", type=int, default=64, help="oracle frames per point per reference step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -60,7 +60,7 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_SCHEDULE_FLOOD 1  /* one group holding every CN: standard (flooding) BP */
 
 /* decode kernel variants */
-#define NDGSBP_VARIANT_AUTO 0    /* autotuned choice when cached, else the heuristic below */
+#define NDGSBP_VARIANT_AUTO 0    /* the library's choice (ndgsbp_autotune picks by measurement) */
 #define NDGSBP_VARIANT_SMEM 1    /* edge messages resident in shared memory (small codes) */
 #define NDGSBP_VARIANT_GLOBAL 2  /* edge messages in per-CTA global-memory slots */
 #define NDGSBP_VARIANT_QC 3      /* layered QC kernel: circulant index arithmetic, no tables */
@@ -68,6 +68,8 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_VARIANT_QC_PAIR 5   /* layered QC kernel, two CNs per thread, packed FP32 arithmetic */
 #define NDGSBP_VARIANT_QC_PAIR_GLOBAL 6 /* the pair kernel with messages in global-memory slots */
 #define NDGSBP_VARIANT_TILE 7      /* tile kernel: any QC window, degree <= 32, several frames per CTA */
+#define NDGSBP_VARIANT_QC_FRAMES2 8 /* layered QC kernel, two frames per thread, packed FP32 arithmetic */
+#define NDGSBP_VARIANT_QC_FRAMES2_GLOBAL 9 /* the two-frame kernel with messages in global-memory slots */
 
 /* stats counters accumulated by ndgsbp_decode_ex (uint64 each) */
 #define NDGSBP_STAT_FRAMES 0
@@ -261,8 +263,10 @@ typedef struct ndgsbp_ragged ndgsbp_ragged;
 /* Plan one persistent tile-kernel launch over n_batches <= 8 batches of different codes: each
  * code keeps its own schedule (Sec. II-C Steps 2-4 with its groups) and per-frame early stop;
  * CTAs take tiles of frames of any code from one list (largest codes first) and refill frame
- * slots as frames retire.  params gives max_iter, msg_dtype, llr_max, early_stop and
- * block_threads (shared by every code).  The batches' buffers are recorded in the handle: later
+ * slots as frames retire.  params gives max_iter, msg_dtype, llr_max, early_stop, block_threads
+ * (shared by every code) and ctas_per_sm, the residency target k: every CTA's shared memory is
+ * capped at 1/k of the SM's, and a code whose messages do not fit under the cap keeps them in
+ * global memory (0 = 2 CTAs per SM when every code fits, else 1).  The batches' buffers are recorded in the handle: later
  * launches reuse them, so refill their contents rather than moving them.  Allocates the tile
  * list and the launch's workspace (owned by the handle; call before any stream capture).
  * Errors: INVALID, UNSUPPORTED (a code that is not QC in whole layers, degree > 32), CUDA, NOMEM. */
@@ -311,10 +315,11 @@ ndgsbp_status ndgsbp_autotune(const ndgsbp_groups* groups, const ndgsbp_params* 
 
 /* Tile shape of a ragged launch: for each block size 128, 256, 384, 512 the per-code tile shape
  * (frames_per_cta, lanes_per_cn) is tuned with ndgsbp_autotune (TILE_ONLY) on the first
- * sample_frames frames of each batch (all when <= 0), then the whole ragged launch over the
- * batches is timed (one untimed launch, best of two timed); the fastest block size wins.  On
- * return batches[i].frames_per_cta / lanes_per_cn and *params_out (variant TILE, block_threads)
- * hold the winner, and *best_ms its launch time.  The timing launches write the batches'
+ * sample_frames frames of each batch (all when <= 0); then the whole ragged launch over the
+ * batches is timed (one untimed launch, best of two timed) at 1, 2, 3 and 4 CTAs per SM, with
+ * frame slots capped to fit; the fastest (block size, residency) wins.  On return
+ * batches[i].frames_per_cta / lanes_per_cn and *params_out (variant TILE, block_threads,
+ * ctas_per_sm) hold the winner, and *best_ms its launch time.  The timing launches write the batches'
  * output buffers.  Errors: as ndgsbp_autotune and ndgsbp_ragged_create. */
 ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches,
                                      const ndgsbp_params* params, int64_t sample_frames,
@@ -322,9 +327,10 @@ ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches,
                                      double* best_ms);
 
 /* ---- Serving: continuous batching of decode requests ---------------------------------------
- * A server owns, per code, a pool of frame slots in device memory (channel LLRs, posterior,
- * messages, outputs) sized so that all pools fit hbm_budget_bytes (split in proportion to
- * weights; NULL = equal shares).  A host thread of the library admits the frames of queued
+ * A server owns, per code, a pool of frame slots (posterior and messages of running frames in
+ * device memory; LLR staging and outputs in pinned host memory that the kernel reads and writes
+ * directly) sized so that all pools fit hbm_budget_bytes (split in proportion to weights; NULL =
+ * equal shares).  A host thread of the library admits the frames of queued
  * requests into free slots in arrival order, runs epoch launches of the tile kernel in which
  * every running frame advances by at most epoch_iters iterations (its state stays in device
  * memory between epochs), and retires frames whose syndrome is zero (Step 4 b) or that reached
@@ -342,6 +348,9 @@ typedef struct ndgsbp_server_stats {
     int64_t iterations;          /* frame-iterations run */
     double busy_seconds;         /* host time with at least one frame on the device */
     int64_t slots_total, slots_in_use;
+    double admit_seconds;        /* host time admitting frames (LLR staging, admit and tile lists) */
+    double device_seconds;       /* host time from an epoch's first enqueue to its stream sync */
+    double harvest_seconds;      /* host time copying retired frames' outputs to their requests */
 } ndgsbp_server_stats;
 
 ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_codes,

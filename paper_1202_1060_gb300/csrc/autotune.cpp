@@ -169,7 +169,9 @@ ndgsbp_status ndgsbp_autotune(const ndgsbp_groups* groups, const ndgsbp_params* 
         for (int cps : {0, 1, 2}) {
             add(NDGSBP_VARIANT_QC, 0, cps, 0, 0);
             add(NDGSBP_VARIANT_QC_PAIR, 0, cps, 0, 0);
+            add(NDGSBP_VARIANT_QC_FRAMES2, 0, cps, 0, 0);
         }
+        for (int cps : {0, 2, 3, 4}) add(NDGSBP_VARIANT_QC_FRAMES2_GLOBAL, 0, cps, 0, 0);
     }
     const int maxdeg = g.qc.ok ? g.qc.max_deg : 0;
     const int threads_list[] = {128, 256, 384, 512};
@@ -269,29 +271,33 @@ ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches, c
             b[i].lanes_per_cn = r.best.lanes_per_cn;
         }
         if (st || b.empty()) continue;
-        // the whole launch at this block size
-        ndgsbp_ragged* rg = nullptr;
-        if (ndgsbp_ragged_create(b.data(), n_batches, &p, &rg) != NDGSBP_OK) {
-            clear_error();
-            continue;
-        }
-        std::vector<float> t;
-        for (int rep = 0; rep < 3 && !st; ++rep) {
-            cudaEventRecord(e0, stream);
-            st = ndgsbp_ragged_launch(rg, stream);
-            cudaEventRecord(e1, stream);
-            if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = fail(NDGSBP_ERR_CUDA, "ragged_autotune: launch failed");
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) t.push_back(ms);
-        }
-        ndgsbp_ragged_destroy(rg);
-        if (st) break;
-        const double ms = std::min(t[0], t[1]);
-        if (best < 0.0 || ms < best) {
-            best = ms;
-            best_b = b;
-            best_p = p;
+        // the whole launch at this block size and each residency target
+        for (int k = 1; k <= 4 && !st; ++k) {
+            p.ctas_per_sm = k;
+            ndgsbp_ragged* rg = nullptr;
+            if (ndgsbp_ragged_create(b.data(), n_batches, &p, &rg) != NDGSBP_OK) {
+                clear_error();
+                continue;
+            }
+            std::vector<float> t;
+            for (int rep = 0; rep < 3 && !st; ++rep) {
+                cudaEventRecord(e0, stream);
+                st = ndgsbp_ragged_launch(rg, stream);
+                cudaEventRecord(e1, stream);
+                if (!st && cudaEventSynchronize(e1) != cudaSuccess)
+                    st = fail(NDGSBP_ERR_CUDA, "ragged_autotune: launch failed");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) t.push_back(ms);
+            }
+            ndgsbp_ragged_destroy(rg);
+            if (st) break;
+            const double ms = std::min(t[0], t[1]);
+            if (best < 0.0 || ms < best) {
+                best = ms;
+                best_b = b;
+                best_p = p;
+            }
         }
     }
     if (e1) cudaEventDestroy(e1);

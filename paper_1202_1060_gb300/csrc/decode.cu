@@ -362,7 +362,7 @@ static ndgsbp_status validate_params(const ndgsbp_params* p) {
         return fail(NDGSBP_ERR_INVALID, "frames_per_cta must be in [0, 16]");
     if (p->lanes_per_cn != 0 && p->lanes_per_cn != 1 && p->lanes_per_cn != 2 && p->lanes_per_cn != 4)
         return fail(NDGSBP_ERR_INVALID, "lanes_per_cn must be 0, 1, 2 or 4");
-    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_TILE)
+    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_FRAMES2_GLOBAL)
         return fail(NDGSBP_ERR_INVALID, "unknown variant %d", p->variant);
     return NDGSBP_OK;
 }
@@ -390,6 +390,50 @@ static ndgsbp_status finish_grid(const void* fn, int threads, size_t smem, const
     return NDGSBP_OK;
 }
 
+// Two-frames-per-thread QC kernel: interleaved posteriors and messages, so every per-frame
+// buffer doubles; persistent CTAs take frames two at a time.
+static ndgsbp_status make_qc_frames2_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
+                                          const QcLayout& Q, int maxdc, bool spec, bool force_global,
+                                          const DeviceInfo& di, Plan& plan, bool* ok, bool allow_upload) {
+    if (!spec || maxdc > 16) return NDGSBP_OK;
+    const int active = Q.window * Q.Z;
+    const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
+    if (threads < active || threads > qc_frames2_max_threads(maxdc)) return NDGSBP_OK;
+    const size_t budget = static_cast<size_t>(di.smem_optin) - 96;
+    const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 8);
+    const size_t m_bytes = align16(static_cast<size_t>(Q.msg_slots) * 2 * msg_size(p->msg_dtype));
+    const size_t t_bytes = qc_table_bytes(Q);
+    if (p_bytes + t_bytes > budget) return NDGSBP_OK;
+    const bool msg_smem = !force_global && p_bytes + m_bytes + t_bytes <= budget;
+    const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
+    QcKernelFn fn = pick_qc_frames2_kernel(p->msg_dtype, maxdc, msg_smem);
+    if (!fn) return NDGSBP_OK;
+    int per_sm = 0;
+    int64_t grid = 0;
+    ndgsbp_status st = finish_grid(reinterpret_cast<const void*>(fn), threads, smem, p, (n_frames + 1) / 2, di, per_sm,
+                                   grid);
+    if (st) return st;
+    st = device_qc(g, flood, plan.Q, plan.DQ, allow_upload);
+    if (st) return st;
+    plan.qc = true;
+    plan.qfn = fn;
+    plan.msg_smem = msg_smem;
+    ndgsbp_plan& o = plan.pub;
+    o.variant = msg_smem ? NDGSBP_VARIANT_QC_FRAMES2 : NDGSBP_VARIANT_QC_FRAMES2_GLOBAL;
+    o.block_threads = threads;
+    o.grid = static_cast<int32_t>(grid);
+    o.ctas_per_sm = per_sm;
+    o.max_row_degree = maxdc;
+    o.delta_in_smem = 0;
+    o.smem_bytes = static_cast<int64_t>(smem);
+    o.workspace_bytes = static_cast<int64_t>(
+        kHeaderBytes + (msg_smem ? 0 : align256(static_cast<size_t>(grid) * Q.msg_slots * 2 * msg_size(p->msg_dtype))));
+    o.stored_edges = Q.msg_slots;
+    o.edge_updates_per_iter = flood ? g.code->E : g.edge_updates;
+    *ok = true;
+    return NDGSBP_OK;
+}
+
 // Layered QC kernel plan, when the grouping is made of whole layers and a window fits a CTA.
 // QC / QC_GLOBAL (and AUTO) run the single-CN kernel, QC_PAIR / QC_PAIR_GLOBAL the pair kernel.
 static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
@@ -402,7 +446,11 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     const bool spec = qc_degrees_specialised(Q, maxdc);
     const bool want_single = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL;
     const bool want_pair = p->variant == NDGSBP_VARIANT_QC_PAIR || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL;
-    const bool force_global = p->variant == NDGSBP_VARIANT_QC_GLOBAL || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL;
+    const bool want_f2 = p->variant == NDGSBP_VARIANT_QC_FRAMES2 || p->variant == NDGSBP_VARIANT_QC_FRAMES2_GLOBAL;
+    const bool force_global = p->variant == NDGSBP_VARIANT_QC_GLOBAL || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL ||
+                              p->variant == NDGSBP_VARIANT_QC_FRAMES2_GLOBAL;
+    if (want_f2) return make_qc_frames2_plan(g, p, n_frames, flood, Q, maxdc, spec, force_global, di, plan, ok,
+                                             allow_upload);
     const int active_pair = Q.window * (Q.Z / 2);
     const bool pair_ok = spec && Q.Z % 2 == 0 && (p->block_threads ? p->block_threads : (active_pair + 31) / 32 * 32) <=
                                                       qc_pair_max_threads(maxdc);

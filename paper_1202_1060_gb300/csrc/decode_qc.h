@@ -21,6 +21,9 @@ struct QcArgs {
 typedef void (*QcKernelFn)(const QcArgs);
 
 QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair);
+// Two frames per thread (decode_qc2.cu); degree-specialised codes with MAXDC 8 or 16 only.
+QcKernelFn pick_qc_frames2_kernel(int msg_dtype, int maxdc, bool msg_smem);
+int qc_frames2_max_threads(int maxdc);
 bool qc_degrees_specialised(const QcLayout& Q, int maxdc);
 int qc_pair_max_threads(int maxdc);
 size_t qc_table_bytes(const QcLayout& Q);

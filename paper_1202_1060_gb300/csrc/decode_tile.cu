@@ -359,7 +359,10 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                             if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]);
                         }
                     write_frame_outputs(r, P, f, it, sh.unsat[s] ? 1 : 0, &sh.err);
-                    if (SERVE && tid == 0) C.state_flag[f] = kSlotDone;
+                    if (SERVE && tid == 0) {
+                        C.state_flag[f] = kSlotDone;
+                        if (C.done_list) C.done_list[atomicAdd(C.done_count, 1)] = static_cast<int>(f);
+                    }
                 } else {
                     save_frame<MsgT>(C, base, f);
                     if (tid == 0) C.state_iter[f] = it;

@@ -31,6 +31,8 @@ struct TileCode {
     float* state_P;       // [pool][N] posteriors of running frames
     void* state_msgs;     // [pool][msg_slots] messages of running frames
     int epoch_iters;      // iterations a frame may run in one launch before its state is saved
+    int* done_list;       // [pool] slots whose frame retired in this launch (serving), or null
+    int* done_count;      // number of entries in done_list (zeroed before the launch)
 };
 
 constexpr int kSlotFree = 0, kSlotNew = 1, kSlotRunning = 2, kSlotDone = 3;

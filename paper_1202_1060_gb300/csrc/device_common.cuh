@@ -130,15 +130,16 @@ __device__ __forceinline__ long long next_frame(const RunArgs& r, long long* slo
 }
 
 // Frame epilogue: hard decisions (packed), optional posterior, per-frame outputs and the fused
-// statistics (errors against the transmitted word, iteration histogram, timestamps).
+// statistics (errors against the transmitted word, iteration histogram, timestamps).  The
+// frame's posterior of VN n is P[n * pstride] (pstride 2 when two frames are interleaved).
 __device__ __forceinline__ void write_frame_outputs(const RunArgs& a, const float* __restrict__ P, long long f,
-                                                    int iters, int unsat, unsigned* s_err) {
+                                                    int iters, int unsat, unsigned* s_err, int pstride = 1) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int W = a.W;
     unsigned err = 0u;
     for (int w = warp; w < W; w += nw) {
         const int n = 32 * w + lane;
-        const bool bit = (n < a.N) && (P[n] < 0.f);
+        const bool bit = (n < a.N) && (P[n * pstride] < 0.f);
         const unsigned word = __ballot_sync(0xffffffffu, bit);
         if (lane == 0) {
             a.hard_bits[f * W + w] = word;
@@ -149,7 +150,7 @@ __device__ __forceinline__ void write_frame_outputs(const RunArgs& a, const floa
         }
     }
     if (a.posterior)
-        for (int n = tid; n < a.N; n += nt) a.posterior[f * a.N + n] = P[n];
+        for (int n = tid; n < a.N; n += nt) a.posterior[f * a.N + n] = P[n * pstride];
     if (a.stats && lane == 0 && err) atomicAdd(s_err, err);
     __syncthreads();
     if (tid == 0) {

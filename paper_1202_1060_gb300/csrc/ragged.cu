@@ -62,11 +62,12 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
     const int ms = params->msg_dtype == NDGSBP_F32 ? 4 : 2;
     TileKernelFn fn = pick_tile_kernel(params->msg_dtype);
     if (!fn) return fail(NDGSBP_ERR_INVALID, "ragged_create: msg_dtype must be F32, F16 or BF16");
-    int dev = 0, sms = 0, optin = 0;
+    int dev = 0, sms = 0, optin = 0, smem_sm = 0, reserved = 0;
     RAGGED_TRY(cudaGetDevice(&dev));
     RAGGED_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     RAGGED_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t budget = static_cast<size_t>(optin) - 256;
+    RAGGED_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    RAGGED_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
     auto* h = new (std::nothrow) ndgsbp_ragged;
     if (!h) return fail(NDGSBP_ERR_NOMEM, "out of host memory");
     h->device = dev;
@@ -126,6 +127,21 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         delete h;
         return fail(NDGSBP_ERR_INVALID, "ragged_create: block_threads must be a multiple of 32 up to 1024");
     }
+    // Shared memory per CTA: one launch reserves the same amount for every code, so a code with
+    // large frame slots would hold every CTA to its size.  A residency target of k CTAs per SM
+    // caps each CTA at 1/k of the SM's shared memory; a code whose messages do not fit under the
+    // cap keeps them in global memory.  Default: 2 CTAs per SM when every code fits, else 1.
+    auto cap_for = [&](int k) {
+        const size_t per = static_cast<size_t>(smem_sm) / k - static_cast<size_t>(reserved) - 1024;
+        return std::min(static_cast<size_t>(optin) - 256, per) & ~static_cast<size_t>(15);
+    };
+    auto fits = [&](size_t cap) {
+        for (int i = 0; i < n_batches; ++i)
+            if (table_max + cp[i].p_bytes + cp[i].d_bytes > cap) return false;
+        return true;
+    };
+    const int target = params->ctas_per_sm > 0 ? params->ctas_per_sm : (fits(cap_for(2)) ? 2 : 1);
+    const size_t budget = cap_for(target);
     // slots and shared memory per code; the launch reserves the largest
     size_t smem = table_max;
     size_t ws = 256;
@@ -136,7 +152,8 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         const size_t slot = c.p_bytes + (msg_smem ? c.m_bytes : 0) + c.d_bytes;
         if (table_max + slot > budget) {
             delete h;
-            return fail(NDGSBP_ERR_UNSUPPORTED, "ragged_create: batch %d does not fit in shared memory", i);
+            return fail(NDGSBP_ERR_UNSUPPORTED, "ragged_create: batch %d does not fit in shared memory at %d CTAs per SM",
+                        i, target);
         }
         const int max_slots = static_cast<int>(std::min<size_t>(16, (budget - table_max) / slot));
         const int want = batches[i].frames_per_cta ? batches[i].frames_per_cta
@@ -196,7 +213,7 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         delete h;
         return fail(NDGSBP_ERR_UNSUPPORTED, "ragged_create: the launch does not fit on an SM");
     }
-    if (params->ctas_per_sm > 0) per_sm = std::min(per_sm, params->ctas_per_sm);
+    per_sm = std::min(per_sm, target);
     // tiles: codes with the most work per tile first, so long tiles do not trail the launch
     std::vector<int> order(n_batches);
     for (int i = 0; i < n_batches; ++i) order[i] = i;

@@ -1,24 +1,32 @@
 // Serving: continuous batching of decode requests over device-resident frame slots.
 //
-// Per code the server owns a pool of slots in device memory: channel LLRs, the decoding state
-// of a running frame (posterior, messages, iteration count, status) and its outputs.  A worker
-// thread repeats one epoch:
+// Per code the server owns a pool of slots.  The decoding state of a running frame (posterior,
+// messages, iteration count, status flag) lives in device memory; its channel LLRs are staged in
+// pinned host memory that the kernel reads when the frame starts, and its outputs go straight
+// to pinned host memory that the kernel writes when the frame retires.  A worker thread repeats
+// one epoch:
 //   1. admit: frames of queued requests (arrival order) take free slots of their code's pool;
-//      their LLRs are copied in and their slots marked new;
-//   2. run: one launch of the tile kernel in serving mode over every pool; each running frame
-//      advances by at most epoch_iters iterations, then retires (zero syndrome or max_iter,
-//      outputs written) or is parked with its state in device memory;
-//   3. harvest: statuses and outputs come back; retired frames free their slots and are copied
-//      into their requests' buffers; a request completes when all its frames have retired.
-// Frames of different requests and codes share every launch, and new requests join as soon
-// as slots free up.  Each frame is computed exactly as by the tile kernel in a plain decode.
+//      their LLRs are copied to the slots' staging and the slots are listed for a small admit
+//      kernel that marks them new;
+//   2. run: one launch of the tile kernel in serving mode over the tiles of occupied slots of
+//      every pool; each running frame advances by at most epoch_iters iterations, then retires
+//      (zero syndrome or max_iter: outputs written, slot listed as done) or is parked with its
+//      state in device memory;
+//   3. harvest: the done lists come back (a count per pool); retired frames free their slots
+//      and their outputs are copied into their requests' buffers; a request completes when all
+//      its frames have retired.
+// Frames of different requests and codes share every launch, and new requests join as soon as
+// slots free up.  Each frame is computed exactly as by the tile kernel in a plain decode.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -37,6 +45,20 @@ namespace {
 
 constexpr int kMaxPoolSlots = 16384;
 
+struct AdmitArgs {
+    int* flags[kTileMaxCodes];
+    const int* list;   // entries pool << 24 | slot
+    int n;
+};
+
+// Marks the admitted slots new (their LLRs are already staged).
+__global__ void admit_kernel(const AdmitArgs a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const int e = a.list[i];
+        a.flags[e >> 24][e & 0xffffff] = kSlotNew;
+    }
+}
+
 struct Request {
     int64_t ticket = 0;
     int code = 0;
@@ -54,28 +76,29 @@ struct Pool {
     const Groups* g = nullptr;
     const QcLayout* Q = nullptr;
     const DeviceQc* D = nullptr;
-    int N = 0, W = 0, slots = 0, tpc = 1, le = 1, ds = 1, cta_slots = 1;
-    size_t slot_bytes = 0, p_bytes = 0, m_bytes = 0;
-    // device
-    float* llr = nullptr;
-    uint32_t* hard = nullptr;
-    int32_t* iters = nullptr;
-    uint8_t* ok = nullptr;
+    int N = 0, W = 0, slots = 0, tpc = 1, le = 1, ds = 1, cta_slots = 1, tile_frames = 1;
+    size_t slot_bytes = 0, p_bytes = 0, m_bytes = 0, d_bytes = 0;
+    // device: state of running frames
     int* flag = nullptr;
     int* st_iter = nullptr;
     float* st_P = nullptr;
     void* st_msgs = nullptr;
-    // pinned host
-    float* h_stage = nullptr;     // LLRs of frames admitted this epoch, by slot
-    int* h_new = nullptr;         // kSlotNew for every slot (source of flag uploads)
-    int* h_flag = nullptr;
+    // pinned host, mapped into the device: LLR staging (read by the kernel), outputs and the
+    // done list (written by the kernel)
+    float* h_stage = nullptr;
     uint32_t* h_hard = nullptr;
     int32_t* h_iters = nullptr;
     uint8_t* h_ok = nullptr;
-    std::vector<int> free_slots;
+    int* h_done = nullptr;
+    std::vector<int> free_slots;   // kept in descending order: the lowest free slot is taken first
     std::vector<std::pair<Request*, int64_t>> owner;
-    std::vector<int> admitted_now;
 };
+
+template <typename T>
+T* device_view(T* host) {
+    void* d = nullptr;
+    return cudaHostGetDevicePointer(&d, host, 0) == cudaSuccess ? static_cast<T*>(d) : nullptr;
+}
 
 }  // namespace
 
@@ -86,9 +109,14 @@ struct ndgsbp_server {
     int device = 0;
     TileArgs args{};
     TileKernelFn fn = nullptr;
-    int grid = 0, threads = 0;
+    int max_grid = 0, threads = 0;
     size_t smem = 0;
     int4* d_tiles = nullptr;
+    int4* h_tiles = nullptr;
+    int* d_admit = nullptr;
+    int* h_admit = nullptr;
+    int* d_done_count = nullptr;
+    int* h_done_count = nullptr;
     unsigned long long* d_counter = nullptr;
     cudaStream_t stream = nullptr;
     std::mutex mu;
@@ -119,22 +147,22 @@ ndgsbp_server::~ndgsbp_server() {
     if (cudaGetDevice(&cur) == cudaSuccess && cudaSetDevice(device) == cudaSuccess) {
         if (stream) cudaStreamSynchronize(stream);
         for (Pool& p : pools) {
-            cudaFree(p.llr);
-            cudaFree(p.hard);
-            cudaFree(p.iters);
-            cudaFree(p.ok);
             cudaFree(p.flag);
             cudaFree(p.st_iter);
             cudaFree(p.st_P);
             cudaFree(p.st_msgs);
             cudaFreeHost(p.h_stage);
-            cudaFreeHost(p.h_new);
-            cudaFreeHost(p.h_flag);
             cudaFreeHost(p.h_hard);
             cudaFreeHost(p.h_iters);
             cudaFreeHost(p.h_ok);
+            cudaFreeHost(p.h_done);
         }
         cudaFree(d_tiles);
+        cudaFreeHost(h_tiles);
+        cudaFree(d_admit);
+        cudaFreeHost(h_admit);
+        cudaFree(d_done_count);
+        cudaFreeHost(h_done_count);
         cudaFree(d_counter);
         if (stream) cudaStreamDestroy(stream);
         cudaSetDevice(cur);
@@ -155,10 +183,11 @@ ndgsbp_server::~ndgsbp_server() {
 
 // One epoch; false on a CUDA error (recorded, the worker stops).
 bool ndgsbp_server::epoch() {
-    // 1. admission, in arrival order, frame by frame as slots are free
+    const auto t0 = Clock::now();
+    int n_admit = 0, n_tiles = 0;
     {
         std::lock_guard<std::mutex> lock(mu);
-        for (Pool& p : pools) p.admitted_now.clear();
+        // 1. admission, in arrival order, frame by frame as slots are free
         for (auto it = queue.begin(); it != queue.end();) {
             Request* r = *it;
             Pool& p = pools[r->code];
@@ -168,48 +197,63 @@ bool ndgsbp_server::epoch() {
                 p.owner[slot] = {r, r->admitted};
                 std::memcpy(p.h_stage + static_cast<size_t>(slot) * p.N, r->llr + static_cast<size_t>(r->admitted) * p.N,
                             sizeof(float) * p.N);
-                p.admitted_now.push_back(slot);
+                h_admit[n_admit++] = (r->code << 24) | slot;
                 ++r->admitted;
                 ++in_flight;
             }
             it = (r->admitted == r->n_frames) ? queue.erase(it) : std::next(it);
         }
-    }
-    for (Pool& p : pools) {
-        std::sort(p.admitted_now.begin(), p.admitted_now.end());
-        for (size_t i = 0; i < p.admitted_now.size();) {
-            size_t j = i + 1;
-            while (j < p.admitted_now.size() && p.admitted_now[j] == p.admitted_now[j - 1] + 1) ++j;
-            const int a = p.admitted_now[i], n = static_cast<int>(j - i);
-            SRV_CUDA(cudaMemcpyAsync(p.llr + static_cast<size_t>(a) * p.N, p.h_stage + static_cast<size_t>(a) * p.N,
-                                     sizeof(float) * p.N * n, cudaMemcpyHostToDevice, stream));
-            SRV_CUDA(cudaMemcpyAsync(p.flag + a, p.h_new + a, sizeof(int) * n, cudaMemcpyHostToDevice, stream));
-            i = j;
+        // tiles over the occupied slots of every pool: ranges holding up to tile_frames occupied
+        // slots (free slots inside a range are skipped by the kernel)
+        for (int i = 0; i < static_cast<int>(pools.size()); ++i) {
+            const Pool& p = pools[i];
+            int first = -1, count = 0, last = -1;
+            for (int slot = 0; slot < p.slots; ++slot) {
+                if (!p.owner[slot].first) continue;
+                if (first < 0) first = slot;
+                last = slot;
+                if (++count == p.tile_frames) {
+                    h_tiles[n_tiles++] = make_int4(i, first, last - first + 1, 0);
+                    first = -1;
+                    count = 0;
+                }
+            }
+            if (first >= 0) h_tiles[n_tiles++] = make_int4(i, first, last - first + 1, 0);
         }
     }
-    // 2. one serving launch over every pool
-    const auto t0 = Clock::now();
-    SRV_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), stream));
-    fn<<<grid, threads, smem, stream>>>(args);
-    SRV_CUDA(cudaGetLastError());
-    // 3. statuses and outputs back, then harvest
-    for (Pool& p : pools) {
-        SRV_CUDA(cudaMemcpyAsync(p.h_flag, p.flag, sizeof(int) * p.slots, cudaMemcpyDeviceToHost, stream));
-        SRV_CUDA(cudaMemcpyAsync(p.h_iters, p.iters, sizeof(int32_t) * p.slots, cudaMemcpyDeviceToHost, stream));
-        SRV_CUDA(cudaMemcpyAsync(p.h_ok, p.ok, p.slots, cudaMemcpyDeviceToHost, stream));
-        SRV_CUDA(cudaMemcpyAsync(p.h_hard, p.hard, sizeof(uint32_t) * p.W * p.slots, cudaMemcpyDeviceToHost, stream));
-    }
-    SRV_CUDA(cudaStreamSynchronize(stream));
     const auto t1 = Clock::now();
+    if (n_tiles == 0) return true;
+    // 2. admit, then one serving launch over the occupied tiles
+    if (n_admit) {
+        SRV_CUDA(cudaMemcpyAsync(d_admit, h_admit, sizeof(int) * n_admit, cudaMemcpyHostToDevice, stream));
+        AdmitArgs aa{};
+        for (size_t i = 0; i < pools.size(); ++i) aa.flags[i] = pools[i].flag;
+        aa.list = d_admit;
+        aa.n = n_admit;
+        admit_kernel<<<std::min(1024, (n_admit + 255) / 256), 256, 0, stream>>>(aa);
+        SRV_CUDA(cudaGetLastError());
+    }
+    SRV_CUDA(cudaMemcpyAsync(d_tiles, h_tiles, sizeof(int4) * n_tiles, cudaMemcpyHostToDevice, stream));
+    SRV_CUDA(cudaMemsetAsync(d_done_count, 0, sizeof(int) * pools.size(), stream));
+    SRV_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), stream));
+    TileArgs a = args;
+    a.n_tiles = n_tiles;
+    fn<<<std::min(max_grid, n_tiles), threads, smem, stream>>>(a);
+    SRV_CUDA(cudaGetLastError());
+    SRV_CUDA(cudaMemcpyAsync(h_done_count, d_done_count, sizeof(int) * pools.size(), cudaMemcpyDeviceToHost, stream));
+    SRV_CUDA(cudaStreamSynchronize(stream));
+    const auto t2 = Clock::now();
+    // 3. harvest the retired frames
     std::vector<Request*> finished;
     {
         std::lock_guard<std::mutex> lock(mu);
-        stats.epochs += 1;
-        stats.busy_seconds += std::chrono::duration<double>(t1 - t0).count();
-        for (Pool& p : pools) {
-            for (int slot = 0; slot < p.slots; ++slot) {
+        for (size_t i = 0; i < pools.size(); ++i) {
+            Pool& p = pools[i];
+            const int n_done = h_done_count[i];
+            for (int k = 0; k < n_done; ++k) {
+                const int slot = p.h_done[k];
                 Request* r = p.owner[slot].first;
-                if (!r || p.h_flag[slot] != kSlotDone) continue;
+                if (!r) continue;
                 const int64_t f = p.owner[slot].second;
                 std::memcpy(r->hard + static_cast<size_t>(f) * p.W, p.h_hard + static_cast<size_t>(slot) * p.W,
                             sizeof(uint32_t) * p.W);
@@ -223,12 +267,19 @@ bool ndgsbp_server::epoch() {
                 --in_flight;
                 if (++r->retired == r->n_frames) finished.push_back(r);
             }
+            if (n_done) std::sort(p.free_slots.begin(), p.free_slots.end(), std::greater<int>());
         }
+        const auto t3 = Clock::now();
         for (Request* r : finished) {
             r->done = true;
-            r->t_done = Clock::now();
+            r->t_done = t3;
             stats.requests_completed += 1;
         }
+        stats.epochs += 1;
+        stats.admit_seconds += std::chrono::duration<double>(t1 - t0).count();
+        stats.device_seconds += std::chrono::duration<double>(t2 - t1).count();
+        stats.harvest_seconds += std::chrono::duration<double>(t3 - t2).count();
+        stats.busy_seconds += std::chrono::duration<double>(t3 - t0).count();
     }
     if (!finished.empty()) cv_done.notify_all();
     return true;
@@ -266,10 +317,14 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     const int ms = params->msg_dtype == NDGSBP_F32 ? 4 : 2;
     std::unique_ptr<ndgsbp_server> h(new (std::nothrow) ndgsbp_server);
     if (!h) return fail(NDGSBP_ERR_NOMEM, "out of host memory");
-    int dev = 0, sms = 0, optin = 0;
+    int dev = 0, sms = 0, optin = 0, smem_sm = 0, reserved = 0, mapped = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) ||
+        cudaDeviceGetAttribute(&mapped, cudaDevAttrCanMapHostMemory, dev))
         return fail(NDGSBP_ERR_CUDA, "server_create: no CUDA device");
+    if (!mapped) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: the device cannot map host memory");
     h->device = dev;
     h->params = *params;
     h->epoch_iters = epoch_iters;
@@ -277,7 +332,6 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     double wsum = 0.0;
     for (int i = 0; i < n_codes; ++i) wsum += weights ? std::max(0.0, weights[i]) : 1.0;
     if (!(wsum > 0.0)) return fail(NDGSBP_ERR_INVALID, "server_create: weights sum to zero");
-    const size_t budget = static_cast<size_t>(optin) - 256;
     size_t table_max = 0;
     int threads = params->block_threads;
     for (int i = 0; i < n_codes; ++i) {
@@ -293,60 +347,94 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         p.ds = p.Q->max_deg | 1;
         p.N = p.g->code->N;
         p.W = (p.N + 31) / 32;
+        p.p_bytes = a16(static_cast<size_t>(p.N) * 4);
+        p.m_bytes = a16(static_cast<size_t>(p.Q->msg_slots) * ms);
+        p.d_bytes = a16(static_cast<size_t>(p.Q->window) * p.Q->Z * p.ds * 4);
         table_max = std::max(table_max, tile_table_bytes(*p.Q));
         if (!params->block_threads)
             threads = std::max(threads, std::min(512, std::max(128, (p.Q->window * p.Q->Z * p.tpc + 31) / 32 * 32)));
     }
+    if (threads <= 0 || threads > 1024 || threads % 32)
+        return fail(NDGSBP_ERR_INVALID, "server_create: block_threads must be a multiple of 32 up to 1024");
+    // Shared memory per CTA under a residency target of k CTAs per SM (as for ragged launches):
+    // a code whose messages do not fit under the cap works on them in device memory, where a
+    // parked frame keeps them anyway.  Default k: 2 when every code fits, else 1.
+    auto cap_for = [&](int k) {
+        const size_t per = static_cast<size_t>(smem_sm) / k - static_cast<size_t>(reserved) - 1024;
+        return std::min(static_cast<size_t>(optin) - 256, per) & ~static_cast<size_t>(15);
+    };
+    auto fits = [&](size_t cap) {
+        for (const Pool& p : h->pools)
+            if (table_max + p.p_bytes + p.d_bytes > cap) return false;
+        return true;
+    };
+    const int target = params->ctas_per_sm > 0 ? params->ctas_per_sm : (fits(cap_for(2)) ? 2 : 1);
+    const size_t budget = cap_for(target);
     size_t smem = table_max;
     for (int i = 0; i < n_codes; ++i) {
         Pool& p = h->pools[i];
-        p.p_bytes = a16(static_cast<size_t>(p.N) * 4);
-        const size_t m = a16(static_cast<size_t>(p.Q->msg_slots) * ms);
-        const size_t d = a16(static_cast<size_t>(p.Q->window) * p.Q->Z * p.ds * 4);
-        p.m_bytes = table_max + p.p_bytes + m + d <= budget ? m : 0;
-        p.slot_bytes = p.p_bytes + p.m_bytes + d;
-        if (table_max + p.slot_bytes > budget) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d too large", i);
+        if (table_max + p.p_bytes + p.m_bytes + p.d_bytes > budget) p.m_bytes = 0;
+        p.slot_bytes = p.p_bytes + p.m_bytes + p.d_bytes;
+        if (table_max + p.slot_bytes > budget)
+            return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d does not fit at %d CTAs per SM", i, target);
         const int per_slot = p.Q->window * p.Q->Z * p.tpc;
-        p.cta_slots = std::max(1, std::min<int>({16, threads / per_slot, static_cast<int>((budget - table_max) / p.slot_bytes)}));
+        p.cta_slots = std::max(1, std::min<int>({16, std::max(1, threads / per_slot),
+                                                 static_cast<int>((budget - table_max) / p.slot_bytes)}));
+        p.tile_frames = 2 * p.cta_slots;
         smem = std::max(smem, table_max + p.cta_slots * p.slot_bytes);
-        // pool size from the budget share: LLR, posterior, messages, outputs and status per slot
+        // pool size from the budget share: posterior and messages of a running frame, LLR
+        // staging, outputs and status per slot
         const double share = (weights ? std::max(0.0, weights[i]) : 1.0) / wsum;
         const size_t per = sizeof(float) * p.N * 2 + static_cast<size_t>(p.Q->msg_slots) * ms + sizeof(uint32_t) * p.W + 16;
         p.slots = static_cast<int>(std::min<double>(kMaxPoolSlots, std::floor(share * hbm_budget_bytes / per)));
         if (p.slots < 1) return fail(NDGSBP_ERR_BUDGET, "server_create: the budget leaves no slot for code %d", i);
     }
-    if (threads <= 0 || threads > 1024 || threads % 32)
-        return fail(NDGSBP_ERR_INVALID, "server_create: block_threads must be a multiple of 32 up to 1024");
     cudaError_t e = cudaSuccess;
     auto dmalloc = [&](void** ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
         if (e == cudaSuccess) e = cudaMemset(*ptr, 0, bytes);
     };
     auto hmalloc = [&](void** ptr, size_t bytes) {
-        if (e == cudaSuccess) e = cudaHostAlloc(ptr, bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc(ptr, bytes, cudaHostAllocMapped);
         if (e == cudaSuccess) std::memset(*ptr, 0, bytes);
     };
-    std::vector<int4> tiles;
+    int max_tiles = 0;
     for (int i = 0; i < n_codes; ++i) {
         Pool& p = h->pools[i];
-        dmalloc(reinterpret_cast<void**>(&p.llr), sizeof(float) * p.N * static_cast<size_t>(p.slots));
-        dmalloc(reinterpret_cast<void**>(&p.hard), sizeof(uint32_t) * p.W * static_cast<size_t>(p.slots));
-        dmalloc(reinterpret_cast<void**>(&p.iters), sizeof(int32_t) * p.slots);
-        dmalloc(reinterpret_cast<void**>(&p.ok), p.slots);
         dmalloc(reinterpret_cast<void**>(&p.flag), sizeof(int) * p.slots);
         dmalloc(reinterpret_cast<void**>(&p.st_iter), sizeof(int) * p.slots);
         dmalloc(reinterpret_cast<void**>(&p.st_P), sizeof(float) * p.N * static_cast<size_t>(p.slots));
         dmalloc(&p.st_msgs, static_cast<size_t>(p.Q->msg_slots) * ms * p.slots);
         hmalloc(reinterpret_cast<void**>(&p.h_stage), sizeof(float) * p.N * static_cast<size_t>(p.slots));
-        hmalloc(reinterpret_cast<void**>(&p.h_new), sizeof(int) * p.slots);
-        hmalloc(reinterpret_cast<void**>(&p.h_flag), sizeof(int) * p.slots);
         hmalloc(reinterpret_cast<void**>(&p.h_hard), sizeof(uint32_t) * p.W * static_cast<size_t>(p.slots));
         hmalloc(reinterpret_cast<void**>(&p.h_iters), sizeof(int32_t) * p.slots);
         hmalloc(reinterpret_cast<void**>(&p.h_ok), p.slots);
+        hmalloc(reinterpret_cast<void**>(&p.h_done), sizeof(int) * p.slots);
         if (e != cudaSuccess) return fail(NDGSBP_ERR_NOMEM, "server_create: %s", cudaGetErrorString(e));
-        for (int s = 0; s < p.slots; ++s) p.h_new[s] = kSlotNew;
         p.owner.assign(p.slots, {nullptr, 0});
         for (int s = p.slots - 1; s >= 0; --s) p.free_slots.push_back(s);
+        max_tiles += (p.slots + p.tile_frames - 1) / p.tile_frames;
+        h->stats.slots_total += p.slots;
+    }
+    dmalloc(reinterpret_cast<void**>(&h->d_tiles), sizeof(int4) * max_tiles);
+    hmalloc(reinterpret_cast<void**>(&h->h_tiles), sizeof(int4) * max_tiles);
+    dmalloc(reinterpret_cast<void**>(&h->d_admit), sizeof(int) * h->stats.slots_total);
+    hmalloc(reinterpret_cast<void**>(&h->h_admit), sizeof(int) * h->stats.slots_total);
+    dmalloc(reinterpret_cast<void**>(&h->d_done_count), sizeof(int) * kTileMaxCodes);
+    hmalloc(reinterpret_cast<void**>(&h->h_done_count), sizeof(int) * kTileMaxCodes);
+    dmalloc(reinterpret_cast<void**>(&h->d_counter), 256);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), threads, smem);
+    if (e != cudaSuccess) return fail(NDGSBP_ERR_CUDA, "server_create: %s", cudaGetErrorString(e));
+    if (per_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: the launch does not fit on an SM");
+    per_sm = std::min(per_sm, target);
+    for (int i = 0; i < n_codes; ++i) {
+        Pool& p = h->pools[i];
         TileCode& C = h->args.codes[i];
         C.N = p.N;
         C.E = static_cast<int>(p.g->code->E);
@@ -374,44 +462,33 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         C.state_P = p.st_P;
         C.state_msgs = p.st_msgs;
         C.epoch_iters = epoch_iters;
+        C.done_list = device_view(p.h_done);
+        C.done_count = h->d_done_count + i;
         RunArgs& r = C.r;
         r.N = p.N;
         r.E = C.E;
         r.W = p.W;
-        r.llr = p.llr;
+        r.llr = device_view(p.h_stage);
         r.llr_dtype = NDGSBP_F32;
         r.n_frames = p.slots;
         r.max_iter = params->max_iter;
         r.llr_max = params->llr_max;
         r.early_stop = params->early_stop ? 1 : 0;
-        r.hard_bits = p.hard;
-        r.iters = p.iters;
-        r.synd_ok = p.ok;
-        const int tf = p.cta_slots * 2;
-        for (int s = 0; s < p.slots; s += tf) tiles.push_back(make_int4(i, s, std::min(tf, p.slots - s), 0));
-        h->stats.slots_total += p.slots;
+        r.hard_bits = device_view(p.h_hard);
+        r.iters = device_view(p.h_iters);
+        r.synd_ok = device_view(p.h_ok);
+        if (!C.done_list || !r.llr || !r.hard_bits || !r.iters || !r.synd_ok)
+            return fail(NDGSBP_ERR_CUDA, "server_create: cannot map host buffers into the device");
     }
-    dmalloc(reinterpret_cast<void**>(&h->d_tiles), sizeof(int4) * tiles.size());
-    if (e == cudaSuccess) e = cudaMemcpy(h->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
-    dmalloc(reinterpret_cast<void**>(&h->d_counter), 256);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
-    int per_sm = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), threads, smem);
-    if (e != cudaSuccess) return fail(NDGSBP_ERR_CUDA, "server_create: %s", cudaGetErrorString(e));
-    if (per_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: the launch does not fit on an SM");
-    if (params->ctas_per_sm > 0) per_sm = std::min(per_sm, params->ctas_per_sm);
     h->args.n_codes = n_codes;
     h->args.tiles = h->d_tiles;
-    h->args.n_tiles = static_cast<int>(tiles.size());
+    h->args.n_tiles = 0;
     h->args.tile_counter = h->d_counter;
     h->args.table_bytes = static_cast<int>(table_max);
     h->fn = fn;
     h->threads = threads;
     h->smem = smem;
-    h->grid = std::max(1, std::min(per_sm * sms, h->args.n_tiles));
+    h->max_grid = std::max(1, per_sm * sms);
     ndgsbp_server* raw = h.release();
     raw->worker = std::thread([raw] { raw->run(); });
     *out = raw;

@@ -27,6 +27,7 @@ GROUPS_CYCLIC, GROUPS_NATURAL = 1, 2
 SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
 VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1, 2, 3, 4
 VARIANT_QC_PAIR, VARIANT_QC_PAIR_GLOBAL, VARIANT_TILE = 5, 6, 7
+VARIANT_QC_FRAMES2, VARIANT_QC_FRAMES2_GLOBAL = 8, 9
 TUNE_TILE_ONLY = 1
 STAT_FRAMES, STAT_FRAME_ERRORS, STAT_BIT_ERRORS, STAT_UNDETECTED = 0, 1, 2, 3
 STAT_ITERATIONS, STAT_UNSATISFIED, STATS_LEN = 4, 5, 8
@@ -81,7 +82,9 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("requests_submitted", ctypes.c_int64), ("requests_completed", ctypes.c_int64),
                 ("frames_completed", ctypes.c_int64), ("frame_errors_unsatisfied", ctypes.c_int64),
                 ("epochs", ctypes.c_int64), ("iterations", ctypes.c_int64), ("busy_seconds", ctypes.c_double),
-                ("slots_total", ctypes.c_int64), ("slots_in_use", ctypes.c_int64)]
+                ("slots_total", ctypes.c_int64), ("slots_in_use", ctypes.c_int64),
+                ("admit_seconds", ctypes.c_double), ("device_seconds", ctypes.c_double),
+                ("harvest_seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -82,7 +82,7 @@ def test_ragged_autotune(env):
     p, ms = nd.ragged_autotune(batches, p0, sample_frames=1024)
     shapes = [(b["frames_per_cta"], b["lanes_per_cn"]) for b in batches]
     print(f"\nragged tuned: threads {p.block_threads}, per-code (fpc, lanes) {shapes}, {ms:.3f} ms")
-    assert p.variant == nd.VARIANT_TILE and p.block_threads in (128, 256, 384, 512)
+    assert p.variant == nd.VARIANT_TILE and p.block_threads in (128, 256, 384, 512) and 1 <= p.ctas_per_sm <= 4
     assert all(1 <= f <= 16 and l in (1, 2, 4) for f, l in shapes)
     assert ms > 0
     # the tuned launch decodes each code as that code alone with the same shape

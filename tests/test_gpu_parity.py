@@ -239,7 +239,9 @@ def test_variants_and_block_sizes_agree_bitwise(env, name, kind, qc, msg):
               dict(variant=nd.VARIANT_GLOBAL, block_threads=128, ctas_per_sm=1)]
     if qc:
         others += [dict(variant=nd.VARIANT_QC), dict(variant=nd.VARIANT_QC_GLOBAL),
-                   dict(variant=nd.VARIANT_QC_PAIR), dict(variant=nd.VARIANT_QC_PAIR_GLOBAL)]
+                   dict(variant=nd.VARIANT_QC_PAIR), dict(variant=nd.VARIANT_QC_PAIR_GLOBAL),
+                   dict(variant=nd.VARIANT_QC_FRAMES2), dict(variant=nd.VARIANT_QC_FRAMES2_GLOBAL),
+                   dict(variant=nd.VARIANT_QC_FRAMES2, ctas_per_sm=1)]
     for kw in others:
         other = _run(nd, torch, g, c, llr, **kw0, **kw)
         if kw["variant"] >= nd.VARIANT_QC:
@@ -465,3 +467,25 @@ def test_tile_kernel(env, oracle_mod, name, kind, lanes, ebn0):
         if tpc == 1:
             base = _run(nd, torch, g, c, llr, max_iter=30, schedule=sched, variant=nd.VARIANT_SMEM)
             assert (first["post"] == base["post"]).all()
+
+
+@pytest.mark.parametrize("msg", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("name,ebn0", [("qc_n2304_r12", 1.25), ("qc_n2304_r34", 3.0)])
+def test_frames2_kernel_equals_single_frame_kernel(env, name, ebn0, msg):
+    """Two frames per thread: each frame gets the single-frame QC kernel's result bit for bit,
+    with odd batch sizes (an idle slot at the tail), slots refilled at different iterations,
+    messages written out, statistics, and with early stop off (max_iter stops)."""
+    nd, torch = env
+    c = I.code_by_name(name)
+    code, g = _groups(nd, c, "layers_cyclic")
+    mdt = {"f32": nd.F32, "f16": nd.F16, "bf16": nd.BF16}[msg]
+    for F in (1, 3, 65, 301):
+        llr = I.channel_llr(c.N, F, ebn0, I.design_rate(c), seed=600 + F)
+        for es in (1, 0):
+            kw = dict(max_iter=12, early_stop=es, msg_dtype=mdt)
+            base = _run(nd, torch, g, c, llr, want_msgs=True, stats=True, variant=nd.VARIANT_QC, **kw)
+            for v in (nd.VARIANT_QC_FRAMES2, nd.VARIANT_QC_FRAMES2_GLOBAL):
+                other = _run(nd, torch, g, c, llr, want_msgs=True, stats=True, variant=v, **kw)
+                assert other["plan"]["variant"] == v
+                for k in ("post", "iters", "ok", "hard", "msgs", "stats", "hist"):
+                    assert (other[k] == base[k]).all(), (F, es, v, k)
