@@ -70,6 +70,9 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_VARIANT_TILE 7      /* tile kernel: any QC window, degree <= 32, several frames per CTA */
 #define NDGSBP_VARIANT_QC_FRAMES2 8 /* layered QC kernel, two frames per thread, packed FP32 arithmetic */
 #define NDGSBP_VARIANT_QC_FRAMES2_GLOBAL 9 /* the two-frame kernel with messages in global-memory slots */
+#define NDGSBP_VARIANT_QC_TWO_ROUND 10 /* layered QC kernel with both write-back rounds on every edge
+                                         (QC uses direct write-back off shared block columns for
+                                         2-layer windows; results are the same) */
 
 /* stats counters accumulated by ndgsbp_decode_ex (uint64 each) */
 #define NDGSBP_STAT_FRAMES 0
@@ -330,8 +333,9 @@ ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches,
  * A server owns, per code, a pool of frame slots (posterior and messages of running frames in
  * device memory; LLR staging and outputs in pinned host memory that the kernel reads and writes
  * directly) sized so that all pools fit hbm_budget_bytes (split in proportion to weights; NULL =
- * equal shares).  A host thread of the library admits the frames of queued
- * requests into free slots in arrival order, runs epoch launches of the tile kernel in which
+ * equal shares).  A staging thread of the library places the frames of queued
+ * requests into free slots in arrival order (copying their LLRs while epochs run); a worker
+ * thread runs epoch launches of the tile kernel in which
  * every running frame advances by at most epoch_iters iterations (its state stays in device
  * memory between epochs), and retires frames whose syndrome is zero (Step 4 b) or that reached
  * params->max_iter, freeing their slots for the next frames at once.  A request completes when
@@ -348,7 +352,7 @@ typedef struct ndgsbp_server_stats {
     int64_t iterations;          /* frame-iterations run */
     double busy_seconds;         /* host time with at least one frame on the device */
     int64_t slots_total, slots_in_use;
-    double admit_seconds;        /* host time admitting frames (LLR staging, admit and tile lists) */
+    double admit_seconds;        /* staging-thread time copying admitted frames' LLRs (overlaps epochs) */
     double device_seconds;       /* host time from an epoch's first enqueue to its stream sync */
     double harvest_seconds;      /* host time copying retired frames' outputs to their requests */
 } ndgsbp_server_stats;

@@ -251,6 +251,7 @@ static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     BlobBuilder b;
     const size_t o_tab = b.add(Q.edge_tab), o_deg = b.add(Q.layer_deg), o_off = b.add(Q.layer_off);
     const size_t o_gl = b.add(Q.group_layers), o_csr = b.add(Q.csr_of), o_str = b.add(Q.layer_stride);
+    const size_t o_w2 = b.add(Q.win2);
     void* blob = nullptr;
     ndgsbp_status st = b.upload(&blob);
     if (st) return st;
@@ -262,6 +263,7 @@ static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     D.layer_off = reinterpret_cast<const int32_t*>(p + o_off);
     D.group_layers = reinterpret_cast<const int32_t*>(p + o_gl);
     D.csr_of = reinterpret_cast<const int32_t*>(p + o_csr);
+    D.win2 = Q.win2.empty() ? nullptr : reinterpret_cast<const int32_t*>(p + o_w2);
     return NDGSBP_OK;
 }
 
@@ -362,7 +364,7 @@ static ndgsbp_status validate_params(const ndgsbp_params* p) {
         return fail(NDGSBP_ERR_INVALID, "frames_per_cta must be in [0, 16]");
     if (p->lanes_per_cn != 0 && p->lanes_per_cn != 1 && p->lanes_per_cn != 2 && p->lanes_per_cn != 4)
         return fail(NDGSBP_ERR_INVALID, "lanes_per_cn must be 0, 1, 2 or 4");
-    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_FRAMES2_GLOBAL)
+    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_TWO_ROUND)
         return fail(NDGSBP_ERR_INVALID, "unknown variant %d", p->variant);
     return NDGSBP_OK;
 }
@@ -444,7 +446,8 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     const int maxdc = degree_bound(Q.max_deg);
     if (!maxdc) return NDGSBP_OK;
     const bool spec = qc_degrees_specialised(Q, maxdc);
-    const bool want_single = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL;
+    const bool want_single = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL ||
+                             p->variant == NDGSBP_VARIANT_QC_TWO_ROUND;
     const bool want_pair = p->variant == NDGSBP_VARIANT_QC_PAIR || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL;
     const bool want_f2 = p->variant == NDGSBP_VARIANT_QC_FRAMES2 || p->variant == NDGSBP_VARIANT_QC_FRAMES2_GLOBAL;
     const bool force_global = p->variant == NDGSBP_VARIANT_QC_GLOBAL || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL ||
@@ -472,7 +475,8 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     if (p_bytes + t_bytes > budget) return NDGSBP_OK;
     const bool msg_smem = !force_global && p_bytes + m_bytes + t_bytes <= budget;
     const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
-    QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair);
+    const bool w2 = !pair && Q.window == 2 && !Q.win2.empty() && p->variant != NDGSBP_VARIANT_QC_TWO_ROUND;
+    QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair, w2);
     if (!fn) return NDGSBP_OK;
     int per_sm = 0;
     int64_t grid = 0;
@@ -485,7 +489,8 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     plan.msg_smem = msg_smem;
     ndgsbp_plan& o = plan.pub;
     o.variant = pair ? (msg_smem ? NDGSBP_VARIANT_QC_PAIR : NDGSBP_VARIANT_QC_PAIR_GLOBAL)
-                     : (msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL);
+                     : (p->variant == NDGSBP_VARIANT_QC_TWO_ROUND ? NDGSBP_VARIANT_QC_TWO_ROUND
+                                                                  : (msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL));
     o.block_threads = threads;
     o.grid = static_cast<int32_t>(grid);
     o.ctas_per_sm = per_sm;

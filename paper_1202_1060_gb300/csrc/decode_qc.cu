@@ -46,6 +46,60 @@ __device__ __forceinline__ void qc_phase_a(const int2* __restrict__ et, int c, i
     });
 }
 
+// Phase A for a window of 2 layers, with the write-back of every edge whose block column the
+// other layer of the window does not touch done at once: that VN is read by this CN alone in
+// this group, so P_n + change is final.  Of an edge in a shared block column, position 0
+// leaves its change in dx for the position-1 CN on the same VN, which adds both in phase B in
+// position order ((P + change_0) + change_1, the order of the two-round write-back), so results
+// do not change.
+template <int D, int MAXDC, typename MsgT, bool POS1>
+__device__ __forceinline__ void qc_phase_a_w2(const int2* __restrict__ et, unsigned shared, int c, int c4,
+                                              int Z4, float* __restrict__ P, MsgT* __restrict__ m,
+                                              float* __restrict__ dxc, float lim, int (&vb)[MAXDC],
+                                              float (&dl)[MAXDC]) {
+    static_assert(D <= MAXDC, "degree above the bound");
+    float t[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        vb[k] = qc_vb(et[k], c, c4, Z4);
+        t[k] = at_byte(P, vb[k]) - to_f(m[k]);
+    }
+    // the old message is read again from m[k] instead of held in a register (this path keeps
+    // more values live than the two-round one)
+    check_node_update<D>(t, D, lim, [&](int k, float val) {
+        const MsgT q = from_f<MsgT>(val);
+        const float d = to_f(q) - to_f(m[k]);
+        m[k] = q;
+        if ((shared >> k) & 1u) {
+            if (POS1)
+                dl[k] = d;
+            else
+                dxc[k] = d;
+        } else {
+            at_byte(P, vb[k]) += d;
+        }
+    });
+}
+
+// Phase B of a 2-layer window: position-1 CN c adds, on each shared VN, the position-0 change
+// (from dx) and then its own (kept in dl).  w2 (global memory, read through L1) gives, per
+// shared edge k, the position-0 edge k0 on the same block column and the CN offset s_1 - s_0.
+template <int D, int MAXDC>
+__device__ __forceinline__ void qc_phase_b_w2(const int2* __restrict__ et, const int2* __restrict__ w2, unsigned shared,
+                                              int c, int c4, int Z, int Z4, int dxs, float* __restrict__ P,
+                                              const float* __restrict__ dx, const float (&dl)[MAXDC]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if ((shared >> k) & 1u) {
+            const int2 e = __ldg(w2 + k);
+            int c0 = c + e.y;
+            c0 -= c0 >= Z ? Z : 0;
+            float& p = at_byte(P, qc_vb(et[k], c, c4, Z4));
+            p = (p + dx[c0 * dxs + e.x]) + dl[k];
+        }
+    }
+}
+
 template <int MAXDC, typename MsgT>
 __device__ __forceinline__ void qc_phase_a_any(const int2* __restrict__ et, int c, int c4, int Z4, int d,
                                                float* __restrict__ P, MsgT* __restrict__ m, float lim,
@@ -90,6 +144,9 @@ struct QcSmem {
     int* lstride;
     int* loff;
     int* glay;
+    unsigned* w2mask;   // [G][2] bit k: edge k of that window position is on a shared block column
+    float* dx;   // [Z][dxs] position-0 changes on shared block columns
+    int dxs;     // odd stride >= maxdeg
 };
 
 template <typename MsgT, bool MSG_SMEM>
@@ -109,7 +166,22 @@ __device__ __forceinline__ QcSmem qc_smem_layout(unsigned char* smem, const QcAr
     s.loff = reinterpret_cast<int*>(smem + off);
     off += (static_cast<size_t>(a.nl) * 4 + 15) & ~static_cast<size_t>(15);
     s.glay = reinterpret_cast<int*>(smem + off);
+    off += (static_cast<size_t>(a.G) * a.window * 4 + 15) & ~static_cast<size_t>(15);
+    s.dxs = a.maxdeg | 1;
+    s.w2mask = reinterpret_cast<unsigned*>(smem + off);
+    if (a.win2) off += (static_cast<size_t>(a.G) * 2 * 4 + 15) & ~static_cast<size_t>(15);
+    s.dx = reinterpret_cast<float*>(smem + off);
     const int tid = threadIdx.x, nt = blockDim.x;
+    if (a.win2) {
+        for (int i = tid; i < a.G * 2; i += nt) {
+            unsigned mk = 0u;
+            for (int k = 0; k < a.maxdeg; ++k) {
+                const int x = a.win2[i * a.maxdeg + k].x;
+                mk |= ((i & 1) ? x >= 0 : x != 0) ? 1u << k : 0u;
+            }
+            s.w2mask[i] = mk;
+        }
+    }
     for (int i = tid; i < a.nl * a.maxdeg; i += nt) s.tab[i] = a.edge_tab[i];
     for (int i = tid; i < a.nl; i += nt) {
         s.ldeg[i] = a.layer_deg[i];
@@ -139,7 +211,7 @@ __device__ __forceinline__ void qc_frame_messages_out(const QcArgs& a, const Msg
     }
 }
 
-template <typename MsgT, bool MSG_SMEM, int MAXDC, bool SPEC>
+template <typename MsgT, bool MSG_SMEM, int MAXDC, bool SPEC, bool W2>
 __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const QcArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_frame;
@@ -167,6 +239,42 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const
                 float dl[MAXDC];
                 int vb[MAXDC];
                 int d = 0;
+                if constexpr (SPEC && W2) {
+                    // 2-layer window: direct write-back off the shared block columns, one
+                    // ordered round on them
+                    if (active) {
+                        const int l = s.glay[g * W + j];
+                        d = s.ldeg[l];
+                        const int2* et = s.tab + l * md;
+                        MsgT* m = msg + s.loff[l] + c * s.lstride[l];
+                        const unsigned mk = s.w2mask[g * 2 + j];
+                        float* dxc = s.dx + c * s.dxs;
+                        if (j == 0) {
+#define NDGSBP_CASE_W0(D) \
+    if (d == D) qc_phase_a_w2<NDGSBP_DD(D), MAXDC, MsgT, false>(et, mk, c, c4, Z4, P, m, dxc, lim, vb, dl);
+                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_W0)
+#undef NDGSBP_CASE_W0
+                        } else {
+#define NDGSBP_CASE_W1(D) \
+    if (d == D) qc_phase_a_w2<NDGSBP_DD(D), MAXDC, MsgT, true>(et, mk, c, c4, Z4, P, m, dxc, lim, vb, dl);
+                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_W1)
+#undef NDGSBP_CASE_W1
+                        }
+                    }
+                    __syncthreads();
+                    if (active && j == 1) {
+                        const int l = s.glay[g * W + 1];
+                        const int2* et = s.tab + l * md;
+                        const int2* w2 = a.win2 + (g * 2 + 1) * md;
+                        const unsigned mk = s.w2mask[g * 2 + 1];
+#define NDGSBP_CASE_WB(D) \
+    if (d == D) qc_phase_b_w2<NDGSBP_DD(D), MAXDC>(et, w2, mk, c, c4, Z, Z4, s.dxs, P, s.dx, dl);
+                        NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_WB)
+#undef NDGSBP_CASE_WB
+                    }
+                    __syncthreads();
+                    continue;
+                }
                 if (active) {
                     const int l = s.glay[g * W + j];
                     d = s.ldeg[l];
@@ -359,20 +467,24 @@ __global__ void __launch_bounds__(pair_max_threads(MAXDC)) qc_pair_kernel(const 
 
 // ---- kernel selection ---------------------------------------------------------------------
 template <typename MsgT, int MAXDC>
-static QcKernelFn pick_qc_storage(bool msg_smem, bool spec, bool pair) {
+static QcKernelFn pick_qc_storage(bool msg_smem, bool spec, bool pair, bool w2) {
     if (pair) return msg_smem ? qc_pair_kernel<MsgT, true, MAXDC> : qc_pair_kernel<MsgT, false, MAXDC>;
-    if (spec) return msg_smem ? qc_decode_kernel<MsgT, true, MAXDC, true> : qc_decode_kernel<MsgT, false, MAXDC, true>;
-    return msg_smem ? qc_decode_kernel<MsgT, true, MAXDC, false> : qc_decode_kernel<MsgT, false, MAXDC, false>;
+    if (spec && w2)
+        return msg_smem ? qc_decode_kernel<MsgT, true, MAXDC, true, true> : qc_decode_kernel<MsgT, false, MAXDC, true, true>;
+    if (spec)
+        return msg_smem ? qc_decode_kernel<MsgT, true, MAXDC, true, false>
+                        : qc_decode_kernel<MsgT, false, MAXDC, true, false>;
+    return msg_smem ? qc_decode_kernel<MsgT, true, MAXDC, false, false> : qc_decode_kernel<MsgT, false, MAXDC, false, false>;
 }
 
 template <typename MsgT>
-static QcKernelFn pick_qc_degree(int maxdc, bool msg_smem, bool spec, bool pair) {
+static QcKernelFn pick_qc_degree(int maxdc, bool msg_smem, bool spec, bool pair, bool w2) {
     switch (maxdc) {
-        case 8: return pick_qc_storage<MsgT, 8>(msg_smem, spec, pair);
-        case 16: return pick_qc_storage<MsgT, 16>(msg_smem, spec, pair);
+        case 8: return pick_qc_storage<MsgT, 8>(msg_smem, spec, pair, w2);
+        case 16: return pick_qc_storage<MsgT, 16>(msg_smem, spec, pair, w2);
         case 32:
             if (spec || pair) return nullptr;
-            return msg_smem ? qc_decode_kernel<MsgT, true, 32, false> : qc_decode_kernel<MsgT, false, 32, false>;
+            return msg_smem ? qc_decode_kernel<MsgT, true, 32, false, false> : qc_decode_kernel<MsgT, false, 32, false, false>;
         default: return nullptr;
     }
 }
@@ -386,11 +498,11 @@ bool qc_degrees_specialised(const QcLayout& Q, int maxdc) {
 
 int qc_pair_max_threads(int maxdc) { return pair_max_threads(maxdc); }
 
-QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair) {
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair, bool w2) {
     switch (msg_dtype) {
-        case NDGSBP_F32: return pick_qc_degree<float>(maxdc, msg_smem, spec, pair);
-        case NDGSBP_F16: return pick_qc_degree<__half>(maxdc, msg_smem, spec, pair);
-        case NDGSBP_BF16: return pick_qc_degree<__nv_bfloat16>(maxdc, msg_smem, spec, pair);
+        case NDGSBP_F32: return pick_qc_degree<float>(maxdc, msg_smem, spec, pair, w2);
+        case NDGSBP_F16: return pick_qc_degree<__half>(maxdc, msg_smem, spec, pair, w2);
+        case NDGSBP_BF16: return pick_qc_degree<__nv_bfloat16>(maxdc, msg_smem, spec, pair, w2);
         default: return nullptr;
     }
 }
@@ -399,8 +511,10 @@ static size_t a16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
 size_t qc_table_bytes(const QcLayout& Q) {
     const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;
-    return a16(static_cast<size_t>(Q.n_layers) * Q.max_deg * 8) + 3 * a16(static_cast<size_t>(Q.n_layers) * 4) +
-           a16(G * Q.window * 4);
+    size_t b = a16(static_cast<size_t>(Q.n_layers) * Q.max_deg * 8) + 3 * a16(static_cast<size_t>(Q.n_layers) * 4) +
+               a16(G * Q.window * 4);
+    if (!Q.win2.empty()) b += a16(G * 2 * 4) + a16(static_cast<size_t>(Q.Z) * (Q.max_deg | 1) * 4);
+    return b;
 }
 
 void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs) {
@@ -417,6 +531,7 @@ void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs
     a.group_layers = D.group_layers;
     a.csr_of = D.csr_of;
     a.ws_msgs = ws_msgs;
+    a.win2 = reinterpret_cast<const int2*>(D.win2);
 }
 
 }  // namespace ndgsbp

@@ -16,11 +16,13 @@ struct QcArgs {
     const int32_t* group_layers;  // [G][window]
     const int32_t* csr_of;        // [msg_slots] CSR position of each stored message, -1 = padding
     void* ws_msgs;                // per-CTA message slots when messages are not in shared memory
+    const int2* win2;             // [G][2][maxdeg] block columns shared by 2-layer windows, or null
 };
 
 typedef void (*QcKernelFn)(const QcArgs);
 
-QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair);
+// w2: the 2-layer-window instance (direct write-back off shared block columns; needs win2).
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair, bool w2 = false);
 // Two frames per thread (decode_qc2.cu); degree-specialised codes with MAXDC 8 or 16 only.
 QcKernelFn pick_qc_frames2_kernel(int msg_dtype, int maxdc, bool msg_smem);
 int qc_frames2_max_threads(int maxdc);

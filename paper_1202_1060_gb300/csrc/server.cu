@@ -5,9 +5,10 @@
 // pinned host memory that the kernel reads when the frame starts, and its outputs go straight
 // to pinned host memory that the kernel writes when the frame retires.  A worker thread repeats
 // one epoch:
-//   1. admit: frames of queued requests (arrival order) take free slots of their code's pool;
-//      their LLRs are copied to the slots' staging and the slots are listed for a small admit
-//      kernel that marks them new;
+//   1. admit: frames that a staging thread has already placed (queued requests' frames, in
+//      arrival order, take free slots of their code's pool and have their LLRs copied to the
+//      slots' staging, concurrently with the epochs) are listed for a small admit kernel that
+//      marks their slots new;
 //   2. run: one launch of the tile kernel in serving mode over the tiles of occupied slots of
 //      every pool; each running frame advances by at most epoch_iters iterations, then retires
 //      (zero syndrome or max_iter: outputs written, slot listed as done) or is parked with its
@@ -91,8 +92,12 @@ struct Pool {
     uint8_t* h_ok = nullptr;
     int* h_done = nullptr;
     std::vector<int> free_slots;   // kept in descending order: the lowest free slot is taken first
-    std::vector<std::pair<Request*, int64_t>> owner;
+    std::vector<std::pair<Request*, int64_t>> owner;   // frame held by each slot (staged or running)
+    std::vector<uint8_t> running;   // the slot's frame has been launched
+    std::vector<int> ready;         // staged slots waiting for the next epoch
 };
+
+constexpr int kStageBatch = 512;   // frames the staging thread places per lock hold
 
 template <typename T>
 T* device_view(T* host) {
@@ -120,20 +125,28 @@ struct ndgsbp_server {
     unsigned long long* d_counter = nullptr;
     cudaStream_t stream = nullptr;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_stage;
     std::deque<Request*> queue;
     std::unordered_map<int64_t, std::unique_ptr<Request>> reqs;
     int64_t next_ticket = 1;
-    int64_t in_flight = 0;   // frames holding a slot
+    int64_t in_flight = 0;   // frames holding a slot (staged or running)
+    int64_t n_running = 0;   // launched frames not yet retired
+    int64_t n_ready = 0;     // staged frames waiting for an epoch
     bool stop = false;
     ndgsbp_status failed = NDGSBP_OK;
     std::string failure;
-    std::thread worker;
+    std::thread worker, stager;
     ndgsbp_server_stats stats{};
 
     ~ndgsbp_server();
     void run();
+    void stage();
     bool epoch();
+    bool can_stage() const {
+        for (const Request* r : queue)
+            if (!pools[r->code].free_slots.empty()) return true;
+        return false;
+    }
 };
 
 ndgsbp_server::~ndgsbp_server() {
@@ -142,6 +155,8 @@ ndgsbp_server::~ndgsbp_server() {
         stop = true;
     }
     cv_work.notify_all();
+    cv_stage.notify_all();
+    if (stager.joinable()) stager.join();
     if (worker.joinable()) worker.join();
     int cur = 0;
     if (cudaGetDevice(&cur) == cudaSuccess && cudaSetDevice(device) == cudaSuccess) {
@@ -187,29 +202,24 @@ bool ndgsbp_server::epoch() {
     int n_admit = 0, n_tiles = 0;
     {
         std::lock_guard<std::mutex> lock(mu);
-        // 1. admission, in arrival order, frame by frame as slots are free
-        for (auto it = queue.begin(); it != queue.end();) {
-            Request* r = *it;
-            Pool& p = pools[r->code];
-            while (r->admitted < r->n_frames && !p.free_slots.empty()) {
-                const int slot = p.free_slots.back();
-                p.free_slots.pop_back();
-                p.owner[slot] = {r, r->admitted};
-                std::memcpy(p.h_stage + static_cast<size_t>(slot) * p.N, r->llr + static_cast<size_t>(r->admitted) * p.N,
-                            sizeof(float) * p.N);
-                h_admit[n_admit++] = (r->code << 24) | slot;
-                ++r->admitted;
-                ++in_flight;
+        // 1. admission of the staged frames
+        for (int i = 0; i < static_cast<int>(pools.size()); ++i) {
+            Pool& p = pools[i];
+            for (int slot : p.ready) {
+                h_admit[n_admit++] = (i << 24) | slot;
+                p.running[slot] = 1;
             }
-            it = (r->admitted == r->n_frames) ? queue.erase(it) : std::next(it);
+            n_running += static_cast<int64_t>(p.ready.size());
+            p.ready.clear();
         }
-        // tiles over the occupied slots of every pool: ranges holding up to tile_frames occupied
-        // slots (free slots inside a range are skipped by the kernel)
+        n_ready = 0;
+        // tiles over the running slots of every pool: ranges holding up to tile_frames running
+        // slots (other slots inside a range are skipped by the kernel)
         for (int i = 0; i < static_cast<int>(pools.size()); ++i) {
             const Pool& p = pools[i];
             int first = -1, count = 0, last = -1;
             for (int slot = 0; slot < p.slots; ++slot) {
-                if (!p.owner[slot].first) continue;
+                if (!p.running[slot]) continue;
                 if (first < 0) first = slot;
                 last = slot;
                 if (++count == p.tile_frames) {
@@ -263,8 +273,10 @@ bool ndgsbp_server::epoch() {
                 stats.iterations += p.h_iters[slot];
                 if (!p.h_ok[slot]) stats.frame_errors_unsatisfied += 1;
                 p.owner[slot] = {nullptr, 0};
+                p.running[slot] = 0;
                 p.free_slots.push_back(slot);
                 --in_flight;
+                --n_running;
                 if (++r->retired == r->n_frames) finished.push_back(r);
             }
             if (n_done) std::sort(p.free_slots.begin(), p.free_slots.end(), std::greater<int>());
@@ -276,12 +288,12 @@ bool ndgsbp_server::epoch() {
             stats.requests_completed += 1;
         }
         stats.epochs += 1;
-        stats.admit_seconds += std::chrono::duration<double>(t1 - t0).count();
         stats.device_seconds += std::chrono::duration<double>(t2 - t1).count();
         stats.harvest_seconds += std::chrono::duration<double>(t3 - t2).count();
         stats.busy_seconds += std::chrono::duration<double>(t3 - t0).count();
     }
     if (!finished.empty()) cv_done.notify_all();
+    cv_stage.notify_one();
     return true;
 }
 
@@ -290,13 +302,59 @@ void ndgsbp_server::run() {
     for (;;) {
         {
             std::unique_lock<std::mutex> lock(mu);
-            cv_work.wait(lock, [&] { return stop || !queue.empty() || in_flight > 0; });
+            cv_work.wait(lock, [&] { return stop || n_ready > 0 || n_running > 0; });
             if (stop) return;
         }
         if (!epoch()) {
             cv_done.notify_all();
             return;
         }
+    }
+}
+
+// Staging thread: places queued frames, in arrival order, into free slots and copies their LLRs
+// to the slots' staging while epochs run; the next epoch admits them.
+void ndgsbp_server::stage() {
+    struct Job {
+        float* dst;
+        const float* src;
+        size_t n;
+        int pool, slot;
+    };
+    std::vector<Job> jobs;
+    jobs.reserve(kStageBatch);
+    for (;;) {
+        jobs.clear();
+        {
+            std::unique_lock<std::mutex> lock(mu);
+            cv_stage.wait(lock, [&] { return stop || can_stage(); });
+            if (stop) return;
+            for (auto it = queue.begin(); it != queue.end() && static_cast<int>(jobs.size()) < kStageBatch;) {
+                Request* r = *it;
+                Pool& p = pools[r->code];
+                while (r->admitted < r->n_frames && !p.free_slots.empty() && static_cast<int>(jobs.size()) < kStageBatch) {
+                    const int slot = p.free_slots.back();
+                    p.free_slots.pop_back();
+                    p.owner[slot] = {r, r->admitted};
+                    jobs.push_back({p.h_stage + static_cast<size_t>(slot) * p.N,
+                                    r->llr + static_cast<size_t>(r->admitted) * p.N, static_cast<size_t>(p.N), r->code,
+                                    slot});
+                    ++r->admitted;
+                    ++in_flight;
+                }
+                it = (r->admitted == r->n_frames) ? queue.erase(it) : std::next(it);
+            }
+        }
+        const auto t0 = Clock::now();
+        for (const Job& j : jobs) std::memcpy(j.dst, j.src, sizeof(float) * j.n);
+        const auto t1 = Clock::now();
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            for (const Job& j : jobs) pools[j.pool].ready.push_back(j.slot);
+            n_ready += static_cast<int64_t>(jobs.size());
+            stats.admit_seconds += std::chrono::duration<double>(t1 - t0).count();
+        }
+        cv_work.notify_one();
     }
 }
 
@@ -412,6 +470,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         hmalloc(reinterpret_cast<void**>(&p.h_done), sizeof(int) * p.slots);
         if (e != cudaSuccess) return fail(NDGSBP_ERR_NOMEM, "server_create: %s", cudaGetErrorString(e));
         p.owner.assign(p.slots, {nullptr, 0});
+        p.running.assign(p.slots, 0);
         for (int s = p.slots - 1; s >= 0; --s) p.free_slots.push_back(s);
         max_tiles += (p.slots + p.tile_frames - 1) / p.tile_frames;
         h->stats.slots_total += p.slots;
@@ -491,6 +550,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     h->max_grid = std::max(1, per_sm * sms);
     ndgsbp_server* raw = h.release();
     raw->worker = std::thread([raw] { raw->run(); });
+    raw->stager = std::thread([raw] { raw->stage(); });
     *out = raw;
     return NDGSBP_OK;
 }
@@ -519,7 +579,7 @@ ndgsbp_status ndgsbp_server_submit(ndgsbp_server* s, int32_t code, const float* 
         s->reqs.emplace(r->ticket, std::move(r));
         s->stats.requests_submitted += 1;
     }
-    s->cv_work.notify_one();
+    s->cv_stage.notify_one();
     return NDGSBP_OK;
 }
 

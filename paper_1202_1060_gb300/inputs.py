@@ -27,7 +27,7 @@ import numpy as np
 __all__ = [
     "Code", "code_from_rows", "gallager_code", "qc_code", "tree_code", "fig1_code",
     "design_rate", "sigma2_from_ebn0", "channel_llr", "random_codeword", "has_4cycle",
-    "code_by_name", "CODE_NAMES", "degree_profile",
+    "code_by_name", "CODE_NAMES", "degree_profile", "write_alist", "read_alist",
 ]
 
 
@@ -101,6 +101,61 @@ def degree_profile(code: Code) -> dict:
     lam = {int(i): float((cd == i).sum() * i / E) for i in np.unique(cd)}
     rho = {int(j): float((rd == j).sum() * j / E) for j in np.unique(rd)}
     return {"lambda": lam, "rho": rho}
+
+
+# ----------------------------------------------------------------------------------------
+# alist files (MacKay's sparse-matrix text format, in which the paper's codes are published)
+# ----------------------------------------------------------------------------------------
+
+def write_alist(code: Code, path: str) -> None:
+    """Write H as an alist file: "N M", the largest column and row weights, the N column and M
+    row weights, then per column its rows and per row its columns (1-based, zero-padded to
+    the largest weight)."""
+    cols = [[] for _ in range(code.N)]
+    for m, r in enumerate(code.rows()):
+        for n in r:
+            cols[int(n)].append(m)
+    rows = [[int(n) for n in r] for r in code.rows()]
+    mc = max((len(c) for c in cols), default=0)
+    mr = max((len(r) for r in rows), default=0)
+    lines = [f"{code.N} {code.M}", f"{mc} {mr}", " ".join(str(len(c)) for c in cols),
+             " ".join(str(len(r)) for r in rows)]
+    lines += [" ".join(str(m + 1) for m in c + [-1] * (mc - len(c))) for c in cols]
+    lines += [" ".join(str(n + 1) for n in r + [-1] * (mr - len(r))) for r in rows]
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+def read_alist(path: str, name: str | None = None) -> Code:
+    """Read an alist file (the format written by write_alist); the row lists define H and the
+    column lists must agree with them."""
+    with open(path) as f:
+        tok = [int(t) for t in f.read().split()]
+    N, M, mc, mr = tok[0], tok[1], tok[2], tok[3]
+    pos = 4
+    cw = tok[pos:pos + N]
+    pos += N
+    rw = tok[pos:pos + M]
+    pos += M
+    cols = []
+    for n in range(N):
+        ent = tok[pos:pos + mc]
+        pos += mc
+        cols.append([m - 1 for m in ent if m > 0])
+        if len(cols[-1]) != cw[n]:
+            raise ValueError(f"column {n + 1}: weight {cw[n]} but {len(cols[-1])} entries")
+    rows = []
+    for m in range(M):
+        ent = tok[pos:pos + mr]
+        pos += mr
+        rows.append([n - 1 for n in ent if n > 0])
+        if len(rows[-1]) != rw[m]:
+            raise ValueError(f"row {m + 1}: weight {rw[m]} but {len(rows[-1])} entries")
+    from_cols = sorted((m, n) for n, c in enumerate(cols) for m in c)
+    from_rows = sorted((m, n) for m, r in enumerate(rows) for n in r)
+    if from_cols != from_rows:
+        raise ValueError("column and row lists disagree")
+    return code_from_rows(rows, N, name=name or path)
 
 
 # ----------------------------------------------------------------------------------------
