@@ -357,7 +357,7 @@ def run_ours(args):
     kname = {nd.VARIANT_QC: "qc_decode_kernel", nd.VARIANT_QC_GLOBAL: "qc_decode_kernel",
              nd.VARIANT_QC_PAIR: "qc_pair_kernel", nd.VARIANT_QC_PAIR_GLOBAL: "qc_pair_kernel",
              nd.VARIANT_QC_FRAMES2: "qc_frames2_kernel", nd.VARIANT_QC_FRAMES2_GLOBAL: "qc_frames2_kernel",
-             nd.VARIANT_TILE: "tile_decode_kernel", nd.VARIANT_QC_TWO_ROUND: "qc_decode_kernel"}.get(plan.variant,
+             nd.VARIANT_TILE: "tile_decode_kernel", nd.VARIANT_QC_DIRECT: "qc_decode_kernel"}.get(plan.variant,
                                                                                             "decode_kernel")
     traffic, traffic_rec = profiled_traffic(kname)
     roofline = {

@@ -70,9 +70,9 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_VARIANT_TILE 7      /* tile kernel: any QC window, degree <= 32, several frames per CTA */
 #define NDGSBP_VARIANT_QC_FRAMES2 8 /* layered QC kernel, two frames per thread, packed FP32 arithmetic */
 #define NDGSBP_VARIANT_QC_FRAMES2_GLOBAL 9 /* the two-frame kernel with messages in global-memory slots */
-#define NDGSBP_VARIANT_QC_TWO_ROUND 10 /* layered QC kernel with both write-back rounds on every edge
-                                         (QC uses direct write-back off shared block columns for
-                                         2-layer windows; results are the same) */
+#define NDGSBP_VARIANT_QC_DIRECT 10 /* layered QC kernel, 2-layer windows: edges off the block
+                                      columns both layers touch are written back at once, one
+                                      ordered round for the rest (same results as QC) */
 
 /* stats counters accumulated by ndgsbp_decode_ex (uint64 each) */
 #define NDGSBP_STAT_FRAMES 0

@@ -171,7 +171,7 @@ ndgsbp_status ndgsbp_autotune(const ndgsbp_groups* groups, const ndgsbp_params* 
             add(NDGSBP_VARIANT_QC_PAIR, 0, cps, 0, 0);
             add(NDGSBP_VARIANT_QC_FRAMES2, 0, cps, 0, 0);
         }
-        add(NDGSBP_VARIANT_QC_TWO_ROUND, 0, 0, 0, 0);
+        add(NDGSBP_VARIANT_QC_DIRECT, 0, 0, 0, 0);
         for (int cps : {0, 2, 3, 4}) add(NDGSBP_VARIANT_QC_FRAMES2_GLOBAL, 0, cps, 0, 0);
     }
     const int maxdeg = g.qc.ok ? g.qc.max_deg : 0;

@@ -364,7 +364,7 @@ static ndgsbp_status validate_params(const ndgsbp_params* p) {
         return fail(NDGSBP_ERR_INVALID, "frames_per_cta must be in [0, 16]");
     if (p->lanes_per_cn != 0 && p->lanes_per_cn != 1 && p->lanes_per_cn != 2 && p->lanes_per_cn != 4)
         return fail(NDGSBP_ERR_INVALID, "lanes_per_cn must be 0, 1, 2 or 4");
-    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_TWO_ROUND)
+    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_DIRECT)
         return fail(NDGSBP_ERR_INVALID, "unknown variant %d", p->variant);
     return NDGSBP_OK;
 }
@@ -447,7 +447,7 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     if (!maxdc) return NDGSBP_OK;
     const bool spec = qc_degrees_specialised(Q, maxdc);
     const bool want_single = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL ||
-                             p->variant == NDGSBP_VARIANT_QC_TWO_ROUND;
+                             p->variant == NDGSBP_VARIANT_QC_DIRECT;
     const bool want_pair = p->variant == NDGSBP_VARIANT_QC_PAIR || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL;
     const bool want_f2 = p->variant == NDGSBP_VARIANT_QC_FRAMES2 || p->variant == NDGSBP_VARIANT_QC_FRAMES2_GLOBAL;
     const bool force_global = p->variant == NDGSBP_VARIANT_QC_GLOBAL || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL ||
@@ -475,7 +475,11 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     if (p_bytes + t_bytes > budget) return NDGSBP_OK;
     const bool msg_smem = !force_global && p_bytes + m_bytes + t_bytes <= budget;
     const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
-    const bool w2 = !pair && Q.window == 2 && !Q.win2.empty() && p->variant != NDGSBP_VARIANT_QC_TWO_ROUND;
+    // direct write-back for 2-layer windows only on request: on GB300 the two-round kernel is
+    // faster (3.37 vs 3.05 Gbit/s on the n=2304 sweep) although it runs one barrier more
+    const bool want_direct = p->variant == NDGSBP_VARIANT_QC_DIRECT;
+    if (want_direct && !(spec && Q.window == 2 && !Q.win2.empty())) return NDGSBP_OK;
+    const bool w2 = !pair && want_direct;
     QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair, w2);
     if (!fn) return NDGSBP_OK;
     int per_sm = 0;
@@ -489,8 +493,7 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     plan.msg_smem = msg_smem;
     ndgsbp_plan& o = plan.pub;
     o.variant = pair ? (msg_smem ? NDGSBP_VARIANT_QC_PAIR : NDGSBP_VARIANT_QC_PAIR_GLOBAL)
-                     : (p->variant == NDGSBP_VARIANT_QC_TWO_ROUND ? NDGSBP_VARIANT_QC_TWO_ROUND
-                                                                  : (msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL));
+                     : (w2 ? NDGSBP_VARIANT_QC_DIRECT : (msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL));
     o.block_threads = threads;
     o.grid = static_cast<int32_t>(grid);
     o.ctas_per_sm = per_sm;

@@ -27,7 +27,7 @@ GROUPS_CYCLIC, GROUPS_NATURAL = 1, 2
 SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
 VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1, 2, 3, 4
 VARIANT_QC_PAIR, VARIANT_QC_PAIR_GLOBAL, VARIANT_TILE = 5, 6, 7
-VARIANT_QC_FRAMES2, VARIANT_QC_FRAMES2_GLOBAL, VARIANT_QC_TWO_ROUND = 8, 9, 10
+VARIANT_QC_FRAMES2, VARIANT_QC_FRAMES2_GLOBAL, VARIANT_QC_DIRECT = 8, 9, 10
 TUNE_TILE_ONLY = 1
 STAT_FRAMES, STAT_FRAME_ERRORS, STAT_BIT_ERRORS, STAT_UNDETECTED = 0, 1, 2, 3
 STAT_ITERATIONS, STAT_UNSATISFIED, STATS_LEN = 4, 5, 8
