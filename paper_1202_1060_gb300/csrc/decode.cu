@@ -746,6 +746,7 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
         C.layer_off = D.layer_off;
         C.group_layers = D.group_layers;
         C.csr_of = D.csr_of;
+        tile_code_finish(C);
         C.ws_msgs = plan.msg_smem ? nullptr : ws + kHeaderBytes;
         a.n_codes = 1;
         a.tiles = nullptr;

@@ -213,11 +213,11 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                 // ---- phase A: Eq. (1) on every CN of the group in every filled slot ----------
                 for (int rr = 0; rr < rounds; ++rr) {
                     const int i = rr * nt + tid;
-                    const int s = i / per_slot;
+                    const int s = fast_div(i, C.div_slot);
                     const bool live = i < work && sh.frame[s] >= 0;
                     const int w = i - s * per_slot;
                     const int cnl = w >> tsh, p = w & (tpc - 1);
-                    const int j = cnl / Z, c = cnl - j * Z;
+                    const int j = fast_div(cnl, C.div_z), c = cnl - j * Z;
                     int L = 0;
                     float t[kLane], old[kLane], xu[kLane], pn[kLane], pe[kLane];
                     float cn = 1.f, ce = 0.f;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                 const int pwork = C.slots * per_pos;
                 for (int jj = 0; jj < W; ++jj) {
                     for (int i = tid; i < pwork; i += nt) {
-                        const int s = i / per_pos;
+                        const int s = fast_div(i, C.div_pos);
                         if (sh.frame[s] < 0) continue;
                         const int w = i - s * per_pos;
                         const int c = w >> tsh, p = w & (tpc - 1);
@@ -320,13 +320,13 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                 const int srounds = (swork + nt - 1) / nt;
                 for (int rr = 0; rr < srounds; ++rr) {
                     const int i = rr * nt + tid;
-                    const int s = i / per_s;
+                    const int s = fast_div(i, C.div_syn);
                     unsigned pbit = 0u;
                     const bool live = i < swork && sh.frame[s] >= 0 && (r.early_stop || sh.iter[s] >= r.max_iter);
                     const int w = i - s * per_s;
                     const int cn_i = w >> tsh, p = w & (tpc - 1);
                     if (live) {
-                        const int l = cn_i / Z, c = cn_i - l * Z;
+                        const int l = fast_div(cn_i, C.div_z), c = cn_i - l * Z;
                         const int k0 = p * le;
                         const int L = min(max(ldeg[l] - k0, 0), le);
                         float* P = reinterpret_cast<float*>(slots_base + static_cast<size_t>(s) * C.slot_bytes);
@@ -405,6 +405,13 @@ size_t tile_table_bytes(const QcLayout& Q) {
     const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;
     const size_t b = static_cast<size_t>(Q.n_layers) * Q.max_deg * 8 + 3 * static_cast<size_t>(Q.n_layers) * 4 + G * Q.window * 4;
     return (b + 15) & ~static_cast<size_t>(15);
+}
+
+void tile_code_finish(TileCode& C) {
+    C.div_slot = make_fastdiv(static_cast<unsigned>(C.window * C.Z * C.tpc));
+    C.div_pos = make_fastdiv(static_cast<unsigned>(C.Z * C.tpc));
+    C.div_syn = make_fastdiv(static_cast<unsigned>(C.nl * C.Z * C.tpc));
+    C.div_z = make_fastdiv(static_cast<unsigned>(C.Z));
 }
 
 int tile_lanes_per_cn(int maxdeg) { return maxdeg <= 8 ? 1 : maxdeg <= 16 ? 2 : maxdeg <= 32 ? 4 : 0; }

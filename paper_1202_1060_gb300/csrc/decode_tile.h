@@ -7,6 +7,25 @@
 
 namespace ndgsbp {
 
+// Division by a divisor fixed for a launch, as a multiply and a shift: q = (n m) >> k with
+// k = 32 + ceil(log2 d) and m = ceil(2^k / d), exact for 0 <= n < 2^32 (2^k >= 2^32 d, so the
+// rounding of m adds less than 1/d to n/d).
+struct FastDiv {
+    unsigned long long m;
+    int k;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    const int k = 32 + l;
+    return FastDiv{((1ull << k) + d - 1) / d, k};
+}
+
+__device__ __forceinline__ int fast_div(int n, FastDiv f) {
+    return static_cast<int>((static_cast<unsigned long long>(static_cast<unsigned>(n)) * f.m) >> f.k);
+}
+
 // One code of a launch: its layered QC description, its batch, and how a CTA lays it out.
 struct TileCode {
     int N, E, Z, nl, G, window, maxdeg, msg_slots;
@@ -33,7 +52,15 @@ struct TileCode {
     int epoch_iters;      // iterations a frame may run in one launch before its state is saved
     int* done_list;       // [pool] slots whose frame retired in this launch (serving), or null
     int* done_count;      // number of entries in done_list (zeroed before the launch)
+    // divisions of the kernel's index arithmetic (set by tile_code_finish)
+    FastDiv div_slot;     // by window * Z * tpc (CN-lanes of one group in one slot)
+    FastDiv div_pos;      // by Z * tpc (CN-lanes of one layer)
+    FastDiv div_syn;      // by nl * Z * tpc (CN-lanes of all layers)
+    FastDiv div_z;        // by Z
 };
+
+// Fills the derived fields of a TileCode whose shape (window, Z, tpc, nl) is set.
+void tile_code_finish(TileCode& C);
 
 constexpr int kSlotFree = 0, kSlotNew = 1, kSlotRunning = 2, kSlotDone = 3;
 

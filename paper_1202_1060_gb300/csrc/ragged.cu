@@ -183,6 +183,7 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         C.layer_off = c.D->layer_off;
         C.group_layers = c.D->group_layers;
         C.csr_of = c.D->csr_of;
+        tile_code_finish(C);
         RunArgs& r = C.r;
         const ndgsbp_batch& b = batches[i];
         r.N = C.N;

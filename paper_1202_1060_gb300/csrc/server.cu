@@ -516,6 +516,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         C.layer_off = p.D->layer_off;
         C.group_layers = p.D->group_layers;
         C.csr_of = p.D->csr_of;
+        tile_code_finish(C);
         C.state_flag = p.flag;
         C.state_iter = p.st_iter;
         C.state_P = p.st_P;

@@ -241,7 +241,9 @@ def test_variants_and_block_sizes_agree_bitwise(env, name, kind, qc, msg):
         others += [dict(variant=nd.VARIANT_QC), dict(variant=nd.VARIANT_QC_GLOBAL),
                    dict(variant=nd.VARIANT_QC_PAIR), dict(variant=nd.VARIANT_QC_PAIR_GLOBAL),
                    dict(variant=nd.VARIANT_QC_FRAMES2), dict(variant=nd.VARIANT_QC_FRAMES2_GLOBAL),
-                   dict(variant=nd.VARIANT_QC_FRAMES2, ctas_per_sm=1), dict(variant=nd.VARIANT_QC_DIRECT)]
+                   dict(variant=nd.VARIANT_QC_FRAMES2, ctas_per_sm=1)]
+        if kind in ("layers_cyclic", "layers_linear"):   # 2-layer windows
+            others.append(dict(variant=nd.VARIANT_QC_DIRECT))
     for kw in others:
         other = _run(nd, torch, g, c, llr, **kw0, **kw)
         if kw["variant"] >= nd.VARIANT_QC:
