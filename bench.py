@@ -367,6 +367,7 @@ def run_ours(args):
                 f"kernel over its CUDA-event time; peak = {MUFU_PER_CLK_PER_SM} MUFU/clk/SM x {sms} SMs x "
                 f"{peak_clock_mhz:.0f} MHz (clock from MEASURED_PEAKS.json, {peak_kind})",
         "kernel": kname, "launches": len(dec_ms), "avg_launch_ms": sum(dec_ms) / len(dec_ms),
+        "share_of_step": sum(dec_ms) / 1e3 / elapsed,
         "edge_updates_per_launch": edge_updates_iter * iter_sum / len(dec_ms),
         "hbm_bytes_per_launch_algorithmic": F * (c.N * 4 + W * 4 + 5),
         "hbm_frac_of_measured": F * (c.N * 4 + W * 4 + 5) / (sum(dec_ms) / len(dec_ms) / 1e3) / 1e9 / peaks["hbm_gbs"],

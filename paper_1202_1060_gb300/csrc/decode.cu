@@ -343,6 +343,7 @@ struct Plan {
     int tile_tpc = 1, tile_le = 1, tile_slots = 1, tile_slot_bytes = 0, tile_p_bytes = 0, tile_m_bytes = 0;
     int tile_delta_stride = 1, tile_frames = 1, tile_table_bytes = 0, n_tiles = 0;
     bool msg_smem = false, delta_smem = false;
+    bool qc_w2 = false;   // QC kernel with the 2-layer window tables
     const Layout* L = nullptr;
     const DeviceLayout* D = nullptr;
     const QcLayout* Q = nullptr;
@@ -468,18 +469,18 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     const int active = pair ? active_pair : Q.window * Q.Z;
     const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
     if (threads < active || threads > (pair ? qc_pair_max_threads(maxdc) : max_threads_for(maxdc))) return NDGSBP_OK;
-    const size_t budget = static_cast<size_t>(di.smem_optin) - 64;
-    const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 4);
-    const size_t m_bytes = align16(static_cast<size_t>(Q.msg_slots) * msg_size(p->msg_dtype));
-    const size_t t_bytes = qc_table_bytes(Q);
-    if (p_bytes + t_bytes > budget) return NDGSBP_OK;
-    const bool msg_smem = !force_global && p_bytes + m_bytes + t_bytes <= budget;
-    const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
     // direct write-back for 2-layer windows only on request: on GB300 the two-round kernel is
     // faster (3.37 vs 3.05 Gbit/s on the n=2304 sweep) although it runs one barrier more
     const bool want_direct = p->variant == NDGSBP_VARIANT_QC_DIRECT;
     if (want_direct && !(spec && Q.window == 2 && !Q.win2.empty())) return NDGSBP_OK;
     const bool w2 = !pair && want_direct;
+    const size_t budget = static_cast<size_t>(di.smem_optin) - 64;
+    const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 4);
+    const size_t m_bytes = align16(static_cast<size_t>(Q.msg_slots) * msg_size(p->msg_dtype));
+    const size_t t_bytes = qc_table_bytes(Q, w2);
+    if (p_bytes + t_bytes > budget) return NDGSBP_OK;
+    const bool msg_smem = !force_global && p_bytes + m_bytes + t_bytes <= budget;
+    const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
     QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair, w2);
     if (!fn) return NDGSBP_OK;
     int per_sm = 0;
@@ -491,6 +492,7 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     plan.qc = true;
     plan.qfn = fn;
     plan.msg_smem = msg_smem;
+    plan.qc_w2 = w2;
     ndgsbp_plan& o = plan.pub;
     o.variant = pair ? (msg_smem ? NDGSBP_VARIANT_QC_PAIR : NDGSBP_VARIANT_QC_PAIR_GLOBAL)
                      : (w2 ? NDGSBP_VARIANT_QC_DIRECT : (msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL));
@@ -760,7 +762,7 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
         std::memset(&a, 0, sizeof(a));
         fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior,
                  extras);
-        fill_qc_args(a, *plan.Q, *plan.DQ, plan.msg_smem ? nullptr : ws + kHeaderBytes);
+        fill_qc_args(a, *plan.Q, *plan.DQ, plan.msg_smem ? nullptr : ws + kHeaderBytes, plan.qc_w2);
         plan.qfn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
     } else {
         const Layout& L = *plan.L;

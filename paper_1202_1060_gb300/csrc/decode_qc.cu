@@ -509,15 +509,15 @@ QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bo
 
 static size_t a16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
-size_t qc_table_bytes(const QcLayout& Q) {
+size_t qc_table_bytes(const QcLayout& Q, bool w2) {
     const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;
     size_t b = a16(static_cast<size_t>(Q.n_layers) * Q.max_deg * 8) + 3 * a16(static_cast<size_t>(Q.n_layers) * 4) +
                a16(G * Q.window * 4);
-    if (!Q.win2.empty()) b += a16(G * 2 * 4) + a16(static_cast<size_t>(Q.Z) * (Q.max_deg | 1) * 4);
+    if (w2) b += a16(G * 2 * 4) + a16(static_cast<size_t>(Q.Z) * (Q.max_deg | 1) * 4);
     return b;
 }
 
-void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs) {
+void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs, bool w2) {
     a.Z = Q.Z;
     a.nl = Q.n_layers;
     a.window = Q.window;
@@ -531,7 +531,7 @@ void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs
     a.group_layers = D.group_layers;
     a.csr_of = D.csr_of;
     a.ws_msgs = ws_msgs;
-    a.win2 = reinterpret_cast<const int2*>(D.win2);
+    a.win2 = w2 ? reinterpret_cast<const int2*>(D.win2) : nullptr;
 }
 
 }  // namespace ndgsbp

@@ -28,7 +28,8 @@ QcKernelFn pick_qc_frames2_kernel(int msg_dtype, int maxdc, bool msg_smem);
 int qc_frames2_max_threads(int maxdc);
 bool qc_degrees_specialised(const QcLayout& Q, int maxdc);
 int qc_pair_max_threads(int maxdc);
-size_t qc_table_bytes(const QcLayout& Q);
-void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs);
+// Shared bytes of a launch's tables (w2: with the 2-layer window masks and change buffer).
+size_t qc_table_bytes(const QcLayout& Q, bool w2 = false);
+void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs, bool w2 = false);
 
 }  // namespace ndgsbp

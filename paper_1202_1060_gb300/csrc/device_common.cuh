@@ -103,7 +103,8 @@ __device__ __forceinline__ void check_node_update(const float (&t)[MAXDC], int d
             cn = cn * n;
         }
     }
-    const unsigned par = __popc(sbits) & 1u;
+    // bit k of sflip = sign of output k: the parity of all input signs xor sign k
+    const unsigned sflip = sbits ^ (0u - (__popc(sbits) & 1u));
     float sn = 1.f, se = 0.f;
 #pragma unroll
     for (int k = MAXDC - 1; k >= 0; --k) {
@@ -114,7 +115,7 @@ __device__ __forceinline__ void check_node_update(const float (&t)[MAXDC], int d
             const float ee = fmaf(pe[k], sn + se, pn[k] * se);
             const float w = fmaf(en * rcp_approx(ee), 2.f, 1.f);
             const float mag = fminf(0.69314718055994531f * lg2_approx(w), lim);
-            const unsigned sgn = ((par ^ (sbits >> k)) & 1u) << 31;
+            const unsigned sgn = (sflip << (31 - k)) & 0x80000000u;
             emit(k, __uint_as_float(__float_as_uint(mag) | sgn));
             se = fmaf(se, n + u, sn * u);
             sn = sn * n;

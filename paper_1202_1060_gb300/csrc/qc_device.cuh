@@ -42,7 +42,8 @@ __device__ __forceinline__ void check_node_update2(const float2 (&t)[D], float l
         ce = __ffma2_rn(ce, __fadd2_rn(n, u), __fmul2_rn(cn, u));
         cn = __fmul2_rn(cn, n);
     }
-    const unsigned par0 = __popc(sb0) & 1u, par1 = __popc(sb1) & 1u;
+    // bit k of sf0 / sf1 = sign of output k: the parity of all input signs xor sign k
+    const unsigned sf0 = sb0 ^ (0u - (__popc(sb0) & 1u)), sf1 = sb1 ^ (0u - (__popc(sb1) & 1u));
     float2 sn = f2(1.f), se = f2(0.f);
 #pragma unroll
     for (int k = D - 1; k >= 0; --k) {
@@ -53,7 +54,7 @@ __device__ __forceinline__ void check_node_update2(const float2 (&t)[D], float l
         const float2 w = __ffma2_rn(__fmul2_rn(en, make_float2(rcp_approx(ee.x), rcp_approx(ee.y))), f2(2.f), f2(1.f));
         const float2 lg = __fmul2_rn(f2(0.69314718055994531f), make_float2(lg2_approx(w.x), lg2_approx(w.y)));
         const float m0 = fminf(lg.x, lim), m1 = fminf(lg.y, lim);
-        const unsigned g0 = ((par0 ^ (sb0 >> k)) & 1u) << 31, g1 = ((par1 ^ (sb1 >> k)) & 1u) << 31;
+        const unsigned g0 = (sf0 << (31 - k)) & 0x80000000u, g1 = (sf1 << (31 - k)) & 0x80000000u;
         emit(k, make_float2(__uint_as_float(__float_as_uint(m0) | g0), __uint_as_float(__float_as_uint(m1) | g1)));
         se = __ffma2_rn(se, __fadd2_rn(n, u), __fmul2_rn(sn, u));
         sn = __fmul2_rn(sn, n);
