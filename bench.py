@@ -393,6 +393,10 @@ def run_ours(args):
         cpu["oracle_fer"] = [f / args.cpu_frames for f in fe_or]
         cpu["oracle_fer_ci95"] = fer_ci
         cpu["gpu_fer_inside_ci"] = all(lo <= g <= hi for g, (lo, hi) in zip(fer, fer_ci))
+        # the same oracle on one core (a smaller sample)
+        dt1, nf1, _ = oracle_sweep(args.cpu_frames_1core, threads=1)
+        cpu["one_core"] = {"value": nf1 * 1152 / dt1 / 1e9, "unit": "Gbit/s", "cores": 1,
+                           "sample": f"{args.cpu_frames_1core} frames at each of the {len(EBN0)} points, {dt1:.1f} s"}
 
     if rank == 0:
         line = {
@@ -858,6 +862,7 @@ def main():
     ap.add_argument("--frames", type=int, default=FRAMES, help="frames per Eb/N0 point per GPU")
     ap.add_argument("--variant", type=int, default=0, help="decode variant (0 = library choice)")
     ap.add_argument("--cpu-frames", type=int, default=4096, help="oracle sample per Eb/N0 point")
+    ap.add_argument("--cpu-frames-1core", type=int, default=64, help="one-core oracle sample per Eb/N0 point")
     ap.add_argument("--ref-frames", type=int, default=64, help="oracle frames per point per reference step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -95,7 +95,9 @@ typedef struct ndgsbp_params {
     int32_t early_stop;     /* 1: stop a frame at the first zero syndrome (Step 4 b) */
     int32_t variant;        /* NDGSBP_VARIANT_* */
     int32_t block_threads;  /* 0 = chosen by the library; else a multiple of 32, <= 1024 */
-    int32_t ctas_per_sm;    /* 0 = as many as fit; else an upper bound */
+    int32_t ctas_per_sm;    /* 0 = as many as fit; else an upper bound (for the TILE variant and
+                               ragged launches also the residency target that caps each CTA's
+                               shared memory at 1/ctas_per_sm of the SM's) */
     int32_t frames_per_cta; /* TILE variant: frame slots per CTA, 0 = library choice, <= 16 */
     int32_t lanes_per_cn;   /* TILE variant: threads per CN (1, 2 or 4), 0 = library choice */
 } ndgsbp_params;
@@ -289,8 +291,9 @@ ndgsbp_status ndgsbp_ragged_destroy(ndgsbp_ragged* ragged);
  * [n_frames][N] (a representative sample: the iteration counts follow its noise level) and
  * returns the fastest in result->best: params with variant, block_threads, ctas_per_sm,
  * frames_per_cta and lanes_per_cn filled in (the other fields as given).  Candidates are the
- * library's default choice, the QC kernels at 0/1/2 CTAs per SM, and tile shapes (1, 2 or 4
- * lanes per CN x 1..16 frames per CTA x 128..512 threads) that the plan accepts.  Each
+ * library's default choice, the QC kernels at 0/1/2 CTAs per SM (single-frame, two-frame, pair
+ * and direct write-back forms), and tile shapes (1, 2 or 4 lanes per CN x 1..16 frames per CTA
+ * x 128..512 threads, at the default residency and at 1 CTA per SM) that the plan accepts.  Each
  * candidate is an ordinary decode into the tuner's own scratch buffers: one untimed call, then
  * the median of three timed by CUDA events on a private stream.  Shapes with the same lanes
  * per CN give bit-identical results; more lanes per CN split a CN's edges between lanes and so

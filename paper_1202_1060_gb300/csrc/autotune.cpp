@@ -183,6 +183,8 @@ ndgsbp_status ndgsbp_autotune(const ndgsbp_groups* groups, const ndgsbp_params* 
             for (int t : threads_list) {
                 if (tile_only && params->block_threads && t != threads_list[0]) continue;
                 add(NDGSBP_VARIANT_TILE, t, params->ctas_per_sm, fpc, lanes);
+                // one CTA per SM with the whole SM's shared memory (messages on chip when they fit)
+                if (!tile_only && !params->ctas_per_sm) add(NDGSBP_VARIANT_TILE, t, 1, fpc, lanes);
             }
     }
     if (cand.empty()) return fail(NDGSBP_ERR_UNSUPPORTED, "autotune: no launch shape fits this grouping");

@@ -371,13 +371,15 @@ static ndgsbp_status validate_params(const ndgsbp_params* p) {
 }
 
 struct DeviceInfo {
-    int dev = 0, sms = 0, smem_optin = 0;
+    int dev = 0, sms = 0, smem_optin = 0, smem_sm = 0, smem_reserved = 0;
 };
 
 static ndgsbp_status device_info(DeviceInfo& di) {
     CUDA_TRY(cudaGetDevice(&di.dev));
     CUDA_TRY(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, di.dev));
     CUDA_TRY(cudaDeviceGetAttribute(&di.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, di.dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&di.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, di.dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&di.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, di.dev));
     return NDGSBP_OK;
 }
 
@@ -523,11 +525,20 @@ static ndgsbp_status make_tile_plan(const Groups& g, const ndgsbp_params* p, int
     const int ds = Q.max_deg | 1;
     const int per_slot = Q.window * Q.Z * tpc;
     int threads = p->block_threads ? p->block_threads : std::min(512, std::max(128, (per_slot + 31) / 32 * 32));
-    const size_t budget = static_cast<size_t>(di.smem_optin) - 256;
     const size_t table = tile_table_bytes(Q);
     const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 4);
     const size_t m_bytes = align16(static_cast<size_t>(Q.msg_slots) * msg_size(p->msg_dtype));
     const size_t d_bytes = align16(static_cast<size_t>(Q.window) * Q.Z * ds * 4);
+    // Shared memory per CTA under a residency target of k CTAs per SM: ctas_per_sm when set,
+    // else 2 when a frame's posterior and deltas fit under half an SM, else 1.  Messages that
+    // do not fit under the cap live in workspace slots (a code whose messages would fill a whole
+    // SM runs two CTAs with global messages rather than one with shared ones).
+    auto cap_for = [&](int k) {
+        const size_t per = static_cast<size_t>(di.smem_sm) / k - static_cast<size_t>(di.smem_reserved) - 1024;
+        return std::min(static_cast<size_t>(di.smem_optin) - 256, per) & ~static_cast<size_t>(15);
+    };
+    const int target = p->ctas_per_sm > 0 ? p->ctas_per_sm : (table + p_bytes + d_bytes <= cap_for(2) ? 2 : 1);
+    const size_t budget = cap_for(target);
     const bool msg_smem = p->variant != NDGSBP_VARIANT_GLOBAL && table + p_bytes + m_bytes + d_bytes <= budget;
     const size_t slot_bytes = p_bytes + (msg_smem ? m_bytes : 0) + d_bytes;
     if (table + slot_bytes > budget) return NDGSBP_OK;
