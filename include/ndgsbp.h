@@ -384,6 +384,33 @@ ndgsbp_status ndgsbp_server_stats_get(ndgsbp_server* server, ndgsbp_server_stats
 /* Stops the worker (finishing the epoch in flight) and frees the pools. */
 ndgsbp_status ndgsbp_server_destroy(ndgsbp_server* server);
 
+/* ---- Gaussian-approximation analysis (Sec. III), FP64 on the GPU ----------------------------
+ * The GA mean recursion for the flooding schedule (Eq. (4) with every other CN of class a, then
+ * Eqs. (15)-(16)): mu_v,i = mu0 + (i - 1) mu_c and mu_c <- sum_j rho_j Phi^-1(1 - (1 - sum_i
+ * lambda_i Phi(mu_v,i))^(j-1)), from mu_c = 0, with mu0 = 2 / sigma^2 and sigma^2 =
+ * 1 / (2 rate 10^(Eb/N0 / 10)), evaluated for n_points Eb/N0 values at once in FP64 (one warp per
+ * point).  phi_kind: EXACT = Eq. (14) by the trapezoidal rule (769 nodes over x in [-12, 12], T =
+ * mu + 2 sqrt(mu) x), CLOSED = the closed-form approximation of the GA analysis the paper cites
+ * (the form that reproduces Table I's thresholds).  lambda[i] / rho[j]: edge-perspective degree
+ * fractions indexed by degree, i <= dv_max <= 64, j <= dc_max <= 64 (Sec. II-B).  Per point (host
+ * arrays, written before return): converged = 1 when mu_c reached mu_cap (error-free decoding),
+ * iters = the iteration at which it did, or at which mu_c stopped moving (a fixed point: relative
+ * change <= 1e-12), or max_iter; mu_c = the last CN mean.  Synchronous; allocates device memory.
+ * Errors: INVALID, CUDA. */
+#define NDGSBP_GA_PHI_EXACT 0
+#define NDGSBP_GA_PHI_CLOSED 1
+ndgsbp_status ndgsbp_ga_flood(const double* lambda, int32_t dv_max, const double* rho, int32_t dc_max,
+                              double rate, const double* ebn0_db, int32_t n_points, int32_t phi_kind,
+                              int32_t max_iter, double mu_cap, uint8_t* converged, int32_t* iters,
+                              double* mu_c);
+/* GA threshold: the smallest Eb/N0 in [lo_db, hi_db] at which ndgsbp_ga_flood converges, found
+ * by refining the bracketing pair of a 64-point grid until it is narrower than tol_db; the upper
+ * end of the final pair is returned.  Errors: INVALID, INFEASIBLE (no convergence at hi_db), CUDA. */
+ndgsbp_status ndgsbp_ga_flood_threshold(const double* lambda, int32_t dv_max, const double* rho,
+                                        int32_t dc_max, double rate, int32_t phi_kind,
+                                        int32_t max_iter, double mu_cap, double lo_db, double hi_db,
+                                        double tol_db, double* threshold_db);
+
 /* ---- Decoding without allocating (the paper has no counterpart) ---------------------------
  * ndgsbp_decode_static is ndgsbp_decode without a workspace: it allocates no device memory.  It
  * is for callers that cannot allocate while they decode -- a real-time receive loop that may

@@ -29,6 +29,7 @@ VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1
 VARIANT_QC_PAIR, VARIANT_QC_PAIR_GLOBAL, VARIANT_TILE = 5, 6, 7
 VARIANT_QC_FRAMES2, VARIANT_QC_FRAMES2_GLOBAL, VARIANT_QC_DIRECT = 8, 9, 10
 TUNE_TILE_ONLY = 1
+GA_PHI_EXACT, GA_PHI_CLOSED = 0, 1
 STAT_FRAMES, STAT_FRAME_ERRORS, STAT_BIT_ERRORS, STAT_UNDETECTED = 0, 1, 2, 3
 STAT_ITERATIONS, STAT_UNSATISFIED, STATS_LEN = 4, 5, 8
 
@@ -122,6 +123,9 @@ _SIGS = {
                                ctypes.POINTER(TuneResult)]),
     "ndgsbp_ragged_autotune": (_I32, [_P, _I32, ctypes.POINTER(Params), _I64, ctypes.c_char_p,
                                       ctypes.POINTER(Params), ctypes.POINTER(_D)]),
+    "ndgsbp_ga_flood": (_I32, [_P, _I32, _P, _I32, _D, _P, _I32, _I32, _I32, _D, _P, _P, _P]),
+    "ndgsbp_ga_flood_threshold": (_I32, [_P, _I32, _P, _I32, _D, _I32, _I32, _D, _D, _D, _D,
+                                         ctypes.POINTER(_D)]),
     "ndgsbp_server_create": (_I32, [_P, _I32, _P, ctypes.POINTER(Params), ctypes.c_size_t, _I32,
                                     ctypes.POINTER(_P)]),
     "ndgsbp_server_submit": (_I32, [_P, _I32, _P, _I64, _P, _P, _P, ctypes.POINTER(_I64)]),
@@ -495,6 +499,40 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def _degree_array(frac: dict):
+    d = max(frac)
+    a = np.zeros(d + 1, np.float64)
+    for k, v in frac.items():
+        a[k] = v
+    return a, d
+
+
+def ga_flood(lam: dict, rho: dict, rate: float, ebn0_db, phi_kind: int = GA_PHI_EXACT, max_iter: int = 20000,
+             mu_cap: float = 60.0):
+    """ndgsbp_ga_flood: (converged bool [n], iterations int [n], mu_c [n]) for each Eb/N0."""
+    la, dv = _degree_array(lam)
+    ra, dc = _degree_array(rho)
+    e = np.ascontiguousarray(np.atleast_1d(ebn0_db), np.float64)
+    n = e.size
+    cv = np.zeros(n, np.uint8)
+    it = np.zeros(n, np.int32)
+    mu = np.zeros(n, np.float64)
+    _check(_lib.ndgsbp_ga_flood(_hptr(la), dv, _hptr(ra), dc, float(rate), _hptr(e), n, int(phi_kind),
+                                int(max_iter), float(mu_cap), _hptr(cv), _hptr(it), _hptr(mu)))
+    return cv.astype(bool), it, mu
+
+
+def ga_flood_threshold(lam: dict, rho: dict, rate: float, phi_kind: int = GA_PHI_EXACT, lo_db: float = 0.0,
+                       hi_db: float = 3.0, tol_db: float = 1e-4, max_iter: int = 20000, mu_cap: float = 60.0) -> float:
+    la, dv = _degree_array(lam)
+    ra, dc = _degree_array(rho)
+    out = ctypes.c_double()
+    _check(_lib.ndgsbp_ga_flood_threshold(_hptr(la), dv, _hptr(ra), dc, float(rate), int(phi_kind), int(max_iter),
+                                          float(mu_cap), float(lo_db), float(hi_db), float(tol_db),
+                                          ctypes.byref(out)))
+    return out.value
 
 
 def unpack_bits(words, N: int):
