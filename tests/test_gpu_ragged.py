@@ -126,3 +126,40 @@ def test_ragged_graph_replay(env):
     torch.cuda.synchronize()
     for b, (h, it) in zip(batches, saved):
         assert torch.equal(b["hard_bits"], h) and torch.equal(b["iters"], it)
+
+
+def test_ragged_empty_batch_and_residency_targets(env):
+    """A batch with no frames in the mix, and every residency target (CTAs per SM): results are
+    those of each code alone; a target under which a code's frame slot cannot fit is refused."""
+    nd, torch = env
+    batches = _setup(nd, torch, [60, 0, 40, 12], "f16", seed=3)
+    alone = []
+    for b in batches:
+        if b["llr"].shape[0] == 0:
+            alone.append(None)
+            continue
+        p = nd.params_default(max_iter=20, msg_dtype=nd.F16)
+        lanes = {8: 1, 16: 2, 32: 4}[min(x for x in (8, 16, 32) if x >= int(b["c"].row_degrees().max()))]
+        alone.append(_alone(nd, torch, b, p, lanes))
+    torch.cuda.synchronize()
+    ran = 0
+    for k in (1, 2, 3, 4):
+        params = nd.params_default(max_iter=20, msg_dtype=nd.F16, ctas_per_sm=k)
+        try:
+            rg = nd.Ragged(batches, params)
+        except nd.NdgsbpError as e:
+            assert e.status == nd.ERR_UNSUPPORTED and k >= 3, (k, str(e))
+            continue
+        plan, _ = rg.info()
+        assert plan["ctas_per_sm"] <= k
+        for b in batches:
+            b["hard_bits"].zero_()
+            b["iters"].zero_()
+        rg.launch()
+        torch.cuda.synchronize()
+        for b, a in zip(batches, alone):
+            if a is None:
+                continue
+            assert torch.equal(b["hard_bits"], a[0]) and torch.equal(b["iters"], a[1]), (k, b["c"].name)
+        ran += 1
+    assert ran >= 2
