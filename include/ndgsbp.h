@@ -54,6 +54,11 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_UNIT_LAYER 1      /* groups are built from layers of Z consecutive CNs (QC codes) */
 #define NDGSBP_GROUPS_CYCLIC 1   /* G windows around a ring of units (see ndgsbp_group_sizes) */
 #define NDGSBP_GROUPS_NATURAL 2  /* take units in index order instead of drawing them at random */
+#define NDGSBP_GROUPS_STRUCTURED 4 /* CN units only: group 1 and the overlaps as in Step 1; the fresh
+                                      CNs of group g >= 2 are picked greedily, each adding the most
+                                      VNs of the previous group's VN neighbourhood not yet reached
+                                      by group g (raises the CoCSG l of Sec. II-A), ties broken by
+                                      the random draw order */
 
 /* schedules */
 #define NDGSBP_SCHEDULE_GROUPS 0 /* the groups of the handle: GSBP when disjoint, NDGSBP when not */

@@ -147,6 +147,42 @@ def groups(M: int, G: int, r: float, seed: int, unit: int = 1, cyclic: bool = Fa
     return gp, gc[:n].copy()
 
 
+def groups_structured(code, G: int, r: float, seed: int):
+    """Structure-aware Step 1 (the CoCSG-raising direction the paper names as future work):
+    group 1 and every overlap as in Step 1 (linear groups of CNs); the fresh CNs of group g >= 2
+    are picked one at a time, each the unused CN adding the most VNs of the previous group's VN
+    neighbourhood N(G_{g-1}) that group g does not reach yet; ties go to the earlier CN in the
+    Fisher-Yates order of SplitMix64(seed) (the order Step 1 draws from).  Returns (grp_ptr,
+    grp_cn) like ``groups``."""
+    M = code.M
+    NG, o, fresh = group_sizes(M, G, r)
+    order = [int(m) for m in groups(M, 1, 0.0, seed, unit=1, cyclic=True)[1]]   # the full draw
+    rows = [set(int(v) for v in row) for row in code.rows()]
+    out = [order[:NG]]
+    used = set(out[0])
+    for g in range(1, G):
+        prev = out[g - 1]
+        nbr = set().union(*(rows[m] for m in prev))
+        cur = prev[len(prev) - o:]
+        reach = set().union(*(rows[m] for m in cur)) if cur else set()
+        for _ in range(int(fresh[g])):
+            best, best_gain = None, -1
+            for i in range(NG, M):
+                m = order[i]
+                if m in used:
+                    continue
+                gain = len((rows[m] & nbr) - reach)
+                if gain > best_gain:
+                    best, best_gain = m, gain
+            used.add(best)
+            cur.append(best)
+            reach |= rows[best]
+        out.append(cur)
+    gp = np.zeros(G + 1, np.int32)
+    gp[1:] = np.cumsum([len(x) for x in out])
+    return gp, np.asarray([m for x in out for m in x], np.int32)
+
+
 def budget_iters(M: int, G: int, NG: int, r: float, imax: int) -> int:
     """Equal-complexity iteration allowance of Sec. IV: M I_max / (M + (G-1) N_G r)."""
     return int(_load().oracle_budget_iters(M, G, NG, float(r), imax))

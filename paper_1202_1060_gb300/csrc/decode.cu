@@ -483,7 +483,14 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     if (p_bytes + t_bytes > budget) return NDGSBP_OK;
     const bool msg_smem = !force_global && p_bytes + m_bytes + t_bytes <= budget;
     const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
-    QcKernelFn fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair, w2);
+    // 16-bit messages halve the shared memory of a frame: when 6 CTAs fit, use the instance
+    // compiled for 6 resident CTAs (56 registers) instead of the 64-register one (5 CTAs)
+    QcKernelFn fn = nullptr;
+    const bool occ_ok = !pair && !w2 && spec && maxdc == 8 && msg_smem && p->msg_dtype != NDGSBP_F32 &&
+                        threads <= qc_occ_threads() && (p->ctas_per_sm == 0 || p->ctas_per_sm >= 6) &&
+                        6 * (smem + static_cast<size_t>(di.smem_reserved) + 1024) <= static_cast<size_t>(di.smem_sm);
+    if (occ_ok) fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair, w2, true);
+    if (!fn) fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair, w2);
     if (!fn) return NDGSBP_OK;
     int per_sm = 0;
     int64_t grid = 0;

@@ -211,8 +211,13 @@ __device__ __forceinline__ void qc_frame_messages_out(const QcArgs& a, const Msg
     }
 }
 
-template <typename MsgT, bool MSG_SMEM, int MAXDC, bool SPEC, bool W2>
-__global__ void __launch_bounds__(max_threads_for(MAXDC)) qc_decode_kernel(const QcArgs a) {
+// OCC > 0: an instance for blocks of at most kOccThreads threads compiled for OCC resident CTAs
+// per SM (fewer registers), for launches whose shared memory allows that many.
+constexpr int kOccThreads = 192;
+
+template <typename MsgT, bool MSG_SMEM, int MAXDC, bool SPEC, bool W2, int OCC = 0>
+__global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OCC ? OCC : 1)
+    qc_decode_kernel(const QcArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_frame;
     __shared__ unsigned s_err;
@@ -478,7 +483,12 @@ static QcKernelFn pick_qc_storage(bool msg_smem, bool spec, bool pair, bool w2) 
 }
 
 template <typename MsgT>
-static QcKernelFn pick_qc_degree(int maxdc, bool msg_smem, bool spec, bool pair, bool w2) {
+static QcKernelFn pick_qc_degree(int maxdc, bool msg_smem, bool spec, bool pair, bool w2, bool occ6) {
+    if (occ6) {
+        // 6 CTAs of <= 192 threads per SM: degree <= 8, messages in shared memory, 16-bit storage
+        if (maxdc != 8 || !msg_smem || !spec || pair || w2 || sizeof(MsgT) != 2) return nullptr;
+        return qc_decode_kernel<MsgT, true, 8, true, false, 6>;
+    }
     switch (maxdc) {
         case 8: return pick_qc_storage<MsgT, 8>(msg_smem, spec, pair, w2);
         case 16: return pick_qc_storage<MsgT, 16>(msg_smem, spec, pair, w2);
@@ -498,11 +508,13 @@ bool qc_degrees_specialised(const QcLayout& Q, int maxdc) {
 
 int qc_pair_max_threads(int maxdc) { return pair_max_threads(maxdc); }
 
-QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair, bool w2) {
+int qc_occ_threads() { return kOccThreads; }
+
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair, bool w2, bool occ6) {
     switch (msg_dtype) {
-        case NDGSBP_F32: return pick_qc_degree<float>(maxdc, msg_smem, spec, pair, w2);
-        case NDGSBP_F16: return pick_qc_degree<__half>(maxdc, msg_smem, spec, pair, w2);
-        case NDGSBP_BF16: return pick_qc_degree<__nv_bfloat16>(maxdc, msg_smem, spec, pair, w2);
+        case NDGSBP_F32: return pick_qc_degree<float>(maxdc, msg_smem, spec, pair, w2, occ6);
+        case NDGSBP_F16: return pick_qc_degree<__half>(maxdc, msg_smem, spec, pair, w2, occ6);
+        case NDGSBP_BF16: return pick_qc_degree<__nv_bfloat16>(maxdc, msg_smem, spec, pair, w2, occ6);
         default: return nullptr;
     }
 }

@@ -22,7 +22,11 @@ struct QcArgs {
 typedef void (*QcKernelFn)(const QcArgs);
 
 // w2: the 2-layer-window instance (direct write-back off shared block columns; needs win2).
-QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair, bool w2 = false);
+// occ6: the instance compiled for 6 resident CTAs of at most qc_occ_threads() threads (16-bit
+// messages in shared memory, degree <= 8); nullptr when it does not apply.
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair, bool w2 = false,
+                          bool occ6 = false);
+int qc_occ_threads();
 // Two frames per thread (decode_qc2.cu); degree-specialised codes with MAXDC 8 or 16 only.
 QcKernelFn pick_qc_frames2_kernel(int msg_dtype, int maxdc, bool msg_smem);
 int qc_frames2_max_threads(int maxdc);

@@ -85,8 +85,51 @@ static ndgsbp_status group_sizes(int Mu, int G, double r, int flags, int* NG, in
 
 // Step 1 of Sec. II-C on unit indices.  Draws are forward Fisher-Yates steps over the pool of
 // unused units; a group's overlap is the tail of its predecessor.
+// Structure-aware Step 1 (the paper's future-work direction of choosing groups for a larger
+// CoCSG l, the number of VNs two consecutive groups share): group 1 and every overlap as in
+// Step 1; the f_g fresh CNs of group g >= 2 are picked one at a time, each the unused CN that
+// adds the most VNs of N(G_{g-1}) not yet in N(G_g) (a greedy for |N(G_g) & N(G_{g-1})|), ties
+// going to the earlier CN of the random draw order (the rest of the Fisher-Yates draw).
+static void structured_groups(const Code& c, int G, int NG, int o, const std::vector<int>& fresh,
+                              const std::vector<int>& pool, std::vector<std::vector<int>>& groups) {
+    std::vector<char> used(c.M, 0), in_prev(c.N, 0), covered(c.N, 0);
+    groups.assign(G, {});
+    groups[0].assign(pool.begin(), pool.begin() + NG);
+    for (int m : groups[0]) used[m] = 1;
+    for (int g = 1; g < G; ++g) {
+        const std::vector<int>& prev = groups[g - 1];
+        std::fill(in_prev.begin(), in_prev.end(), 0);
+        std::fill(covered.begin(), covered.end(), 0);
+        for (int m : prev)
+            for (int e = c.row_ptr[m]; e < c.row_ptr[m + 1]; ++e) in_prev[c.col_idx[e]] = 1;
+        groups[g].assign(prev.end() - o, prev.end());
+        for (int m : groups[g])
+            for (int e = c.row_ptr[m]; e < c.row_ptr[m + 1]; ++e) covered[c.col_idx[e]] = 1;
+        for (int k = 0; k < fresh[g]; ++k) {
+            int best = -1, best_gain = -1;
+            for (size_t i = NG; i < pool.size(); ++i) {
+                const int m = pool[i];
+                if (used[m]) continue;
+                int gain = 0;
+                for (int e = c.row_ptr[m]; e < c.row_ptr[m + 1]; ++e) {
+                    const int v = c.col_idx[e];
+                    gain += in_prev[v] && !covered[v];
+                }
+                if (gain > best_gain) {
+                    best_gain = gain;
+                    best = static_cast<int>(i);
+                }
+            }
+            const int m = pool[best];
+            used[m] = 1;
+            groups[g].push_back(m);
+            for (int e = c.row_ptr[m]; e < c.row_ptr[m + 1]; ++e) covered[c.col_idx[e]] = 1;
+        }
+    }
+}
+
 static ndgsbp_status draw_unit_groups(int Mu, int G, double r, uint64_t seed, int flags,
-                                      std::vector<std::vector<int>>& groups) {
+                                      std::vector<std::vector<int>>& groups, const Code* structure = nullptr) {
     int NG = 0, o = 0;
     std::vector<int> fresh;
     ndgsbp_status st = group_sizes(Mu, G, r, flags, &NG, &o, &fresh);
@@ -105,6 +148,11 @@ static ndgsbp_status draw_unit_groups(int Mu, int G, double r, uint64_t seed, in
         }
     };
     groups.assign(G, {});
+    if (flags & NDGSBP_GROUPS_STRUCTURED) {
+        draw(Mu);   // the whole random order: group 1, then the tie-break order
+        structured_groups(*structure, G, NG, o, fresh, pool, groups);
+        return NDGSBP_OK;
+    }
     if (flags & NDGSBP_GROUPS_CYCLIC) {
         draw(Mu);
         const int s = Mu / G;
@@ -498,8 +546,11 @@ ndgsbp_status ndgsbp_groups_build(const ndgsbp_code* code, int32_t G, double r, 
     } else if (unit != NDGSBP_UNIT_CN) {
         return fail(NDGSBP_ERR_INVALID, "groups_build: unknown unit %d", unit);
     }
+    if ((flags & NDGSBP_GROUPS_STRUCTURED) &&
+        (unit != NDGSBP_UNIT_CN || (flags & (NDGSBP_GROUPS_CYCLIC | NDGSBP_GROUPS_NATURAL))))
+        return fail(NDGSBP_ERR_INVALID, "groups_build: STRUCTURED takes CN units, without CYCLIC or NATURAL");
     std::vector<std::vector<int>> ug;
-    ndgsbp_status st = draw_unit_groups(c.M / usize, G, r, seed, flags, ug);
+    ndgsbp_status st = draw_unit_groups(c.M / usize, G, r, seed, flags, ug, &c);
     if (st) return st;
     std::vector<int32_t> gp(1, 0), gc;
     for (auto& grp : ug) {

@@ -23,7 +23,7 @@ ERR_INVALID, ERR_INFEASIBLE, ERR_CUDA, ERR_WORKSPACE = -1, -2, -3, -4
 ERR_BUDGET, ERR_TIMEOUT, ERR_DEVICE, ERR_UNSUPPORTED, ERR_NOMEM = -5, -6, -7, -8, -9
 F32, F16, BF16, F64 = 0, 1, 2, 3
 UNIT_CN, UNIT_LAYER = 0, 1
-GROUPS_CYCLIC, GROUPS_NATURAL = 1, 2
+GROUPS_CYCLIC, GROUPS_NATURAL, GROUPS_STRUCTURED = 1, 2, 4
 SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
 VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1, 2, 3, 4
 VARIANT_QC_PAIR, VARIANT_QC_PAIR_GLOBAL, VARIANT_TILE = 5, 6, 7
