@@ -529,13 +529,14 @@ static ndgsbp_status make_tile_plan(const Groups& g, const ndgsbp_params* p, int
     if (!tpc) return NDGSBP_OK;
     const int le = (Q.max_deg + tpc - 1) / tpc;
     if (le > 8) return fail(NDGSBP_ERR_UNSUPPORTED, "lanes_per_cn %d leaves %d edges per lane (at most 8)", tpc, le);
-    const int ds = Q.max_deg | 1;
+    const TileShape shp = tile_shape(Q, tpc);
+    const int ds = shp.sl;
     const int per_slot = Q.window * Q.Z * tpc;
     int threads = p->block_threads ? p->block_threads : std::min(512, std::max(128, (per_slot + 31) / 32 * 32));
     const size_t table = tile_table_bytes(Q);
     const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 4);
-    const size_t m_bytes = align16(static_cast<size_t>(Q.msg_slots) * msg_size(p->msg_dtype));
-    const size_t d_bytes = align16(static_cast<size_t>(Q.window) * Q.Z * ds * 4);
+    const size_t m_bytes = align16(static_cast<size_t>(shp.msg_slots) * msg_size(p->msg_dtype));
+    const size_t d_bytes = align16(static_cast<size_t>(shp.delta_floats) * 4);
     // Shared memory per CTA under a residency target of k CTAs per SM: ctas_per_sm when set,
     // else 2 when a frame's posterior and deltas fit under half an SM, else 1.  Messages that
     // do not fit under the cap live in workspace slots (a code whose messages would fill a whole
@@ -587,8 +588,8 @@ static ndgsbp_status make_tile_plan(const Groups& g, const ndgsbp_params* p, int
     o.smem_bytes = static_cast<int64_t>(smem);
     o.workspace_bytes = static_cast<int64_t>(
         kHeaderBytes +
-        (msg_smem ? 0 : align256(static_cast<size_t>(grid) * slots * Q.msg_slots * msg_size(p->msg_dtype))));
-    o.stored_edges = Q.msg_slots;
+        (msg_smem ? 0 : align256(static_cast<size_t>(grid) * slots * shp.msg_slots * msg_size(p->msg_dtype))));
+    o.stored_edges = shp.msg_slots;
     o.edge_updates_per_iter = flood ? g.code->E : g.edge_updates;
     *ok = true;
     return NDGSBP_OK;
@@ -752,7 +753,7 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
         C.G = static_cast<int>(Q.group_layers.size() / Q.window);
         C.window = Q.window;
         C.maxdeg = Q.max_deg;
-        C.msg_slots = Q.msg_slots;
+        C.msg_slots = tile_shape(Q, plan.tile_tpc).msg_slots;
         C.tpc = plan.tile_tpc;
         C.le = plan.tile_le;
         C.slots = plan.tile_slots;

@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                         const int d = ldeg[l];
                         k0 = p * le;
                         L = min(max(d - k0, 0), le);
-                        m = slot_msgs<MsgT, SERVE>(C, base, s, sh.frame[s]) + loff[l] + c * lstride[l] + k0;
-                        dl = reinterpret_cast<float*>(base + C.p_bytes + C.m_bytes) + cnl * C.delta_stride + k0;
+                        m = slot_msgs<MsgT, SERVE>(C, base, s, sh.frame[s]) + ((l * Z + c) * tpc + p) * C.delta_stride;
+                        dl = reinterpret_cast<float*>(base + C.p_bytes + C.m_bytes) + (cnl * tpc + p) * C.delta_stride;
                         const int2* et = tab + l * md + k0;
 #pragma unroll
                         for (int k = 0; k < kLane; ++k) {
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                         unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
                         float* P = reinterpret_cast<float*>(base);
                         const float* dl = reinterpret_cast<const float*>(base + C.p_bytes + C.m_bytes) +
-                                          cnl * C.delta_stride + k0;
+                                          (cnl * tpc + p) * C.delta_stride;
                         const int2* et = tab + l * md + k0;
                         for (int k = 0; k < L; ++k) at_b(P, tile_vb(et[k], c, Z4)) += dl[k];
                     }
@@ -353,11 +353,19 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                 float* P = reinterpret_cast<float*>(base);
                 if (done) {
                     MsgT* msg = slot_msgs<MsgT, SERVE>(C, base, s, f);
-                    if (r.msgs_out)
-                        for (int e = tid; e < C.msg_slots; e += nt) {
-                            const int csr = __ldg(C.csr_of + e);
-                            if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]);
+                    if (r.msgs_out) {
+                        // edge k of CN c of layer l is CSR entry ebase(l) + c d_l + k (the rows of a
+                        // layer share its degree and list their VNs by block column)
+                        int ebase = 0;
+                        for (int l = 0; l < nl; ++l) {
+                            const int d = ldeg[l];
+                            for (int i = tid; i < Z * d; i += nt) {
+                                const int c = i / d, k = i - c * d, pl = k / le, kl = k - pl * le;
+                                r.msgs_out[f * r.E + ebase + i] = to_f(msg[((l * Z + c) * tpc + pl) * C.delta_stride + kl]);
+                            }
+                            ebase += Z * d;
                         }
+                    }
                     write_frame_outputs(r, P, f, it, sh.unsat[s] ? 1 : 0, &sh.err);
                     if (SERVE && tid == 0) {
                         C.state_flag[f] = kSlotDone;
@@ -405,6 +413,16 @@ size_t tile_table_bytes(const QcLayout& Q) {
     const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;
     const size_t b = static_cast<size_t>(Q.n_layers) * Q.max_deg * 8 + 3 * static_cast<size_t>(Q.n_layers) * 4 + G * Q.window * 4;
     return (b + 15) & ~static_cast<size_t>(15);
+}
+
+TileShape tile_shape(const QcLayout& Q, int tpc) {
+    TileShape t;
+    t.tpc = tpc;
+    t.le = (Q.max_deg + tpc - 1) / tpc;
+    t.sl = t.le | 1;
+    t.msg_slots = Q.n_layers * Q.Z * tpc * t.sl;
+    t.delta_floats = Q.window * Q.Z * tpc * t.sl;
+    return t;
 }
 
 void tile_code_finish(TileCode& C) {

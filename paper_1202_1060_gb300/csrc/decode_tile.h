@@ -35,7 +35,9 @@ struct TileCode {
     int slot_bytes;       // shared bytes per frame slot: posterior, messages, deltas
     int p_bytes;          // posterior bytes at the start of a slot (16-aligned)
     int m_bytes;          // message bytes after it (0 when messages live in global memory)
-    int delta_stride;     // deltas per CN in the slot's delta buffer (odd >= maxdeg)
+    int delta_stride;     // lane segment stride SL = le | 1: lane p of CN c of layer l keeps its
+                          // messages at ((l Z + c) tpc + p) SL + k and its deltas likewise, so
+                          // the lanes of a warp hit distinct shared-memory banks
     const int2* edge_tab;
     const int32_t* layer_deg;
     const int32_t* layer_stride;
@@ -81,6 +83,13 @@ struct TileArgs {
 typedef void (*TileKernelFn)(const TileArgs);
 
 TileKernelFn pick_tile_kernel(int msg_dtype, bool serve = false);
+
+// Storage shape of the tile kernel for a code at tpc lanes per CN: edges per lane, the odd lane
+// segment stride, messages per frame (all layers) and deltas per frame (one window).
+struct TileShape {
+    int tpc, le, sl, msg_slots, delta_floats;
+};
+TileShape tile_shape(const QcLayout& Q, int tpc);
 size_t tile_table_bytes(const QcLayout& Q);
 // Lanes per CN for a code of the given largest degree (edges per lane at most 8), 0 if above 32.
 int tile_lanes_per_cn(int maxdeg);

@@ -76,7 +76,7 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
     struct CodePlan {
         const QcLayout* Q;
         const DeviceQc* D;
-        int tpc, le, ds, per_slot, slots;
+        int tpc, le, ds, per_slot, slots, msg_slots;
         size_t table, p_bytes, m_bytes, d_bytes;
         double tile_cost;
     };
@@ -112,12 +112,14 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
             delete h;
             return fail(NDGSBP_ERR_UNSUPPORTED, "ragged_create: batch %d: %d edges per lane (at most 8)", i, cp[i].le);
         }
-        cp[i].ds = Q.max_deg | 1;
+        const TileShape shp = tile_shape(Q, tpc);
+        cp[i].ds = shp.sl;
+        cp[i].msg_slots = shp.msg_slots;
         cp[i].per_slot = Q.window * Q.Z * tpc;
         cp[i].table = tile_table_bytes(Q);
         cp[i].p_bytes = a16(static_cast<size_t>(g.code->N) * 4);
-        cp[i].m_bytes = a16(static_cast<size_t>(Q.msg_slots) * ms);
-        cp[i].d_bytes = a16(static_cast<size_t>(Q.window) * Q.Z * cp[i].ds * 4);
+        cp[i].m_bytes = a16(static_cast<size_t>(shp.msg_slots) * ms);
+        cp[i].d_bytes = a16(static_cast<size_t>(shp.delta_floats) * 4);
         cp[i].tile_cost = static_cast<double>(g.edge_updates);
         table_max = std::max(table_max, cp[i].table);
         if (!params->block_threads)
@@ -169,7 +171,7 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         C.G = static_cast<int>(c.Q->group_layers.size() / c.Q->window);
         C.window = c.Q->window;
         C.maxdeg = c.Q->max_deg;
-        C.msg_slots = c.Q->msg_slots;
+        C.msg_slots = c.msg_slots;
         C.tpc = c.tpc;
         C.le = c.le;
         C.slots = c.slots;
@@ -232,7 +234,7 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
     for (int i = 0; i < n_batches; ++i) {
         if (h->args.codes[i].m_bytes == 0) {
             msg_off[i] = ws;
-            ws += a256(static_cast<size_t>(grid) * cp[i].slots * cp[i].Q->msg_slots * ms);
+            ws += a256(static_cast<size_t>(grid) * cp[i].slots * cp[i].msg_slots * ms);
         }
     }
     cudaError_t e = cudaMalloc(&h->workspace, ws);

@@ -77,7 +77,7 @@ struct Pool {
     const Groups* g = nullptr;
     const QcLayout* Q = nullptr;
     const DeviceQc* D = nullptr;
-    int N = 0, W = 0, slots = 0, tpc = 1, le = 1, ds = 1, cta_slots = 1, tile_frames = 1;
+    int N = 0, W = 0, slots = 0, tpc = 1, le = 1, ds = 1, cta_slots = 1, tile_frames = 1, msg_slots = 0;
     size_t slot_bytes = 0, p_bytes = 0, m_bytes = 0, d_bytes = 0;
     // device: state of running frames
     int* flag = nullptr;
@@ -402,12 +402,14 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         p.tpc = tile_lanes_per_cn(p.Q->max_deg);
         if (!p.tpc) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d has row degree above 32", i);
         p.le = (p.Q->max_deg + p.tpc - 1) / p.tpc;
-        p.ds = p.Q->max_deg | 1;
+        const TileShape shp = tile_shape(*p.Q, p.tpc);
+        p.ds = shp.sl;
+        p.msg_slots = shp.msg_slots;
         p.N = p.g->code->N;
         p.W = (p.N + 31) / 32;
         p.p_bytes = a16(static_cast<size_t>(p.N) * 4);
-        p.m_bytes = a16(static_cast<size_t>(p.Q->msg_slots) * ms);
-        p.d_bytes = a16(static_cast<size_t>(p.Q->window) * p.Q->Z * p.ds * 4);
+        p.m_bytes = a16(static_cast<size_t>(p.msg_slots) * ms);
+        p.d_bytes = a16(static_cast<size_t>(shp.delta_floats) * 4);
         table_max = std::max(table_max, tile_table_bytes(*p.Q));
         if (!params->block_threads)
             threads = std::max(threads, std::min(512, std::max(128, (p.Q->window * p.Q->Z * p.tpc + 31) / 32 * 32)));
@@ -443,7 +445,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         // pool size from the budget share: posterior and messages of a running frame, LLR
         // staging, outputs and status per slot
         const double share = (weights ? std::max(0.0, weights[i]) : 1.0) / wsum;
-        const size_t per = sizeof(float) * p.N * 2 + static_cast<size_t>(p.Q->msg_slots) * ms + sizeof(uint32_t) * p.W + 16;
+        const size_t per = sizeof(float) * p.N * 2 + static_cast<size_t>(p.msg_slots) * ms + sizeof(uint32_t) * p.W + 16;
         p.slots = static_cast<int>(std::min<double>(kMaxPoolSlots, std::floor(share * hbm_budget_bytes / per)));
         if (p.slots < 1) return fail(NDGSBP_ERR_BUDGET, "server_create: the budget leaves no slot for code %d", i);
     }
@@ -462,7 +464,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         dmalloc(reinterpret_cast<void**>(&p.flag), sizeof(int) * p.slots);
         dmalloc(reinterpret_cast<void**>(&p.st_iter), sizeof(int) * p.slots);
         dmalloc(reinterpret_cast<void**>(&p.st_P), sizeof(float) * p.N * static_cast<size_t>(p.slots));
-        dmalloc(&p.st_msgs, static_cast<size_t>(p.Q->msg_slots) * ms * p.slots);
+        dmalloc(&p.st_msgs, static_cast<size_t>(p.msg_slots) * ms * p.slots);
         hmalloc(reinterpret_cast<void**>(&p.h_stage), sizeof(float) * p.N * static_cast<size_t>(p.slots));
         hmalloc(reinterpret_cast<void**>(&p.h_hard), sizeof(uint32_t) * p.W * static_cast<size_t>(p.slots));
         hmalloc(reinterpret_cast<void**>(&p.h_iters), sizeof(int32_t) * p.slots);
@@ -502,7 +504,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         C.G = static_cast<int>(p.Q->group_layers.size() / p.Q->window);
         C.window = p.Q->window;
         C.maxdeg = p.Q->max_deg;
-        C.msg_slots = p.Q->msg_slots;
+        C.msg_slots = p.msg_slots;
         C.tpc = p.tpc;
         C.le = p.le;
         C.slots = p.cta_slots;

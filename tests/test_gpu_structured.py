@@ -42,7 +42,10 @@ def test_structured_groups_decode_like_oracle(env, oracle_mod):
     nd.decode(g, p, torch.from_numpy(llr.astype(np.float32)).to(dev), ws, hard, iters)
     q = g.query()
     ref = oracle_mod.ndgsbp_decode(c, q["grp_ptr"], q["cn_idx"], llr.astype(np.float32).astype(np.float64), 35)
-    good = ~(np.abs(ref.total) < 1e-3).any(axis=1)
+    # frames the oracle decodes to a codeword without a near-zero posterior (the criterion of the
+    # other parity tests: non-converged trajectories separate FP32 from FP64 over 35 iterations)
+    good = ~(np.abs(ref.total) < 1e-3).any(axis=1) & (ref.synd_ok == 1)
+    assert good.sum() >= 60
     assert (nd.unpack_bits(hard, c.N)[good] == ref.hard[good]).all()
     assert (iters.cpu().numpy()[good] == ref.iters[good]).all()
 
