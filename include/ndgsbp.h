@@ -184,6 +184,21 @@ ndgsbp_status ndgsbp_groups_build(const ndgsbp_code* code, int32_t G, double r, 
 ndgsbp_status ndgsbp_groups_from_lists(const ndgsbp_code* code, const int32_t* grp_ptr,
                                        const int32_t* cn_idx, int32_t G, ndgsbp_groups** out);
 
+/* Several groupings cycled by iteration -- the literal "go to Step 1" of Step 4 b), which draws
+ * the groups again for every iteration: n_groupings (1..64) groupings are drawn as by
+ * ndgsbp_groups_build with the seeds seed, seed + 1, ..., and iteration l of a decode uses
+ * grouping (l - 1) mod n_groupings.  Decoded by the QC kernels (QC, QC_GLOBAL, QC_PAIR, TILE,
+ * ragged launches, serving) when every grouping is made of whole layers with one window size;
+ * the other plans return UNSUPPORTED.  ndgsbp_groups_query describes grouping 0.
+ * Errors: as ndgsbp_groups_build. */
+ndgsbp_status ndgsbp_groups_build_cycled(const ndgsbp_code* code, int32_t G, double r, uint64_t seed,
+                                         int32_t unit, int32_t flags, int32_t n_groupings,
+                                         ndgsbp_groups** out);
+/* Grouping k (0 <= k < *n_groupings) of a handle, laid out as for ndgsbp_groups_query (G + 1
+ * pointers, *n_entries CN indices).  Any output may be NULL.  Errors: INVALID. */
+ndgsbp_status ndgsbp_groups_query_grouping(const ndgsbp_groups* groups, int32_t k, int32_t* n_groupings,
+                                           int64_t* n_entries, int32_t* grp_ptr, int32_t* cn_idx);
+
 /* Read a grouping back.  Any output may be NULL.  grp_ptr needs G+1 entries and cn_idx
  * n_entries entries (query both counts first with the arrays NULL).  cocsg is the paper's
  * l: the mean over consecutive groups of the VNs adjacent to both (Sec. I, II-B).

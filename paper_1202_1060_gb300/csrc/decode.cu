@@ -400,7 +400,7 @@ static ndgsbp_status finish_grid(const void* fn, int threads, size_t smem, const
 static ndgsbp_status make_qc_frames2_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
                                           const QcLayout& Q, int maxdc, bool spec, bool force_global,
                                           const DeviceInfo& di, Plan& plan, bool* ok, bool allow_upload) {
-    if (!spec || maxdc > 16) return NDGSBP_OK;
+    if (!spec || maxdc > 16 || Q.n_groupings > 1) return NDGSBP_OK;
     const int active = Q.window * Q.Z;
     const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
     if (threads < active || threads > qc_frames2_max_threads(maxdc)) return NDGSBP_OK;
@@ -474,7 +474,7 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     // direct write-back for 2-layer windows only on request: on GB300 the two-round kernel is
     // faster (3.37 vs 3.05 Gbit/s on the n=2304 sweep) although it runs one barrier more
     const bool want_direct = p->variant == NDGSBP_VARIANT_QC_DIRECT;
-    if (want_direct && !(spec && Q.window == 2 && !Q.win2.empty())) return NDGSBP_OK;
+    if (want_direct && !(spec && Q.window == 2 && !Q.win2.empty() && Q.n_groupings == 1)) return NDGSBP_OK;
     const bool w2 = !pair && want_direct;
     const size_t budget = static_cast<size_t>(di.smem_optin) - 64;
     const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 4);
@@ -529,8 +529,8 @@ static ndgsbp_status make_tile_plan(const Groups& g, const ndgsbp_params* p, int
     if (!tpc) return NDGSBP_OK;
     const int le = (Q.max_deg + tpc - 1) / tpc;
     if (le > 8) return fail(NDGSBP_ERR_UNSUPPORTED, "lanes_per_cn %d leaves %d edges per lane (at most 8)", tpc, le);
-    const TileShape shp = tile_shape(Q, tpc);
-    const int ds = shp.sl;
+    const TileShape shp = tile_shape(Q, tpc, p->msg_dtype);
+    const int ds = shp.delta_stride;
     const int per_slot = Q.window * Q.Z * tpc;
     int threads = p->block_threads ? p->block_threads : std::min(512, std::max(128, (per_slot + 31) / 32 * 32));
     const size_t table = tile_table_bytes(Q);
@@ -624,6 +624,8 @@ static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t 
         if (st) return st;
         if (ok) return NDGSBP_OK;
     }
+    if (g.n_groupings > 1 && !flood)
+        return fail(NDGSBP_ERR_UNSUPPORTED, "groupings cycled by iteration need a QC kernel (groups of whole layers)");
     st = device_layout(g, flood, plan.L, plan.D, allow_upload);
     if (st) return st;
     const Layout& L = *plan.L;
@@ -750,10 +752,13 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
         C.E = static_cast<int>(g.code->E);
         C.Z = Q.Z;
         C.nl = Q.n_layers;
-        C.G = static_cast<int>(Q.group_layers.size() / Q.window);
+        C.n_groupings = Q.n_groupings;
+        C.G = static_cast<int>(Q.group_layers.size() / (static_cast<size_t>(Q.window) * Q.n_groupings));
         C.window = Q.window;
         C.maxdeg = Q.max_deg;
-        C.msg_slots = tile_shape(Q, plan.tile_tpc).msg_slots;
+        const TileShape shp = tile_shape(Q, plan.tile_tpc, params->msg_dtype);
+        C.msg_slots = shp.msg_slots;
+        C.msg_stride = shp.msg_stride;
         C.tpc = plan.tile_tpc;
         C.le = plan.tile_le;
         C.slots = plan.tile_slots;

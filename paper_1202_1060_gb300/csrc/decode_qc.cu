@@ -188,7 +188,7 @@ __device__ __forceinline__ QcSmem qc_smem_layout(unsigned char* smem, const QcAr
         s.lstride[i] = a.layer_stride[i];
         s.loff[i] = a.layer_off[i];
     }
-    for (int i = tid; i < a.G * a.window; i += nt) s.glay[i] = a.group_layers[i];
+    for (int i = tid; i < a.G * a.window * a.n_groupings; i += nt) s.glay[i] = a.group_layers[i];
     return s;
 }
 
@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
         __syncthreads();
         int it = 1, unsat = 1;
         for (;; ++it) {
+            const int* gl = s.glay + ((it - 1) % a.n_groupings) * a.G * W;   // this iteration's grouping
             for (int g = 0; g < a.G; ++g) {
                 float dl[MAXDC];
                 int vb[MAXDC];
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
                     // 2-layer window: direct write-back off the shared block columns, one
                     // ordered round on them
                     if (active) {
-                        const int l = s.glay[g * W + j];
+                        const int l = gl[g * W + j];
                         d = s.ldeg[l];
                         const int2* et = s.tab + l * md;
                         MsgT* m = msg + s.loff[l] + c * s.lstride[l];
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
                     }
                     __syncthreads();
                     if (active && j == 1) {
-                        const int l = s.glay[g * W + 1];
+                        const int l = gl[g * W + 1];
                         const int2* et = s.tab + l * md;
                         const int2* w2 = a.win2 + (g * 2 + 1) * md;
                         const unsigned mk = s.w2mask[g * 2 + 1];
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
                     continue;
                 }
                 if (active) {
-                    const int l = s.glay[g * W + j];
+                    const int l = gl[g * W + j];
                     d = s.ldeg[l];
                     const int2* et = s.tab + l * md;
                     MsgT* m = msg + s.loff[l] + c * s.lstride[l];
@@ -417,12 +418,13 @@ __global__ void __launch_bounds__(pair_max_threads(MAXDC)) qc_pair_kernel(const 
         __syncthreads();
         int it = 1, unsat = 1;
         for (;; ++it) {
+            const int* gl = s.glay + ((it - 1) % a.n_groupings) * a.G * W;   // this iteration's grouping
             for (int g = 0; g < a.G; ++g) {
                 float2 dl[MAXDC];
                 int vb0[MAXDC], vb1[MAXDC];
                 int d = 0;
                 if (active) {
-                    const int l = s.glay[g * W + j];
+                    const int l = gl[g * W + j];
                     d = s.ldeg[l];
                     const int S = s.lstride[l];
                     const int2* et = s.tab + l * md;
@@ -533,7 +535,8 @@ void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs
     a.Z = Q.Z;
     a.nl = Q.n_layers;
     a.window = Q.window;
-    a.G = static_cast<int>(Q.group_layers.size() / Q.window);
+    a.n_groupings = Q.n_groupings;
+    a.G = static_cast<int>(Q.group_layers.size() / (static_cast<size_t>(Q.window) * Q.n_groupings));
     a.maxdeg = Q.max_deg;
     a.msg_slots = Q.msg_slots;
     a.edge_tab = reinterpret_cast<const int2*>(D.edge_tab);

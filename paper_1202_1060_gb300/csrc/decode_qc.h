@@ -17,6 +17,7 @@ struct QcArgs {
     const int32_t* csr_of;        // [msg_slots] CSR position of each stored message, -1 = padding
     void* ws_msgs;                // per-CTA message slots when messages are not in shared memory
     const int2* win2;             // [G][2][maxdeg] block columns shared by 2-layer windows, or null
+    int n_groupings;              // group -> layer tables cycled by iteration (group_layers holds all)
 };
 
 typedef void (*QcKernelFn)(const QcArgs);

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                 lstride[i] = C.layer_stride[i];
                 loff[i] = C.layer_off[i];
             }
-            for (int i = tid; i < C.G * W; i += nt) glay[i] = C.group_layers[i];
+            for (int i = tid; i < C.G * W * C.n_groupings; i += nt) glay[i] = C.group_layers[i];
         }
         __syncthreads();
         if (tid == 0) {
@@ -229,11 +229,12 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                     if (live) {
                         unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
                         P = reinterpret_cast<float*>(base);
-                        const int l = glay[g * W + j];
+                        // the slot's grouping for its current iteration (iterations done so far)
+                        const int l = glay[(sh.iter[s] % C.n_groupings) * C.G * W + g * W + j];
                         const int d = ldeg[l];
                         k0 = p * le;
                         L = min(max(d - k0, 0), le);
-                        m = slot_msgs<MsgT, SERVE>(C, base, s, sh.frame[s]) + ((l * Z + c) * tpc + p) * C.delta_stride;
+                        m = slot_msgs<MsgT, SERVE>(C, base, s, sh.frame[s]) + ((l * Z + c) * tpc + p) * C.msg_stride;
                         dl = reinterpret_cast<float*>(base + C.p_bytes + C.m_bytes) + (cnl * tpc + p) * C.delta_stride;
                         const int2* et = tab + l * md + k0;
 #pragma unroll
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                         const int w = i - s * per_pos;
                         const int c = w >> tsh, p = w & (tpc - 1);
                         const int cnl = jj * Z + c;
-                        const int l = glay[g * W + jj];
+                        const int l = glay[(sh.iter[s] % C.n_groupings) * C.G * W + g * W + jj];
                         const int k0 = p * le;
                         const int L = min(max(ldeg[l] - k0, 0), le);
                         unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                             const int d = ldeg[l];
                             for (int i = tid; i < Z * d; i += nt) {
                                 const int c = i / d, k = i - c * d, pl = k / le, kl = k - pl * le;
-                                r.msgs_out[f * r.E + ebase + i] = to_f(msg[((l * Z + c) * tpc + pl) * C.delta_stride + kl]);
+                                r.msgs_out[f * r.E + ebase + i] = to_f(msg[((l * Z + c) * tpc + pl) * C.msg_stride + kl]);
                             }
                             ebase += Z * d;
                         }
@@ -415,13 +416,15 @@ size_t tile_table_bytes(const QcLayout& Q) {
     return (b + 15) & ~static_cast<size_t>(15);
 }
 
-TileShape tile_shape(const QcLayout& Q, int tpc) {
+TileShape tile_shape(const QcLayout& Q, int tpc, int msg_dtype) {
     TileShape t;
     t.tpc = tpc;
     t.le = (Q.max_deg + tpc - 1) / tpc;
-    t.sl = t.le | 1;
-    t.msg_slots = Q.n_layers * Q.Z * tpc * t.sl;
-    t.delta_floats = Q.window * Q.Z * tpc * t.sl;
+    t.delta_stride = t.le | 1;
+    // 16-bit messages: an even stride whose half (in 4-byte words) is odd
+    t.msg_stride = msg_dtype == NDGSBP_F32 ? (t.le | 1) : 2 * (((t.le + 1) / 2) | 1);
+    t.msg_slots = Q.n_layers * Q.Z * tpc * t.msg_stride;
+    t.delta_floats = Q.window * Q.Z * tpc * t.delta_stride;
     return t;
 }
 
@@ -430,6 +433,7 @@ void tile_code_finish(TileCode& C) {
     C.div_pos = make_fastdiv(static_cast<unsigned>(C.Z * C.tpc));
     C.div_syn = make_fastdiv(static_cast<unsigned>(C.nl * C.Z * C.tpc));
     C.div_z = make_fastdiv(static_cast<unsigned>(C.Z));
+    if (C.n_groupings < 1) C.n_groupings = 1;
 }
 
 int tile_lanes_per_cn(int maxdeg) { return maxdeg <= 8 ? 1 : maxdeg <= 16 ? 2 : maxdeg <= 32 ? 4 : 0; }

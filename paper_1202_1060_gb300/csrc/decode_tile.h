@@ -35,9 +35,10 @@ struct TileCode {
     int slot_bytes;       // shared bytes per frame slot: posterior, messages, deltas
     int p_bytes;          // posterior bytes at the start of a slot (16-aligned)
     int m_bytes;          // message bytes after it (0 when messages live in global memory)
-    int delta_stride;     // lane segment stride SL = le | 1: lane p of CN c of layer l keeps its
-                          // messages at ((l Z + c) tpc + p) SL + k and its deltas likewise, so
-                          // the lanes of a warp hit distinct shared-memory banks
+    int delta_stride;     // lane segments: lane p of CN c of layer l keeps its messages at
+    int msg_stride;       // ((l Z + c) tpc + p) msg_stride + k and its window's deltas at
+                          // (cnl tpc + p) delta_stride + k; both strides are odd in 4-byte words,
+                          // so the lanes of a warp hit distinct shared-memory banks
     const int2* edge_tab;
     const int32_t* layer_deg;
     const int32_t* layer_stride;
@@ -52,6 +53,7 @@ struct TileCode {
     float* state_P;       // [pool][N] posteriors of running frames
     void* state_msgs;     // [pool][msg_slots] messages of running frames
     int epoch_iters;      // iterations a frame may run in one launch before its state is saved
+    int n_groupings;      // group -> layer tables cycled by iteration (group_layers holds all)
     int* done_list;       // [pool] slots whose frame retired in this launch (serving), or null
     int* done_count;      // number of entries in done_list (zeroed before the launch)
     // divisions of the kernel's index arithmetic (set by tile_code_finish)
@@ -87,9 +89,9 @@ TileKernelFn pick_tile_kernel(int msg_dtype, bool serve = false);
 // Storage shape of the tile kernel for a code at tpc lanes per CN: edges per lane, the odd lane
 // segment stride, messages per frame (all layers) and deltas per frame (one window).
 struct TileShape {
-    int tpc, le, sl, msg_slots, delta_floats;
+    int tpc, le, msg_stride, delta_stride, msg_slots, delta_floats;
 };
-TileShape tile_shape(const QcLayout& Q, int tpc);
+TileShape tile_shape(const QcLayout& Q, int tpc, int msg_dtype);
 size_t tile_table_bytes(const QcLayout& Q);
 // Lanes per CN for a code of the given largest degree (edges per lane at most 8), 0 if above 32.
 int tile_lanes_per_cn(int maxdeg);

@@ -561,6 +561,54 @@ ndgsbp_status ndgsbp_groups_build(const ndgsbp_code* code, int32_t G, double r, 
     return finish_groups(code->c, std::move(gp), std::move(gc), out);
 }
 
+ndgsbp_status ndgsbp_groups_build_cycled(const ndgsbp_code* code, int32_t G, double r, uint64_t seed,
+                                         int32_t unit, int32_t flags, int32_t n_groupings, ndgsbp_groups** out) {
+    clear_error();
+    if (!code || !out || n_groupings < 1 || n_groupings > 64)
+        return fail(NDGSBP_ERR_INVALID, "groups_build_cycled: need 1..64 groupings");
+    ndgsbp_groups* h = nullptr;
+    ndgsbp_status st = ndgsbp_groups_build(code, G, r, seed, unit, flags, &h);
+    if (st) return st;
+    Groups& g = h->g;
+    for (int k = 1; k < n_groupings; ++k) {
+        ndgsbp_groups* hk = nullptr;
+        st = ndgsbp_groups_build(code, G, r, seed + static_cast<uint64_t>(k), unit, flags, &hk);
+        if (st) {
+            ndgsbp_groups_destroy(h);
+            return st;
+        }
+        const Groups& gk = hk->g;
+        // the QC layout takes the further groupings as more group -> layer tables
+        if (g.qc.ok && gk.qc.ok && gk.qc.window == g.qc.window &&
+            gk.qc.group_layers.size() == static_cast<size_t>(g.G) * g.qc.window) {
+            g.qc.group_layers.insert(g.qc.group_layers.end(), gk.qc.group_layers.begin(), gk.qc.group_layers.end());
+        } else {
+            g.qc.ok = false;
+        }
+        g.cyc_ptr.push_back(gk.grp_ptr);
+        g.cyc_cn.push_back(gk.grp_cn);
+        ndgsbp_groups_destroy(hk);
+    }
+    g.n_groupings = n_groupings;
+    g.qc.n_groupings = n_groupings;
+    *out = h;
+    return NDGSBP_OK;
+}
+
+ndgsbp_status ndgsbp_groups_query_grouping(const ndgsbp_groups* groups, int32_t k, int32_t* n_groupings,
+                                           int64_t* n_entries, int32_t* grp_ptr, int32_t* cn_idx) {
+    if (!groups) return fail(NDGSBP_ERR_INVALID, "groups_query_grouping: null handle");
+    const Groups& g = groups->g;
+    if (n_groupings) *n_groupings = g.n_groupings;
+    if (k < 0 || k >= g.n_groupings) return fail(NDGSBP_ERR_INVALID, "groups_query_grouping: no grouping %d", k);
+    const std::vector<int32_t>& gp = k ? g.cyc_ptr[k - 1] : g.grp_ptr;
+    const std::vector<int32_t>& gc = k ? g.cyc_cn[k - 1] : g.grp_cn;
+    if (n_entries) *n_entries = static_cast<int64_t>(gc.size());
+    if (grp_ptr) std::copy(gp.begin(), gp.end(), grp_ptr);
+    if (cn_idx) std::copy(gc.begin(), gc.end(), cn_idx);
+    return NDGSBP_OK;
+}
+
 ndgsbp_status ndgsbp_groups_from_lists(const ndgsbp_code* code, const int32_t* grp_ptr,
                                        const int32_t* cn_idx, int32_t G, ndgsbp_groups** out) {
     clear_error();

@@ -77,7 +77,8 @@ struct QcLayout {
     std::vector<int32_t> layer_stride;  // [n_layers] messages per CN: the degree rounded up to odd
     std::vector<int32_t> layer_off;     // [n_layers] first stored message of the layer
     std::vector<int32_t> edge_tab;      // [n_layers][max_deg][2]: (4 (b Z + s), Z - s), edges by block column
-    std::vector<int32_t> group_layers;  // [G][window] layer ids in group order
+    int n_groupings = 1;                // groupings cycled by iteration (all with this window)
+    std::vector<int32_t> group_layers;  // [n_groupings][G][window] layer ids in group order
     std::vector<int32_t> csr_of;        // [msg_slots] CSR position of message layer_off[l] + c S_l + k, -1 = pad
     // Windows of 2 layers: [G][2][max_deg][2].  Position 0, edge k: (1 if the other layer of the
     // window has an edge in the same block column, 0).  Position 1, edge k: (edge k0 of the
@@ -101,6 +102,10 @@ struct Groups {
     std::shared_ptr<const Code> code;
     int G = 0;
     std::vector<int32_t> grp_ptr, grp_cn;
+    // further groupings cycled by iteration (iteration l uses grouping (l - 1) mod n_groupings;
+    // grouping 0 is grp_ptr / grp_cn)
+    int n_groupings = 1;
+    std::vector<std::vector<int32_t>> cyc_ptr, cyc_cn;
     double cocsg = 0.0;
     int64_t cn_updates = 0, edge_updates = 0;
     Layout grouped;

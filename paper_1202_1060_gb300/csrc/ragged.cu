@@ -76,7 +76,7 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
     struct CodePlan {
         const QcLayout* Q;
         const DeviceQc* D;
-        int tpc, le, ds, per_slot, slots, msg_slots;
+        int tpc, le, ds, msl, per_slot, slots, msg_slots;
         size_t table, p_bytes, m_bytes, d_bytes;
         double tile_cost;
     };
@@ -112,8 +112,9 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
             delete h;
             return fail(NDGSBP_ERR_UNSUPPORTED, "ragged_create: batch %d: %d edges per lane (at most 8)", i, cp[i].le);
         }
-        const TileShape shp = tile_shape(Q, tpc);
-        cp[i].ds = shp.sl;
+        const TileShape shp = tile_shape(Q, tpc, params->msg_dtype);
+        cp[i].ds = shp.delta_stride;
+        cp[i].msl = shp.msg_stride;
         cp[i].msg_slots = shp.msg_slots;
         cp[i].per_slot = Q.window * Q.Z * tpc;
         cp[i].table = tile_table_bytes(Q);
@@ -168,10 +169,12 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         C.E = static_cast<int>(g.code->E);
         C.Z = c.Q->Z;
         C.nl = c.Q->n_layers;
-        C.G = static_cast<int>(c.Q->group_layers.size() / c.Q->window);
+        C.n_groupings = c.Q->n_groupings;
+        C.G = static_cast<int>(c.Q->group_layers.size() / (static_cast<size_t>(c.Q->window) * c.Q->n_groupings));
         C.window = c.Q->window;
         C.maxdeg = c.Q->max_deg;
         C.msg_slots = c.msg_slots;
+        C.msg_stride = c.msl;
         C.tpc = c.tpc;
         C.le = c.le;
         C.slots = c.slots;

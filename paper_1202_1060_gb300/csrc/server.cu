@@ -77,7 +77,7 @@ struct Pool {
     const Groups* g = nullptr;
     const QcLayout* Q = nullptr;
     const DeviceQc* D = nullptr;
-    int N = 0, W = 0, slots = 0, tpc = 1, le = 1, ds = 1, cta_slots = 1, tile_frames = 1, msg_slots = 0;
+    int N = 0, W = 0, slots = 0, tpc = 1, le = 1, ds = 1, msl = 1, cta_slots = 1, tile_frames = 1, msg_slots = 0;
     size_t slot_bytes = 0, p_bytes = 0, m_bytes = 0, d_bytes = 0;
     // device: state of running frames
     int* flag = nullptr;
@@ -402,8 +402,9 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         p.tpc = tile_lanes_per_cn(p.Q->max_deg);
         if (!p.tpc) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d has row degree above 32", i);
         p.le = (p.Q->max_deg + p.tpc - 1) / p.tpc;
-        const TileShape shp = tile_shape(*p.Q, p.tpc);
-        p.ds = shp.sl;
+        const TileShape shp = tile_shape(*p.Q, p.tpc, params->msg_dtype);
+        p.ds = shp.delta_stride;
+        p.msl = shp.msg_stride;
         p.msg_slots = shp.msg_slots;
         p.N = p.g->code->N;
         p.W = (p.N + 31) / 32;
@@ -501,10 +502,12 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         C.E = static_cast<int>(p.g->code->E);
         C.Z = p.Q->Z;
         C.nl = p.Q->n_layers;
-        C.G = static_cast<int>(p.Q->group_layers.size() / p.Q->window);
+        C.n_groupings = p.Q->n_groupings;
+        C.G = static_cast<int>(p.Q->group_layers.size() / (static_cast<size_t>(p.Q->window) * p.Q->n_groupings));
         C.window = p.Q->window;
         C.maxdeg = p.Q->max_deg;
         C.msg_slots = p.msg_slots;
+        C.msg_stride = p.msl;
         C.tpc = p.tpc;
         C.le = p.le;
         C.slots = p.cta_slots;

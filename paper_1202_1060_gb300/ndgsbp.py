@@ -103,6 +103,8 @@ _SIGS = {
     "ndgsbp_group_sizes": (_I32, [_I32, _I32, _D, _I32, _P, _P]),
     "ndgsbp_groups_build": (_I32, [_P, _I32, _D, _U64, _I32, _I32, ctypes.POINTER(_P)]),
     "ndgsbp_groups_from_lists": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_P)]),
+    "ndgsbp_groups_build_cycled": (_I32, [_P, _I32, _D, _U64, _I32, _I32, _I32, ctypes.POINTER(_P)]),
+    "ndgsbp_groups_query_grouping": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "ndgsbp_groups_query": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "ndgsbp_groups_destroy": (_I32, [_P]),
     "ndgsbp_awgn_llr": (_I32, [_P, _I64, _D, _D, _U64, _P, _I32, _P, _I32, _P]),
@@ -251,11 +253,32 @@ class Groups:
         self.code = code
 
     @classmethod
-    def build(cls, code: Code, G: int, r: float, seed: int, unit: int = UNIT_CN, flags: int = 0):
+    def build(cls, code: Code, G: int, r: float, seed: int, unit: int = UNIT_CN, flags: int = 0,
+              n_groupings: int = 1):
+        """ndgsbp_groups_build, or with n_groupings > 1 ndgsbp_groups_build_cycled (groupings cycled
+        by iteration)."""
         h = ctypes.c_void_p()
-        _check(_lib.ndgsbp_groups_build(code.handle, G, float(r), seed & (2**64 - 1), unit, flags,
-                                        ctypes.byref(h)))
+        if n_groupings == 1:
+            _check(_lib.ndgsbp_groups_build(code.handle, G, float(r), seed & (2**64 - 1), unit, flags,
+                                            ctypes.byref(h)))
+        else:
+            _check(_lib.ndgsbp_groups_build_cycled(code.handle, G, float(r), seed & (2**64 - 1), unit, flags,
+                                                   int(n_groupings), ctypes.byref(h)))
         return cls(h, code)
+
+    def groupings(self):
+        """All groupings cycled by iteration: list of (grp_ptr, cn_idx)."""
+        K = ctypes.c_int32()
+        _check(_lib.ndgsbp_groups_query_grouping(self._h, 0, ctypes.byref(K), None, None, None))
+        out = []
+        for k in range(K.value):
+            n = ctypes.c_int64()
+            _check(_lib.ndgsbp_groups_query_grouping(self._h, k, None, ctypes.byref(n), None, None))
+            gp = np.zeros(self.query()["G"] + 1, np.int32)
+            gc = np.zeros(n.value, np.int32)
+            _check(_lib.ndgsbp_groups_query_grouping(self._h, k, None, None, _hptr(gp), _hptr(gc)))
+            out.append((gp, gc))
+        return out
 
     @classmethod
     def from_lists(cls, code: Code, grp_ptr, cn_idx):
