@@ -32,15 +32,22 @@ __device__ __forceinline__ float& at_b(float* P, int vb) {
     return *reinterpret_cast<float*>(reinterpret_cast<char*>(P) + vb);
 }
 
-// Forward pass over the lane's L edges: prefix pairs, lane total (cn, ce), sign bits.
-template <int L>
-__device__ __forceinline__ void lane_forward(const float (&t)[kLane], float lim, float (&xu)[kLane], float (&pn)[kLane],
-                                             float (&pe)[kLane], float& cn, float& ce, unsigned& sbits) {
+// Forward pass over the lane's LE edge positions, of which the first nreal are edges: prefix
+// pairs, lane total (cn, ce), sign bits.  Every lane of a code runs the same LE (no divergence
+// between lanes holding different edge counts); a position past nreal is the neutral factor
+// tanh = 1, i.e. u = 0 and (N, E) = (1/2, 0), which only scales the lane's pairs by exactly 1/2
+// (t = +0 there, so no sign either): the outputs of the real edges do not change.
+template <int LE>
+__device__ __forceinline__ void lane_forward(const float (&t)[kLane], int nreal, float lim, float (&xu)[kLane],
+                                             float (&pn)[kLane], float (&pe)[kLane], float& cn, float& ce,
+                                             unsigned& sbits) {
 #pragma unroll
-    for (int k = 0; k < L; ++k) {
-        sbits |= (__float_as_uint(t[k]) >> 31) << k;
-        const float x = fminf(fabsf(t[k]), lim);
-        const float u = ex2_approx(x * -1.4426950408889634f);
+    for (int k = 0; k < LE; ++k) {
+        const bool real = k < nreal;
+        const float tk = real ? t[k] : 0.f;
+        sbits |= (__float_as_uint(tk) >> 31) << k;
+        const float x = fminf(fabsf(tk), lim);
+        const float u = real ? ex2_approx(x * -1.4426950408889634f) : 0.f;
         const float n = fmaf(-0.5f, u, 0.5f);
         xu[k] = u;
         pn[k] = cn;
@@ -50,12 +57,14 @@ __device__ __forceinline__ void lane_forward(const float (&t)[kLane], float lim,
     }
 }
 
-// Backward pass: the suffix starts from (sn, se), the product over the other lanes' edges.
-template <int L, typename Emit>
+// Backward pass: the suffix starts from (sn, se), the product over the other lanes' edges;
+// outputs for the nreal real positions only.
+template <int LE, typename Emit>
 __device__ __forceinline__ void lane_backward(const float (&xu)[kLane], const float (&pn)[kLane], const float (&pe)[kLane],
-                                              float sn, float se, unsigned sbits, unsigned par, float lim, Emit emit) {
+                                              int nreal, float sn, float se, unsigned sbits, unsigned par, float lim,
+                                              Emit emit) {
 #pragma unroll
-    for (int k = L - 1; k >= 0; --k) {
+    for (int k = LE - 1; k >= 0; --k) {
         const float u = xu[k];
         const float n = fmaf(-0.5f, u, 0.5f);
         const float en = pn[k] * sn;
@@ -63,7 +72,7 @@ __device__ __forceinline__ void lane_backward(const float (&xu)[kLane], const fl
         const float w = fmaf(en * rcp_approx(ee), 2.f, 1.f);
         const float mag = fminf(0.69314718055994531f * lg2_approx(w), lim);
         const unsigned sgn = ((par ^ (sbits >> k)) & 1u) << 31;
-        emit(k, __uint_as_float(__float_as_uint(mag) | sgn));
+        if (k < nreal) emit(k, __uint_as_float(__float_as_uint(mag) | sgn));
         se = fmaf(se, n + u, sn * u);
         sn = sn * n;
     }
@@ -244,9 +253,9 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                                 t[k] = at_b(P, tile_vb(et[k], c, Z4)) - old[k];
                             }
                         }
-                        switch (L) {
+                        switch (le) {
 #define NDGSBP_FWD(LL) \
-    case LL: lane_forward<LL>(t, lim, xu, pn, pe, cn, ce, sbits); break;
+    case LL: lane_forward<LL>(t, L, lim, xu, pn, pe, cn, ce, sbits); break;
                             NDGSBP_LANE_CASES(NDGSBP_FWD)
 #undef NDGSBP_FWD
                             default: break;
@@ -275,9 +284,9 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                             m[k] = q;
                             dl[k] = to_f(q) - old[k];
                         };
-                        switch (L) {
+                        switch (le) {
 #define NDGSBP_BWD(LL) \
-    case LL: lane_backward<LL>(xu, pn, pe, on, oe, sbits, par, lim, emit); break;
+    case LL: lane_backward<LL>(xu, pn, pe, L, on, oe, sbits, par, lim, emit); break;
                             NDGSBP_LANE_CASES(NDGSBP_BWD)
 #undef NDGSBP_BWD
                             default: break;
