@@ -554,7 +554,7 @@ static ndgsbp_status make_tile_plan(const Groups& g, const ndgsbp_params* p, int
     int slots = p->frames_per_cta ? p->frames_per_cta : std::max(1, std::min(16, threads / per_slot));
     slots = std::min(slots, max_slots);
     const size_t smem = table + static_cast<size_t>(slots) * slot_bytes;
-    TileKernelFn fn = pick_tile_kernel(p->msg_dtype);
+    TileKernelFn fn = pick_tile_kernel(p->msg_dtype, false, tile_lane_width(le), slots * per_slot <= threads);
     if (!fn) return NDGSBP_OK;
     int per_sm = 0;
     int64_t grid = 0;

@@ -23,7 +23,6 @@
 
 namespace ndgsbp {
 
-constexpr int kLane = 8;        // largest number of edges a lane holds
 constexpr int kMaxSlots = 16;   // largest number of frame slots per CTA
 
 __device__ __forceinline__ int tile_vb(int2 e, int c, int Z4) { return e.x + 4 * c - (c >= e.y ? Z4 : 0); }
@@ -33,13 +32,14 @@ __device__ __forceinline__ float& at_b(float* P, int vb) {
 }
 
 // Forward pass over the lane's LE edge positions, of which the first nreal are edges: prefix
-// pairs, lane total (cn, ce), sign bits.  Every lane of a code runs the same LE (no divergence
-// between lanes holding different edge counts); a position past nreal is the neutral factor
+// pairs, lane total (cn, ce), sign bits.  Every lane runs the same LE, the kernel instance's
+// compile-time width (no divergence between lanes holding different edge counts, no dispatch
+// on the width at run time); a position past nreal is the neutral factor
 // tanh = 1, i.e. u = 0 and (N, E) = (1/2, 0), which only scales the lane's pairs by exactly 1/2
 // (t = +0 there, so no sign either): the outputs of the real edges do not change.
 template <int LE>
-__device__ __forceinline__ void lane_forward(const float (&t)[kLane], int nreal, float lim, float (&xu)[kLane],
-                                             float (&pn)[kLane], float (&pe)[kLane], float& cn, float& ce,
+__device__ __forceinline__ void lane_forward(const float (&t)[LE], int nreal, float lim, float (&xu)[LE],
+                                             float (&pn)[LE], float (&pe)[LE], float& cn, float& ce,
                                              unsigned& sbits) {
 #pragma unroll
     for (int k = 0; k < LE; ++k) {
@@ -60,7 +60,7 @@ __device__ __forceinline__ void lane_forward(const float (&t)[kLane], int nreal,
 // Backward pass: the suffix starts from (sn, se), the product over the other lanes' edges;
 // outputs for the nreal real positions only.
 template <int LE, typename Emit>
-__device__ __forceinline__ void lane_backward(const float (&xu)[kLane], const float (&pn)[kLane], const float (&pe)[kLane],
+__device__ __forceinline__ void lane_backward(const float (&xu)[LE], const float (&pn)[LE], const float (&pe)[LE],
                                               int nreal, float sn, float se, unsigned sbits, unsigned par, float lim,
                                               Emit emit) {
 #pragma unroll
@@ -78,17 +78,23 @@ __device__ __forceinline__ void lane_backward(const float (&xu)[kLane], const fl
     }
 }
 
-#define NDGSBP_LANE_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
-
 // Shared state of a CTA (static part).
 struct TileShared {
     long long frame[kMaxSlots];
     int iter[kMaxSlots];
     int epoch[kMaxSlots];
+    int gofs[kMaxSlots];        // offset of the slot's grouping for its next iteration in the group tables
     unsigned unsat[kMaxSlots];
     unsigned err;
     int tile, code, cur_code, next, end, active;
 };
+
+// Iterations done by slot s, and the grouping its next iteration uses (iteration l uses
+// grouping (l - 1) mod n_groupings).
+__device__ __forceinline__ void set_iter(TileShared& sh, const TileCode& C, int s, int it) {
+    sh.iter[s] = it;
+    sh.gofs[s] = (it % C.n_groupings) * C.G * C.window;
+}
 
 template <typename MsgT, bool SERVE>
 __device__ __forceinline__ MsgT* slot_msgs(const TileCode& C, unsigned char* slot_base, int s, long long f) {
@@ -110,6 +116,16 @@ __device__ __forceinline__ long long claim_frame(TileShared& sh, const TileCode&
         return -1;
     }
     return sh.next < sh.end ? sh.next++ : -1;
+}
+
+// Fill slot s with the tile's next frame (tid 0 only).
+template <bool SERVE>
+__device__ __forceinline__ void fill_slot(TileShared& sh, const TileCode& C, int s) {
+    const long long f = claim_frame<SERVE>(sh, C);
+    sh.frame[s] = f;
+    set_iter(sh, C, s, (SERVE && f >= 0) ? (C.state_flag[f] == kSlotNew ? 0 : C.state_iter[f]) : 0);
+    sh.epoch[s] = 0;
+    if (SERVE && f >= 0) C.state_flag[f] = kSlotRunning;
 }
 
 // Load frame f into slot s (all threads): a fresh frame starts from P = L, messages 0; in
@@ -148,7 +164,220 @@ __device__ __forceinline__ void save_frame(const TileCode& C, unsigned char* bas
     }
 }
 
-template <typename MsgT, bool SERVE>
+// Decode the frames of one tile until none is left (all threads).  LE >= the code's edges per
+// lane le: the lane positions past a CN's degree (and in [le, LE)) are neutral.  REGB: one
+// round of the block covers a group (slots x window x Z x tpc <= threads, for every code of the
+// launch), so every lane keeps its message changes in registers for phase B; otherwise they go
+// through the slot's delta buffer.
+template <typename MsgT, bool SERVE, int LE, bool REGB>
+__device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, unsigned char* slots_base,
+                                         TileShared& sh) {
+    const RunArgs& r = C.r;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int Z = C.Z, Z4 = 4 * C.Z, W = C.window, nl = C.nl, md = C.maxdeg, tpc = C.tpc, le = C.le;
+    const int tsh = tpc == 1 ? 0 : (tpc == 2 ? 1 : 2);
+    const int* ldeg = reinterpret_cast<const int*>(tab + nl * md);
+    const int* glay = ldeg + 3 * nl;
+    const int per_slot = W * Z * tpc;           // CN-lanes of one group in one slot
+    const int work = C.slots * per_slot;
+    const int rounds = REGB ? 1 : (work + nt - 1) / nt;
+    const float lim = r.llr_max;
+    const unsigned gmask = tpc == 1 ? 0u : ((1u << tpc) - 1u) << ((tid & 31) & ~(tpc - 1));
+    for (;;) {
+        for (int g = 0; g < C.G; ++g) {
+            // ---- phase A: Eq. (1) on every CN of the group in every filled slot ----------
+            bool live = false;
+            int j = 0, c = 0, L = 0;
+            float* P = nullptr;
+            const int2* et = tab;
+            float dreg[LE];
+            for (int rr = 0; rr < rounds; ++rr) {
+                const int i = rr * nt + tid;
+                const int s = fast_div(i, C.div_slot);
+                live = i < work && sh.frame[s] >= 0;
+                const int w = i - s * per_slot;
+                const int cnl = w >> tsh, p = w & (tpc - 1);
+                j = fast_div(cnl, C.div_z);
+                c = cnl - j * Z;
+                L = 0;
+                float t[LE], old[LE], xu[LE], pn[LE], pe[LE];
+                float cn = 1.f, ce = 0.f;
+                unsigned sbits = 0u;
+                MsgT* m = nullptr;
+                float* dl = nullptr;
+                if (live) {
+                    unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
+                    P = reinterpret_cast<float*>(base);
+                    const int l = glay[sh.gofs[s] + g * W + j];
+                    const int k0 = p * le;
+                    L = min(max(ldeg[l] - k0, 0), le);
+                    m = slot_msgs<MsgT, SERVE>(C, base, s, sh.frame[s]) + ((l * Z + c) * tpc + p) * C.msg_stride;
+                    dl = reinterpret_cast<float*>(base + C.p_bytes + C.m_bytes) + (cnl * tpc + p) * C.delta_stride;
+                    et = tab + l * md + k0;
+#pragma unroll
+                    for (int k = 0; k < LE; ++k) {
+                        if (k < L) {
+                            old[k] = to_f(m[k]);
+                            t[k] = at_b(P, tile_vb(et[k], c, Z4)) - old[k];
+                        }
+                    }
+                    lane_forward<LE>(t, L, lim, xu, pn, pe, cn, ce, sbits);
+                }
+                // product over the other lanes of the CN, and the total sign parity
+                float on = 1.f, oe = 0.f;
+                unsigned par = __popc(sbits) & 1u;
+                if (tpc > 1) {
+                    const float xn = __shfl_xor_sync(gmask, cn, 1), xe = __shfl_xor_sync(gmask, ce, 1);
+                    par ^= __shfl_xor_sync(gmask, par, 1);
+                    if (tpc == 2) {
+                        on = xn;
+                        oe = xe;
+                    } else {
+                        const float pn2 = cn * xn, pe2 = fmaf(ce, xn + xe, cn * xe);   // this pair's total
+                        const float yn = __shfl_xor_sync(gmask, pn2, 2), ye = __shfl_xor_sync(gmask, pe2, 2);
+                        par ^= __shfl_xor_sync(gmask, par, 2);
+                        on = xn * yn;
+                        oe = fmaf(xe, yn + ye, xn * ye);
+                    }
+                }
+                if (live) {
+                    lane_backward<LE>(xu, pn, pe, L, on, oe, sbits, par, lim, [&](int k, float val) {
+                        const MsgT q = from_f<MsgT>(val);
+                        m[k] = q;
+                        const float d = to_f(q) - old[k];
+                        if (REGB)
+                            dreg[k] = d;
+                        else
+                            dl[k] = d;
+                    });
+                }
+            }
+            __syncthreads();
+            // ---- phase B: posterior += changes, layer position by layer position -----------
+            if (REGB) {
+                for (int jj = 0; jj < W; ++jj) {
+                    if (live && j == jj) {
+#pragma unroll
+                        for (int k = 0; k < LE; ++k)
+                            if (k < L) at_b(P, tile_vb(et[k], c, Z4)) += dreg[k];
+                    }
+                    __syncthreads();
+                }
+            } else {
+                const int per_pos = Z * tpc;
+                const int pwork = C.slots * per_pos;
+                for (int jj = 0; jj < W; ++jj) {
+                    for (int i = tid; i < pwork; i += nt) {
+                        const int s = fast_div(i, C.div_pos);
+                        if (sh.frame[s] < 0) continue;
+                        const int w = i - s * per_pos;
+                        const int cb = w >> tsh, p = w & (tpc - 1);
+                        const int cnl = jj * Z + cb;
+                        const int l = glay[sh.gofs[s] + g * W + jj];
+                        const int k0 = p * le;
+                        const int Lb = min(max(ldeg[l] - k0, 0), le);
+                        unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
+                        float* Pb = reinterpret_cast<float*>(base);
+                        const float* dl = reinterpret_cast<const float*>(base + C.p_bytes + C.m_bytes) +
+                                          (cnl * tpc + p) * C.delta_stride;
+                        const int2* eb = tab + l * md + k0;
+#pragma unroll
+                        for (int k = 0; k < LE; ++k)
+                            if (k < Lb) at_b(Pb, tile_vb(eb[k], cb, Z4)) += dl[k];
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+        // ---- Step 4: syndrome of every slot that needs it -----------------------------------
+        if (tid < C.slots) {
+            const int act = sh.frame[tid] >= 0 ? 1 : 0;
+            set_iter(sh, C, tid, sh.iter[tid] + act);
+            sh.epoch[tid] += act;
+            sh.unsat[tid] = 0u;
+        }
+        __syncthreads();
+        {
+            const int per_s = nl * Z * tpc;
+            const int swork = C.slots * per_s;
+            const int srounds = (swork + nt - 1) / nt;
+            for (int rr = 0; rr < srounds; ++rr) {
+                const int i = rr * nt + tid;
+                const int s = fast_div(i, C.div_syn);
+                unsigned pbit = 0u;
+                const bool live = i < swork && sh.frame[s] >= 0 && (r.early_stop || sh.iter[s] >= r.max_iter);
+                const int w = i - s * per_s;
+                const int cn_i = w >> tsh, p = w & (tpc - 1);
+                if (live) {
+                    const int l = fast_div(cn_i, C.div_z), cs = cn_i - l * Z;
+                    const int k0 = p * le;
+                    const int Ls = min(max(ldeg[l] - k0, 0), le);
+                    float* Ps = reinterpret_cast<float*>(slots_base + static_cast<size_t>(s) * C.slot_bytes);
+                    const int2* es = tab + l * md + k0;
+#pragma unroll
+                    for (int k = 0; k < LE; ++k)
+                        if (k < Ls) pbit ^= (at_b(Ps, tile_vb(es[k], cs, Z4)) < 0.f) ? 1u : 0u;
+                }
+                if (tpc > 1) {
+                    pbit ^= __shfl_xor_sync(gmask, pbit, 1);
+                    if (tpc == 4) pbit ^= __shfl_xor_sync(gmask, pbit, 2);
+                }
+                if (live && p == 0 && pbit) sh.unsat[s] = 1u;
+            }
+        }
+        __syncthreads();
+        // ---- retire finished frames (or, serving, park them) and refill their slots ---------
+        for (int s = 0; s < C.slots; ++s) {
+            const long long f = sh.frame[s];
+            if (f < 0) continue;
+            const int it = sh.iter[s];
+            const bool done = (r.early_stop && !sh.unsat[s]) || it >= r.max_iter;
+            const bool park = SERVE && !done && sh.epoch[s] >= C.epoch_iters;
+            if (!done && !park) continue;
+            unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
+            float* P = reinterpret_cast<float*>(base);
+            if (done) {
+                MsgT* msg = slot_msgs<MsgT, SERVE>(C, base, s, f);
+                if (r.msgs_out) {
+                    // edge k of CN c of layer l is CSR entry ebase(l) + c d_l + k (the rows of a
+                    // layer share its degree and list their VNs by block column)
+                    int ebase = 0;
+                    for (int l = 0; l < nl; ++l) {
+                        const int d = ldeg[l];
+                        for (int i = tid; i < Z * d; i += nt) {
+                            const int cc = i / d, k = i - cc * d, pl = k / le, kl = k - pl * le;
+                            r.msgs_out[f * r.E + ebase + i] = to_f(msg[((l * Z + cc) * tpc + pl) * C.msg_stride + kl]);
+                        }
+                        ebase += Z * d;
+                    }
+                }
+                write_frame_outputs(r, P, f, it, sh.unsat[s] ? 1 : 0, &sh.err);
+                if (SERVE && tid == 0) {
+                    C.state_flag[f] = kSlotDone;
+                    if (C.done_list) C.done_list[atomicAdd(C.done_count, 1)] = static_cast<int>(f);
+                }
+            } else {
+                save_frame<MsgT>(C, base, f);
+                if (tid == 0) C.state_iter[f] = it;
+            }
+            __syncthreads();
+            if (tid == 0) fill_slot<SERVE>(sh, C, s);
+            __syncthreads();
+            const long long nf = sh.frame[s];
+            if (nf >= 0) load_frame<MsgT, SERVE>(C, base, s, nf, sh.iter[s]);
+            __syncthreads();
+        }
+        if (tid == 0) {
+            int any = 0;
+            for (int s = 0; s < C.slots; ++s) any |= sh.frame[s] >= 0;
+            sh.active = any;
+        }
+        __syncthreads();
+        if (!sh.active) break;
+    }
+}
+
+template <typename MsgT, bool SERVE, int LE, bool REGB>
 __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TileShared sh;
@@ -174,9 +403,7 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                              static_cast<int>(min(static_cast<long long>(a.tile_frames), a.codes[0].r.n_frames - first)), 0);
         }
         const TileCode& C = a.codes[tile.x];
-        const RunArgs& r = C.r;
-        const int Z = C.Z, Z4 = 4 * C.Z, W = C.window, nl = C.nl, md = C.maxdeg, tpc = C.tpc, le = C.le;
-        const int tsh = tpc == 1 ? 0 : (tpc == 2 ? 1 : 2);
+        const int nl = C.nl, md = C.maxdeg;
         // code tables: (4 (b Z + s), Z - s) per edge, degrees, strides, offsets, group layers
         int* ldeg = reinterpret_cast<int*>(tab + nl * md);
         int* lstride = ldeg + nl;
@@ -189,20 +416,14 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                 lstride[i] = C.layer_stride[i];
                 loff[i] = C.layer_off[i];
             }
-            for (int i = tid; i < C.G * W * C.n_groupings; i += nt) glay[i] = C.group_layers[i];
+            for (int i = tid; i < C.G * C.window * C.n_groupings; i += nt) glay[i] = C.group_layers[i];
         }
         __syncthreads();
         if (tid == 0) {
             sh.cur_code = tile.x;
             sh.next = tile.y;
             sh.end = tile.y + tile.z;
-            for (int s = 0; s < C.slots; ++s) {
-                const long long f = claim_frame<SERVE>(sh, C);
-                sh.frame[s] = f;
-                sh.iter[s] = (SERVE && f >= 0) ? (C.state_flag[f] == kSlotNew ? 0 : C.state_iter[f]) : 0;
-                sh.epoch[s] = 0;
-                if (SERVE && f >= 0) C.state_flag[f] = kSlotRunning;
-            }
+            for (int s = 0; s < C.slots; ++s) fill_slot<SERVE>(sh, C, s);
         }
         __syncthreads();
         // initialisation of every filled slot: P_n = L_n, L_{m->n} = 0 (or the saved state)
@@ -212,212 +433,33 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
             load_frame<MsgT, SERVE>(C, slots_base + static_cast<size_t>(s) * C.slot_bytes, s, f, sh.iter[s]);
         }
         __syncthreads();
-        const int per_slot = W * Z * tpc;           // CN-lanes of one group in one slot
-        const int work = C.slots * per_slot;
-        const int rounds = (work + nt - 1) / nt;
-        const float lim = r.llr_max;
-        const unsigned gmask = tpc == 1 ? 0u : ((1u << tpc) - 1u) << ((tid & 31) & ~(tpc - 1));
-        for (;;) {
-            for (int g = 0; g < C.G; ++g) {
-                // ---- phase A: Eq. (1) on every CN of the group in every filled slot ----------
-                for (int rr = 0; rr < rounds; ++rr) {
-                    const int i = rr * nt + tid;
-                    const int s = fast_div(i, C.div_slot);
-                    const bool live = i < work && sh.frame[s] >= 0;
-                    const int w = i - s * per_slot;
-                    const int cnl = w >> tsh, p = w & (tpc - 1);
-                    const int j = fast_div(cnl, C.div_z), c = cnl - j * Z;
-                    int L = 0;
-                    float t[kLane], old[kLane], xu[kLane], pn[kLane], pe[kLane];
-                    float cn = 1.f, ce = 0.f;
-                    unsigned sbits = 0u;
-                    float* P = nullptr;
-                    MsgT* m = nullptr;
-                    float* dl = nullptr;
-                    int k0 = 0;
-                    if (live) {
-                        unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
-                        P = reinterpret_cast<float*>(base);
-                        // the slot's grouping for its current iteration (iterations done so far)
-                        const int l = glay[(sh.iter[s] % C.n_groupings) * C.G * W + g * W + j];
-                        const int d = ldeg[l];
-                        k0 = p * le;
-                        L = min(max(d - k0, 0), le);
-                        m = slot_msgs<MsgT, SERVE>(C, base, s, sh.frame[s]) + ((l * Z + c) * tpc + p) * C.msg_stride;
-                        dl = reinterpret_cast<float*>(base + C.p_bytes + C.m_bytes) + (cnl * tpc + p) * C.delta_stride;
-                        const int2* et = tab + l * md + k0;
-#pragma unroll
-                        for (int k = 0; k < kLane; ++k) {
-                            if (k < L) {
-                                old[k] = to_f(m[k]);
-                                t[k] = at_b(P, tile_vb(et[k], c, Z4)) - old[k];
-                            }
-                        }
-                        switch (le) {
-#define NDGSBP_FWD(LL) \
-    case LL: lane_forward<LL>(t, L, lim, xu, pn, pe, cn, ce, sbits); break;
-                            NDGSBP_LANE_CASES(NDGSBP_FWD)
-#undef NDGSBP_FWD
-                            default: break;
-                        }
-                    }
-                    // product over the other lanes of the CN, and the total sign parity
-                    float on = 1.f, oe = 0.f;
-                    unsigned par = __popc(sbits) & 1u;
-                    if (tpc > 1) {
-                        const float xn = __shfl_xor_sync(gmask, cn, 1), xe = __shfl_xor_sync(gmask, ce, 1);
-                        par ^= __shfl_xor_sync(gmask, par, 1);
-                        if (tpc == 2) {
-                            on = xn;
-                            oe = xe;
-                        } else {
-                            const float pn2 = cn * xn, pe2 = fmaf(ce, xn + xe, cn * xe);   // this pair's total
-                            const float yn = __shfl_xor_sync(gmask, pn2, 2), ye = __shfl_xor_sync(gmask, pe2, 2);
-                            par ^= __shfl_xor_sync(gmask, par, 2);
-                            on = xn * yn;
-                            oe = fmaf(xe, yn + ye, xn * ye);
-                        }
-                    }
-                    if (live) {
-                        auto emit = [&](int k, float val) {
-                            const MsgT q = from_f<MsgT>(val);
-                            m[k] = q;
-                            dl[k] = to_f(q) - old[k];
-                        };
-                        switch (le) {
-#define NDGSBP_BWD(LL) \
-    case LL: lane_backward<LL>(xu, pn, pe, L, on, oe, sbits, par, lim, emit); break;
-                            NDGSBP_LANE_CASES(NDGSBP_BWD)
-#undef NDGSBP_BWD
-                            default: break;
-                        }
-                    }
-                }
-                __syncthreads();
-                // ---- phase B: posterior += changes, layer position by layer position -----------
-                const int per_pos = Z * tpc;
-                const int pwork = C.slots * per_pos;
-                for (int jj = 0; jj < W; ++jj) {
-                    for (int i = tid; i < pwork; i += nt) {
-                        const int s = fast_div(i, C.div_pos);
-                        if (sh.frame[s] < 0) continue;
-                        const int w = i - s * per_pos;
-                        const int c = w >> tsh, p = w & (tpc - 1);
-                        const int cnl = jj * Z + c;
-                        const int l = glay[(sh.iter[s] % C.n_groupings) * C.G * W + g * W + jj];
-                        const int k0 = p * le;
-                        const int L = min(max(ldeg[l] - k0, 0), le);
-                        unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
-                        float* P = reinterpret_cast<float*>(base);
-                        const float* dl = reinterpret_cast<const float*>(base + C.p_bytes + C.m_bytes) +
-                                          (cnl * tpc + p) * C.delta_stride;
-                        const int2* et = tab + l * md + k0;
-                        for (int k = 0; k < L; ++k) at_b(P, tile_vb(et[k], c, Z4)) += dl[k];
-                    }
-                    __syncthreads();
-                }
-            }
-            // ---- Step 4: syndrome of every slot that needs it -----------------------------------
-            if (tid < C.slots) {
-                sh.iter[tid] += (sh.frame[tid] >= 0) ? 1 : 0;
-                sh.epoch[tid] += (sh.frame[tid] >= 0) ? 1 : 0;
-                sh.unsat[tid] = 0u;
-            }
-            __syncthreads();
-            {
-                const int per_s = nl * Z * tpc;
-                const int swork = C.slots * per_s;
-                const int srounds = (swork + nt - 1) / nt;
-                for (int rr = 0; rr < srounds; ++rr) {
-                    const int i = rr * nt + tid;
-                    const int s = fast_div(i, C.div_syn);
-                    unsigned pbit = 0u;
-                    const bool live = i < swork && sh.frame[s] >= 0 && (r.early_stop || sh.iter[s] >= r.max_iter);
-                    const int w = i - s * per_s;
-                    const int cn_i = w >> tsh, p = w & (tpc - 1);
-                    if (live) {
-                        const int l = fast_div(cn_i, C.div_z), c = cn_i - l * Z;
-                        const int k0 = p * le;
-                        const int L = min(max(ldeg[l] - k0, 0), le);
-                        float* P = reinterpret_cast<float*>(slots_base + static_cast<size_t>(s) * C.slot_bytes);
-                        const int2* et = tab + l * md + k0;
-                        for (int k = 0; k < L; ++k) pbit ^= (at_b(P, tile_vb(et[k], c, Z4)) < 0.f) ? 1u : 0u;
-                    }
-                    if (tpc > 1) {
-                        pbit ^= __shfl_xor_sync(gmask, pbit, 1);
-                        if (tpc == 4) pbit ^= __shfl_xor_sync(gmask, pbit, 2);
-                    }
-                    if (live && p == 0 && pbit) sh.unsat[s] = 1u;
-                }
-            }
-            __syncthreads();
-            // ---- retire finished frames (or, serving, park them) and refill their slots ---------
-            for (int s = 0; s < C.slots; ++s) {
-                const long long f = sh.frame[s];
-                if (f < 0) continue;
-                const int it = sh.iter[s];
-                const bool done = (r.early_stop && !sh.unsat[s]) || it >= r.max_iter;
-                const bool park = SERVE && !done && sh.epoch[s] >= C.epoch_iters;
-                if (!done && !park) continue;
-                unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
-                float* P = reinterpret_cast<float*>(base);
-                if (done) {
-                    MsgT* msg = slot_msgs<MsgT, SERVE>(C, base, s, f);
-                    if (r.msgs_out) {
-                        // edge k of CN c of layer l is CSR entry ebase(l) + c d_l + k (the rows of a
-                        // layer share its degree and list their VNs by block column)
-                        int ebase = 0;
-                        for (int l = 0; l < nl; ++l) {
-                            const int d = ldeg[l];
-                            for (int i = tid; i < Z * d; i += nt) {
-                                const int c = i / d, k = i - c * d, pl = k / le, kl = k - pl * le;
-                                r.msgs_out[f * r.E + ebase + i] = to_f(msg[((l * Z + c) * tpc + pl) * C.msg_stride + kl]);
-                            }
-                            ebase += Z * d;
-                        }
-                    }
-                    write_frame_outputs(r, P, f, it, sh.unsat[s] ? 1 : 0, &sh.err);
-                    if (SERVE && tid == 0) {
-                        C.state_flag[f] = kSlotDone;
-                        if (C.done_list) C.done_list[atomicAdd(C.done_count, 1)] = static_cast<int>(f);
-                    }
-                } else {
-                    save_frame<MsgT>(C, base, f);
-                    if (tid == 0) C.state_iter[f] = it;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    const long long nf = claim_frame<SERVE>(sh, C);
-                    sh.frame[s] = nf;
-                    sh.iter[s] = (SERVE && nf >= 0) ? (C.state_flag[nf] == kSlotNew ? 0 : C.state_iter[nf]) : 0;
-                    sh.epoch[s] = 0;
-                    if (SERVE && nf >= 0) C.state_flag[nf] = kSlotRunning;
-                }
-                __syncthreads();
-                const long long nf = sh.frame[s];
-                if (nf >= 0) load_frame<MsgT, SERVE>(C, base, s, nf, sh.iter[s]);
-                __syncthreads();
-            }
-            if (tid == 0) {
-                int any = 0;
-                for (int s = 0; s < C.slots; ++s) any |= sh.frame[s] >= 0;
-                sh.active = any;
-            }
-            __syncthreads();
-            if (!sh.active) break;
-        }
+        run_tile<MsgT, SERVE, LE, REGB>(C, tab, slots_base, sh);
     }
 }
 
-TileKernelFn pick_tile_kernel(int msg_dtype, bool serve) {
-    switch (msg_dtype) {
-        case NDGSBP_F32: return serve ? tile_decode_kernel<float, true> : tile_decode_kernel<float, false>;
-        case NDGSBP_F16: return serve ? tile_decode_kernel<__half, true> : tile_decode_kernel<__half, false>;
-        case NDGSBP_BF16:
-            return serve ? tile_decode_kernel<__nv_bfloat16, true> : tile_decode_kernel<__nv_bfloat16, false>;
+template <typename MsgT, bool SERVE>
+static TileKernelFn pick_width(int lane_width, bool regb) {
+    switch (lane_width) {
+        case 4: return regb ? tile_decode_kernel<MsgT, SERVE, 4, true> : tile_decode_kernel<MsgT, SERVE, 4, false>;
+        case 6: return regb ? tile_decode_kernel<MsgT, SERVE, 6, true> : tile_decode_kernel<MsgT, SERVE, 6, false>;
+        case 8: return regb ? tile_decode_kernel<MsgT, SERVE, 8, true> : tile_decode_kernel<MsgT, SERVE, 8, false>;
         default: return nullptr;
     }
 }
+
+TileKernelFn pick_tile_kernel(int msg_dtype, bool serve, int lane_width, bool regb) {
+    switch (msg_dtype) {
+        case NDGSBP_F32: return serve ? pick_width<float, true>(lane_width, regb) : pick_width<float, false>(lane_width, regb);
+        case NDGSBP_F16:
+            return serve ? pick_width<__half, true>(lane_width, regb) : pick_width<__half, false>(lane_width, regb);
+        case NDGSBP_BF16:
+            return serve ? pick_width<__nv_bfloat16, true>(lane_width, regb)
+                         : pick_width<__nv_bfloat16, false>(lane_width, regb);
+        default: return nullptr;
+    }
+}
+
+int tile_lane_width(int le) { return le < 1 ? 0 : le <= 4 ? 4 : le <= 6 ? 6 : le <= 8 ? 8 : 0; }
 
 size_t tile_table_bytes(const QcLayout& Q) {
     const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;

@@ -84,7 +84,14 @@ struct TileArgs {
 
 typedef void (*TileKernelFn)(const TileArgs);
 
-TileKernelFn pick_tile_kernel(int msg_dtype, bool serve = false);
+// Kernel instance for a launch: lane_width = tile_lane_width of the largest le among its codes
+// (the unrolled edge positions per lane); regb when one round of the block covers a group of
+// every code (slots x window x Z x tpc <= block threads), which keeps message changes in
+// registers between phases A and B.  nullptr for an unknown dtype or width.
+TileKernelFn pick_tile_kernel(int msg_dtype, bool serve, int lane_width, bool regb);
+
+// Compiled lane width for le edges per lane: 4, 6 or 8 (0 when le is not in 1..8).
+int tile_lane_width(int le);
 
 // Storage shape of the tile kernel for a code at tpc lanes per CN: edges per lane, the odd lane
 // segment stride, messages per frame (all layers) and deltas per frame (one window).

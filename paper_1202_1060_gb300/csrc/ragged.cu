@@ -60,8 +60,8 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
     if (params->max_iter < 1 || !(params->llr_max > 0.f && params->llr_max <= 30.f))
         return fail(NDGSBP_ERR_INVALID, "ragged_create: bad max_iter or llr_max");
     const int ms = params->msg_dtype == NDGSBP_F32 ? 4 : 2;
-    TileKernelFn fn = pick_tile_kernel(params->msg_dtype);
-    if (!fn) return fail(NDGSBP_ERR_INVALID, "ragged_create: msg_dtype must be F32, F16 or BF16");
+    if (!pick_tile_kernel(params->msg_dtype, false, 8, false))
+        return fail(NDGSBP_ERR_INVALID, "ragged_create: msg_dtype must be F32, F16 or BF16");
     int dev = 0, sms = 0, optin = 0, smem_sm = 0, reserved = 0;
     RAGGED_TRY(cudaGetDevice(&dev));
     RAGGED_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -210,6 +210,19 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         if (!msg_smem) {
             msg_off[i] = ws;   // grid not known yet: sized below
         }
+    }
+    // kernel instance: the widest lane of the launch's codes; message changes in registers when
+    // one round of the block covers a group of every code
+    int lane_width = 0;
+    bool regb = true;
+    for (int i = 0; i < n_batches; ++i) {
+        lane_width = std::max(lane_width, tile_lane_width(cp[i].le));
+        regb = regb && cp[i].slots * cp[i].per_slot <= threads;
+    }
+    TileKernelFn fn = pick_tile_kernel(params->msg_dtype, false, lane_width, regb);
+    if (!fn) {
+        delete h;
+        return fail(NDGSBP_ERR_UNSUPPORTED, "ragged_create: no kernel instance for lane width %d", lane_width);
     }
     RAGGED_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));

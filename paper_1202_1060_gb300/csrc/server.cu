@@ -370,8 +370,8 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         return fail(NDGSBP_ERR_INVALID, "server_create: need 1..%d codes, params and epoch_iters >= 1", kTileMaxCodes);
     if (params->max_iter < 1 || !(params->llr_max > 0.f && params->llr_max <= 30.f))
         return fail(NDGSBP_ERR_INVALID, "server_create: bad max_iter or llr_max");
-    TileKernelFn fn = pick_tile_kernel(params->msg_dtype, /*serve=*/true);
-    if (!fn) return fail(NDGSBP_ERR_INVALID, "server_create: msg_dtype must be F32, F16 or BF16");
+    if (!pick_tile_kernel(params->msg_dtype, /*serve=*/true, 8, false))
+        return fail(NDGSBP_ERR_INVALID, "server_create: msg_dtype must be F32, F16 or BF16");
     const int ms = params->msg_dtype == NDGSBP_F32 ? 4 : 2;
     std::unique_ptr<ndgsbp_server> h(new (std::nothrow) ndgsbp_server);
     if (!h) return fail(NDGSBP_ERR_NOMEM, "out of host memory");
@@ -450,6 +450,17 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         p.slots = static_cast<int>(std::min<double>(kMaxPoolSlots, std::floor(share * hbm_budget_bytes / per)));
         if (p.slots < 1) return fail(NDGSBP_ERR_BUDGET, "server_create: the budget leaves no slot for code %d", i);
     }
+    // kernel instance: the widest lane of the pools' codes; message changes in registers when one
+    // round of the block covers a group of every code
+    int lane_width = 0;
+    bool regb = true;
+    for (int i = 0; i < n_codes; ++i) {
+        const Pool& p = h->pools[i];
+        lane_width = std::max(lane_width, tile_lane_width(p.le));
+        regb = regb && p.cta_slots * p.Q->window * p.Q->Z * p.tpc <= threads;
+    }
+    TileKernelFn fn = pick_tile_kernel(params->msg_dtype, /*serve=*/true, lane_width, regb);
+    if (!fn) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: no kernel instance for lane width %d", lane_width);
     cudaError_t e = cudaSuccess;
     auto dmalloc = [&](void** ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
