@@ -522,11 +522,13 @@ def _mufu_roofline(peaks, peak_kind, sms, mufu_ops, kernel_s, kernel, launches, 
 
 
 def run_ragged(args):
-    """Ragged batching: one persistent tile-kernel launch (CUDA-graph replay) over 200,000 frames
-    of 4 QC codes in a 40/30/20/10 mix, FP16 messages, per-frame early stop, I_max 30, tile shape
-    from the autotuner, each code at its FER ~ 1e-3 point.  A step = channel generation for the 4
-    codes + the ragged launch.  Beside it: the plain FP32 single-code batched path (each code's
-    batch decoded by its own default launch) on the same frames."""
+    """Ragged batching over 200,000 frames of 4 QC codes in a 40/30/20/10 mix, FP16 messages,
+    per-frame early stop, I_max 30, each code at its FER ~ 1e-3 point, replayed as a CUDA graph.
+    The autotuner picks the launch: one persistent tile-kernel launch (block size, residency,
+    per-code tile shape) or the per-code mode (each code's own plan, forked streams); the other
+    mode is timed beside it.  A step = channel generation for the 4 codes + the ragged launch.
+    Also beside it: the plain FP32 single-code batched path (each code's batch decoded by its own
+    default launch, one after the other) on the same frames."""
     import numpy as np
     import torch
     torch.cuda.set_device(0)
@@ -561,6 +563,22 @@ def run_ragged(args):
     params, tuned_ms = nd.ragged_autotune(batches, p0, sample_frames=8192,
                                           cache_path=os.path.join(ROOT, "gpurun_out", "tune_cache.txt"))
     tune_s = time.perf_counter() - t0
+    per_code_mode = params.variant == nd.VARIANT_RAGGED_PER_CODE
+    # the other mode, timed on the same frames (tile: the library's default shape)
+    other_p = nd.params_default(max_iter=imax, msg_dtype=nd.F16,
+                                variant=nd.VARIANT_TILE if per_code_mode else nd.VARIANT_RAGGED_PER_CODE)
+    other_b = [dict(b, frames_per_cta=0, lanes_per_cn=0) for b in batches] if per_code_mode else batches
+    rg_other = nd.Ragged(other_b, other_p)
+    for _ in range(2):
+        rg_other.graph_launch(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        rg_other.graph_launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    other_ms = e0.elapsed_time(e1) / 3
+    del rg_other
     rg = nd.Ragged(batches, params)
     plan, n_tiles = rg.info()
     for s in range(args.warmup):
@@ -621,17 +639,25 @@ def run_ragged(args):
         "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f16", "data": "synthetic",
         "config": {"workload": "ragged: 200,000 frames of 4 QC codes (n=576 r1/2, 1152 r2/3, 2304 r3/4, 8192 r27/32) "
-                               "in a 40/30/20/10 mix, one persistent tile-kernel launch replayed as a CUDA graph, "
-                               "FP16 messages, I_max 30, early stop, each code at its FER~1e-3 Eb/N0, tile shape "
-                               "from the autotuner; step = channel generation + decode",
+                               "in a 40/30/20/10 mix, FP16 messages, I_max 30, early stop, each code at its "
+                               "FER~1e-3 Eb/N0, replayed as a CUDA graph; launch mode from the autotuner: "
+                               + ("per-code plans on forked streams" if per_code_mode else
+                                  "one persistent tile-kernel launch") + "; step = channel generation + decode",
+                   "mode": "per_code" if per_code_mode else "tile",
                    "l2": "inputs larger than L2 (1.5 GB of LLRs)"},
         "decode_only_gbit_s": bits * args.steps / dec_s / 1e9,
         "plain_fp32_single_code_gbit_s": bits / plain_s / 1e9,
         "speedup_vs_plain_fp32": (bits * args.steps / dec_s) / (bits / plain_s),
-        "per_code": per_code, "tuned": {"block_threads": params.block_threads, "ctas_per_sm": params.ctas_per_sm, "tile_launch_ms": tuned_ms,
-                                        "tuning_s": tune_s, "tiles": n_tiles, "plan": plan},
-        "clocks": clk, "gpu_launches": 5 * args.steps,
-        "roofline": _mufu_roofline(peaks, kind, sms, mufu * args.steps, dec_s, "tile_decode_kernel", args.steps),
+        "per_code": per_code, "tuned": {"mode": "per_code" if per_code_mode else "tile",
+                                        "block_threads": params.block_threads, "ctas_per_sm": params.ctas_per_sm,
+                                        "launch_ms": tuned_ms, "tuning_s": tune_s, "tiles_or_codes": n_tiles,
+                                        "plan": plan,
+                                        "other_mode_ms": other_ms},
+        "clocks": clk, "gpu_launches": (8 if per_code_mode else 5) * args.steps,
+        "roofline": _mufu_roofline(peaks, kind, sms, mufu * args.steps, dec_s,
+                                   "per-code launches (qc_decode_kernel for n=576/1152/2304, tile_decode_kernel for "
+                                   "n=8192) on forked streams" if per_code_mode else "tile_decode_kernel",
+                                   args.steps),
         "e2e": None, "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)

@@ -78,6 +78,10 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_VARIANT_QC_DIRECT 10 /* layered QC kernel, 2-layer windows: edges off the block
                                       columns both layers touch are written back at once, one
                                       ordered round for the rest (same results as QC) */
+#define NDGSBP_VARIANT_RAGGED_PER_CODE 11 /* ragged launches only: every code runs its own
+                                      ndgsbp_decode plan (the library's choice for it), the launches
+                                      forked onto concurrent streams and joined (same results as
+                                      decoding each batch alone) */
 
 /* stats counters accumulated by ndgsbp_decode_ex (uint64 each) */
 #define NDGSBP_STAT_FRAMES 0
@@ -291,15 +295,23 @@ typedef struct ndgsbp_ragged ndgsbp_ragged;
  * slots as frames retire.  params gives max_iter, msg_dtype, llr_max, early_stop, block_threads
  * (shared by every code) and ctas_per_sm, the residency target k: every CTA's shared memory is
  * capped at 1/k of the SM's, and a code whose messages do not fit under the cap keeps them in
- * global memory (0 = 2 CTAs per SM when every code fits, else 1).  The batches' buffers are recorded in the handle: later
+ * global memory (0 = 2 CTAs per SM when every code fits, else 1).  With params->variant =
+ * NDGSBP_VARIANT_RAGGED_PER_CODE the handle instead keeps one ndgsbp_decode plan per code (the
+ * library's default choice, e.g. the layered QC kernel where it applies; block_threads,
+ * ctas_per_sm and the batches' tile shapes are then ignored) and a launch forks them onto
+ * concurrent streams that the caller's stream joins; a graph replay holds all of them.  Any
+ * grouping is accepted in that mode.  The batches' buffers are recorded in the handle: later
  * launches reuse them, so refill their contents rather than moving them.  Allocates the tile
  * list and the launch's workspace (owned by the handle; call before any stream capture).
  * Errors: INVALID, UNSUPPORTED (a code that is not QC in whole layers, degree > 32), CUDA, NOMEM. */
 ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batches,
                                    const ndgsbp_params* params, ndgsbp_ragged** out);
-/* Launch plan (variant TILE; grid, block, shared bytes) and number of tiles. */
+/* Launch plan (variant TILE; grid, block, shared bytes) and number of tiles; in the per-code
+ * mode variant RAGGED_PER_CODE, the summed grids, the largest block and shared size, and the
+ * number of codes in n_tiles. */
 ndgsbp_status ndgsbp_ragged_info(const ndgsbp_ragged* ragged, ndgsbp_plan* plan, int32_t* n_tiles);
-/* Enqueue the launch on stream: a counter reset and one kernel. */
+/* Enqueue the launch on stream: a counter reset and one kernel (per-code mode: a fork onto the
+ * handle's streams, one reset and kernel per code, and a join back into stream). */
 ndgsbp_status ndgsbp_ragged_launch(ndgsbp_ragged* ragged, void* stream);
 /* The same launch through a CUDA graph: the first call on a stream captures the reset and the
  * kernel into a graph and instantiates it, later calls replay it (one cudaGraphLaunch). */
@@ -343,9 +355,10 @@ ndgsbp_status ndgsbp_autotune(const ndgsbp_groups* groups, const ndgsbp_params* 
  * (frames_per_cta, lanes_per_cn) is tuned with ndgsbp_autotune (TILE_ONLY) on the first
  * sample_frames frames of each batch (all when <= 0); then the whole ragged launch over the
  * batches is timed (one untimed launch, best of two timed) at 1, 2, 3 and 4 CTAs per SM, with
- * frame slots capped to fit; the fastest (block size, residency) wins.  On return
- * batches[i].frames_per_cta / lanes_per_cn and *params_out (variant TILE, block_threads,
- * ctas_per_sm) hold the winner, and *best_ms its launch time.  The timing launches write the batches'
+ * frame slots capped to fit, and the per-code mode (NDGSBP_VARIANT_RAGGED_PER_CODE) is timed
+ * the same way; the fastest (block size, residency) or the per-code mode wins.  On return
+ * batches[i].frames_per_cta / lanes_per_cn and *params_out (variant TILE with block_threads and
+ * ctas_per_sm, or RAGGED_PER_CODE) hold the winner, and *best_ms its launch time.  The timing launches write the batches'
  * output buffers.  Errors: as ndgsbp_autotune and ndgsbp_ragged_create. */
 ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches,
                                      const ndgsbp_params* params, int64_t sample_frames,

@@ -303,6 +303,36 @@ ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches, c
             }
         }
     }
+    // every code on its own default plan, forked onto concurrent streams
+    if (!st) {
+        ndgsbp_params p = *params;
+        p.variant = NDGSBP_VARIANT_RAGGED_PER_CODE;
+        ndgsbp_ragged* rg = nullptr;
+        if (ndgsbp_ragged_create(orig.data(), n_batches, &p, &rg) != NDGSBP_OK) {
+            clear_error();
+        } else {
+            std::vector<float> t;
+            for (int rep = 0; rep < 3 && !st; ++rep) {
+                cudaEventRecord(e0, stream);
+                st = ndgsbp_ragged_launch(rg, stream);
+                cudaEventRecord(e1, stream);
+                if (!st && cudaEventSynchronize(e1) != cudaSuccess)
+                    st = fail(NDGSBP_ERR_CUDA, "ragged_autotune: launch failed");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) t.push_back(ms);
+            }
+            ndgsbp_ragged_destroy(rg);
+            if (!st) {
+                const double ms = std::min(t[0], t[1]);
+                if (best < 0.0 || ms < best) {
+                    best = ms;
+                    best_b = orig;
+                    best_p = p;
+                }
+            }
+        }
+    }
     if (e1) cudaEventDestroy(e1);
     if (e0) cudaEventDestroy(e0);
     if (stream) cudaStreamDestroy(stream);

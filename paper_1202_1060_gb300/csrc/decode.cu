@@ -19,6 +19,7 @@
 // arithmetic instead of tables.
 #include <algorithm>
 #include <cstring>
+#include <new>
 
 #include "decode_qc.h"
 #include "decode_tile.h"
@@ -554,7 +555,7 @@ static ndgsbp_status make_tile_plan(const Groups& g, const ndgsbp_params* p, int
     int slots = p->frames_per_cta ? p->frames_per_cta : std::max(1, std::min(16, threads / per_slot));
     slots = std::min(slots, max_slots);
     const size_t smem = table + static_cast<size_t>(slots) * slot_bytes;
-    TileKernelFn fn = pick_tile_kernel(p->msg_dtype, false, tile_lane_width(le), slots * per_slot <= threads);
+    TileKernelFn fn = pick_tile_kernel(p->msg_dtype, false, tile_lane_width(le), slots * per_slot <= threads, true);
     if (!fn) return NDGSBP_OK;
     int per_sm = 0;
     int64_t grid = 0;
@@ -819,6 +820,33 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
     }
     CUDA_TRY(cudaGetLastError());
     return NDGSBP_OK;
+}
+
+Plan* plan_create(const Groups& g, const ndgsbp_params* p, int64_t n_frames, ndgsbp_status* st) {
+    Plan* plan = new (std::nothrow) Plan;
+    if (!plan) {
+        *st = fail(NDGSBP_ERR_NOMEM, "out of host memory");
+        return nullptr;
+    }
+    *st = make_plan(g, p, n_frames, *plan);
+    if (*st) {
+        delete plan;
+        return nullptr;
+    }
+    return plan;
+}
+
+void plan_destroy(Plan* plan) { delete plan; }
+
+const ndgsbp_plan& plan_info(const Plan& plan) { return plan.pub; }
+
+ndgsbp_status plan_enqueue(const Groups& g, const Plan& plan, const ndgsbp_params* p, const void* d_llr,
+                           int32_t llr_dtype, int64_t n_frames, void* ws, uint32_t* d_hard_bits, int32_t* d_iters,
+                           uint8_t* d_syndrome_ok, float* d_posterior, const ndgsbp_extras* extras, cudaStream_t s) {
+    if (n_frames == 0) return NDGSBP_OK;
+    CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), s));
+    return launch_plan(g, plan, p, d_llr, llr_dtype, n_frames, static_cast<unsigned char*>(ws), d_hard_bits, d_iters,
+                       d_syndrome_ok, d_posterior, extras, s);
 }
 
 }  // namespace ndgsbp

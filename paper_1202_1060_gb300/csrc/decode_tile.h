@@ -87,8 +87,9 @@ typedef void (*TileKernelFn)(const TileArgs);
 // Kernel instance for a launch: lane_width = tile_lane_width of the largest le among its codes
 // (the unrolled edge positions per lane); regb when one round of the block covers a group of
 // every code (slots x window x Z x tpc <= block threads), which keeps message changes in
-// registers between phases A and B.  nullptr for an unknown dtype or width.
-TileKernelFn pick_tile_kernel(int msg_dtype, bool serve, int lane_width, bool regb);
+// registers between phases A and B; single for a launch over one code (codes[0] only).  nullptr
+// for an unknown dtype or width.
+TileKernelFn pick_tile_kernel(int msg_dtype, bool serve, int lane_width, bool regb, bool single);
 
 // Compiled lane width for le edges per lane: 4, 6 or 8 (0 when le is not in 1..8).
 int tile_lane_width(int le);

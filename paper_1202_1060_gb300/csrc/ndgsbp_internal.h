@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime_api.h>
+
 #include "ndgsbp.h"
 
 namespace ndgsbp {
@@ -125,6 +127,18 @@ void compile_qc_layout(const Code& code, const std::vector<int32_t>& grp_ptr,
 const Layout& flood_layout(const Groups& g);
 const QcLayout& flood_qc_layout(const Groups& g);
 void release_device_layouts(Groups& g);   // frees device copies (defined in the CUDA file)
+
+// A decode plan kept across launches (ragged launches in the per-code mode): what
+// ndgsbp_decode plans for (groups, params, n_frames), with the grouping's tables on the device.
+struct Plan;
+Plan* plan_create(const Groups& g, const ndgsbp_params* p, int64_t n_frames, ndgsbp_status* st);
+void plan_destroy(Plan* plan);
+const ndgsbp_plan& plan_info(const Plan& plan);
+// Enqueue the plan's decode on stream s with ws (plan_info(plan).workspace_bytes, 256-aligned)
+// as its scratch: the counter reset and the kernel, as ndgsbp_decode_ex does.
+ndgsbp_status plan_enqueue(const Groups& g, const Plan& plan, const ndgsbp_params* p, const void* d_llr,
+                           int32_t llr_dtype, int64_t n_frames, void* ws, uint32_t* d_hard_bits, int32_t* d_iters,
+                           uint8_t* d_syndrome_ok, float* d_posterior, const ndgsbp_extras* extras, cudaStream_t s);
 
 }  // namespace ndgsbp
 

@@ -1,7 +1,10 @@
 // Ragged batches: several QC codes decoded by one persistent launch of the tile kernel, with
-// an optional CUDA-graph replay of that launch.
+// an optional CUDA-graph replay of that launch.  In the per-code mode every code runs its own
+// decode plan instead, the launches forked onto concurrent streams and joined.
 #include <algorithm>
 #include <cstring>
+#include <memory>
+#include <new>
 #include <vector>
 
 #include "decode_tile.h"
@@ -19,11 +22,23 @@ struct ndgsbp_ragged {
     ndgsbp_plan plan{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // per-code mode: one plan, batch and workspace offset per code; streams for codes 1..n-1,
+    // events[0] forks, events[i] joins code i
+    bool per_code = false;
+    ndgsbp_params params{};
+    std::vector<ndgsbp::Plan*> plans;
+    std::vector<ndgsbp_batch> batches;
+    std::vector<size_t> ws_off;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
     ~ndgsbp_ragged() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        for (ndgsbp::Plan* p : plans) ndgsbp::plan_destroy(p);
         int cur = 0;
         if (cudaGetDevice(&cur) == cudaSuccess && cudaSetDevice(device) == cudaSuccess) {
+            for (cudaStream_t st : streams) cudaStreamDestroy(st);
+            for (cudaEvent_t ev : events) cudaEventDestroy(ev);
             cudaFree(workspace);
             cudaFree(d_tiles);
             cudaSetDevice(cur);
@@ -50,6 +65,59 @@ using namespace ndgsbp;
         if (_e != cudaSuccess) return fail(NDGSBP_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
     } while (0)
 
+// Per-code mode: one ndgsbp_decode plan per batch (the library's default choice for its code),
+// their workspaces in one allocation, streams and events for the fork and the join.
+static ndgsbp_status create_per_code(const ndgsbp_batch* batches, int32_t n_batches, const ndgsbp_params* params,
+                                     ndgsbp_ragged** out) {
+    std::unique_ptr<ndgsbp_ragged> h(new (std::nothrow) ndgsbp_ragged);
+    if (!h) return fail(NDGSBP_ERR_NOMEM, "out of host memory");
+    RAGGED_TRY(cudaGetDevice(&h->device));
+    std::memset(&h->args, 0, sizeof(h->args));
+    h->per_code = true;
+    h->params = *params;
+    h->params.variant = NDGSBP_VARIANT_AUTO;
+    h->params.block_threads = 0;
+    h->params.ctas_per_sm = 0;
+    h->params.frames_per_cta = 0;
+    h->params.lanes_per_cn = 0;
+    h->batches.assign(batches, batches + n_batches);
+    ndgsbp_plan& o = h->plan;
+    std::memset(&o, 0, sizeof(o));
+    o.variant = NDGSBP_VARIANT_RAGGED_PER_CODE;
+    size_t ws = 0;
+    for (int i = 0; i < n_batches; ++i) {
+        const ndgsbp_batch& b = batches[i];
+        if (!b.groups || b.n_frames < 0 || (b.n_frames > 0 && (!b.d_llr || !b.d_hard_bits)))
+            return fail(NDGSBP_ERR_INVALID, "ragged_create: batch %d is incomplete", i);
+        ndgsbp_status st = NDGSBP_OK;
+        Plan* plan = plan_create(b.groups->g, &h->params, std::max<int64_t>(1, b.n_frames), &st);
+        if (!plan) return st;
+        h->plans.push_back(plan);
+        const ndgsbp_plan& pi = plan_info(*plan);
+        h->ws_off.push_back(ws);
+        ws += a256(static_cast<size_t>(std::max<int64_t>(pi.workspace_bytes, 256)));
+        o.block_threads = std::max(o.block_threads, pi.block_threads);
+        o.grid += pi.grid;
+        o.ctas_per_sm = std::max(o.ctas_per_sm, pi.ctas_per_sm);
+        o.max_row_degree = std::max(o.max_row_degree, pi.max_row_degree);
+        o.smem_bytes = std::max(o.smem_bytes, pi.smem_bytes);
+    }
+    o.workspace_bytes = static_cast<int64_t>(ws);
+    RAGGED_TRY(cudaMalloc(&h->workspace, ws));
+    for (int i = 0; i < n_batches; ++i) {
+        cudaEvent_t ev = nullptr;
+        RAGGED_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        h->events.push_back(ev);
+        if (i == 0) continue;
+        cudaStream_t st = nullptr;
+        RAGGED_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        h->streams.push_back(st);
+    }
+    h->n_tiles = n_batches;
+    *out = h.release();
+    return NDGSBP_OK;
+}
+
 extern "C" {
 
 ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batches, const ndgsbp_params* params,
@@ -59,8 +127,9 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         return fail(NDGSBP_ERR_INVALID, "ragged_create: need 1..%d batches", kTileMaxCodes);
     if (params->max_iter < 1 || !(params->llr_max > 0.f && params->llr_max <= 30.f))
         return fail(NDGSBP_ERR_INVALID, "ragged_create: bad max_iter or llr_max");
+    if (params->variant == NDGSBP_VARIANT_RAGGED_PER_CODE) return create_per_code(batches, n_batches, params, out);
     const int ms = params->msg_dtype == NDGSBP_F32 ? 4 : 2;
-    if (!pick_tile_kernel(params->msg_dtype, false, 8, false))
+    if (!pick_tile_kernel(params->msg_dtype, false, 8, false, false))
         return fail(NDGSBP_ERR_INVALID, "ragged_create: msg_dtype must be F32, F16 or BF16");
     int dev = 0, sms = 0, optin = 0, smem_sm = 0, reserved = 0;
     RAGGED_TRY(cudaGetDevice(&dev));
@@ -219,7 +288,7 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         lane_width = std::max(lane_width, tile_lane_width(cp[i].le));
         regb = regb && cp[i].slots * cp[i].per_slot <= threads;
     }
-    TileKernelFn fn = pick_tile_kernel(params->msg_dtype, false, lane_width, regb);
+    TileKernelFn fn = pick_tile_kernel(params->msg_dtype, false, lane_width, regb, n_batches == 1);
     if (!fn) {
         delete h;
         return fail(NDGSBP_ERR_UNSUPPORTED, "ragged_create: no kernel instance for lane width %d", lane_width);
@@ -297,6 +366,29 @@ ndgsbp_status ndgsbp_ragged_info(const ndgsbp_ragged* ragged, ndgsbp_plan* plan,
 }
 
 static ndgsbp_status enqueue(ndgsbp_ragged* h, cudaStream_t s) {
+    if (h->per_code) {
+        // fork: codes 1..n-1 on the handle's streams after everything before on s; join: s waits
+        // for all of them
+        const int n = static_cast<int>(h->plans.size());
+        RAGGED_TRY(cudaEventRecord(h->events[0], s));
+        for (int i = 0; i < n; ++i) {
+            cudaStream_t si = i == 0 ? s : h->streams[i - 1];
+            if (i > 0) RAGGED_TRY(cudaStreamWaitEvent(si, h->events[0], 0));
+            const ndgsbp_batch& b = h->batches[i];
+            ndgsbp_extras ex;
+            std::memset(&ex, 0, sizeof(ex));
+            ex.d_stats = b.d_stats;
+            ex.d_start_ns = b.d_start_ns;
+            ex.d_retire_ns = b.d_retire_ns;
+            ndgsbp_status st = plan_enqueue(b.groups->g, *h->plans[i], &h->params, b.d_llr, b.llr_dtype, b.n_frames,
+                                            static_cast<unsigned char*>(h->workspace) + h->ws_off[i], b.d_hard_bits,
+                                            b.d_iters, b.d_syndrome_ok, b.d_posterior, &ex, si);
+            if (st) return st;
+            if (i > 0) RAGGED_TRY(cudaEventRecord(h->events[i], si));
+        }
+        for (int i = 1; i < n; ++i) RAGGED_TRY(cudaStreamWaitEvent(s, h->events[i], 0));
+        return NDGSBP_OK;
+    }
     RAGGED_TRY(cudaMemsetAsync(h->workspace, 0, sizeof(unsigned long long), s));
     if (h->n_tiles > 0) h->fn<<<h->grid, h->threads, h->smem, s>>>(h->args);
     RAGGED_TRY(cudaGetLastError());

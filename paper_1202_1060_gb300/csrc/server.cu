@@ -370,7 +370,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         return fail(NDGSBP_ERR_INVALID, "server_create: need 1..%d codes, params and epoch_iters >= 1", kTileMaxCodes);
     if (params->max_iter < 1 || !(params->llr_max > 0.f && params->llr_max <= 30.f))
         return fail(NDGSBP_ERR_INVALID, "server_create: bad max_iter or llr_max");
-    if (!pick_tile_kernel(params->msg_dtype, /*serve=*/true, 8, false))
+    if (!pick_tile_kernel(params->msg_dtype, /*serve=*/true, 8, false, false))
         return fail(NDGSBP_ERR_INVALID, "server_create: msg_dtype must be F32, F16 or BF16");
     const int ms = params->msg_dtype == NDGSBP_F32 ? 4 : 2;
     std::unique_ptr<ndgsbp_server> h(new (std::nothrow) ndgsbp_server);
@@ -459,7 +459,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         lane_width = std::max(lane_width, tile_lane_width(p.le));
         regb = regb && p.cta_slots * p.Q->window * p.Q->Z * p.tpc <= threads;
     }
-    TileKernelFn fn = pick_tile_kernel(params->msg_dtype, /*serve=*/true, lane_width, regb);
+    TileKernelFn fn = pick_tile_kernel(params->msg_dtype, /*serve=*/true, lane_width, regb, false);
     if (!fn) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: no kernel instance for lane width %d", lane_width);
     cudaError_t e = cudaSuccess;
     auto dmalloc = [&](void** ptr, size_t bytes) {

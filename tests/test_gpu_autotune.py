@@ -82,16 +82,24 @@ def test_ragged_autotune(env):
     p, ms = nd.ragged_autotune(batches, p0, sample_frames=1024)
     shapes = [(b["frames_per_cta"], b["lanes_per_cn"]) for b in batches]
     print(f"\nragged tuned: threads {p.block_threads}, per-code (fpc, lanes) {shapes}, {ms:.3f} ms")
-    assert p.variant == nd.VARIANT_TILE and p.block_threads in (128, 256, 384, 512) and 1 <= p.ctas_per_sm <= 4
-    assert all(1 <= f <= 16 and l in (1, 2, 4) for f, l in shapes)
     assert ms > 0
-    # the tuned launch decodes each code as that code alone with the same shape
+    if p.variant == nd.VARIANT_RAGGED_PER_CODE:
+        # every code on its own default plan: the batches keep the library's shape choice
+        assert all(f == 0 and l == 0 for f, l in shapes)
+    else:
+        assert p.variant == nd.VARIANT_TILE and p.block_threads in (128, 256, 384, 512) and 1 <= p.ctas_per_sm <= 4
+        assert all(1 <= f <= 16 and l in (1, 2, 4) for f, l in shapes)
+    # the tuned launch decodes each code as that code alone with the same shape (per-code mode:
+    # with the default plan)
     rg = nd.Ragged(batches, p)
     rg.launch()
     torch.cuda.synchronize()
     for b in batches:
         q = nd.Params.from_buffer_copy(p)
-        q.frames_per_cta, q.lanes_per_cn = b["frames_per_cta"], b["lanes_per_cn"]
+        if p.variant == nd.VARIANT_RAGGED_PER_CODE:
+            q.variant = nd.VARIANT_AUTO
+        else:
+            q.frames_per_cta, q.lanes_per_cn = b["frames_per_cta"], b["lanes_per_cn"]
         h, i, o = _decode(nd, torch, b["groups"], b["c"], q, b["llr"])
         np.testing.assert_array_equal(b["hard_bits"].cpu().numpy(), h)
         np.testing.assert_array_equal(b["iters"].cpu().numpy(), i)

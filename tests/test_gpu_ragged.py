@@ -163,3 +163,89 @@ def test_ragged_empty_batch_and_residency_targets(env):
             assert torch.equal(b["hard_bits"], a[0]) and torch.equal(b["iters"], a[1]), (k, b["c"].name)
         ran += 1
     assert ran >= 2
+
+
+def _default_alone(nd, torch, b, params):
+    """The batch decoded alone by ndgsbp_decode with the library's default plan."""
+    F = b["llr"].shape[0]
+    p = nd.Params.from_buffer_copy(params)
+    p.variant = nd.VARIANT_AUTO
+    dev = b["llr"].device
+    hard = torch.zeros_like(b["hard_bits"])
+    iters = torch.zeros_like(b["iters"])
+    ok = torch.zeros_like(b["syndrome_ok"])
+    post = torch.zeros_like(b["posterior"])
+    ws = torch.zeros(max(256, b["groups"].workspace_size(p, F)), dtype=torch.uint8, device=dev)
+    nd.decode(b["groups"], p, b["llr"], ws, hard, iters, ok, post)
+    return hard, iters, ok, post
+
+
+@pytest.mark.parametrize("msg", ["f16", "f32"])
+def test_ragged_per_code_mode(env, msg):
+    """Per-code mode: every code on its own default plan, forked onto concurrent streams.  Each
+    batch's outputs and statistics equal those of the batch decoded alone; the graph replay
+    equals the plain launch, also after the inputs are refilled; an empty batch is skipped."""
+    nd, torch = env
+    params = nd.params_default(max_iter=25, msg_dtype=nd.F16 if msg == "f16" else nd.F32,
+                               variant=nd.VARIANT_RAGGED_PER_CODE)
+    batches = _setup(nd, torch, [300, 0, 150, 80], msg, seed=4)
+    rg = nd.Ragged(batches, params)
+    plan, n = rg.info()
+    assert plan["variant"] == nd.VARIANT_RAGGED_PER_CODE and n == len(batches)
+    rg.launch()
+    torch.cuda.synchronize()
+    for b in batches:
+        if b["llr"].shape[0] == 0:
+            continue
+        hard, iters, ok, post = _default_alone(nd, torch, b, params)
+        torch.cuda.synchronize()
+        assert torch.equal(hard, b["hard_bits"]) and torch.equal(iters, b["iters"]), b["c"].name
+        assert torch.equal(post, b["posterior"]) and torch.equal(ok, b["syndrome_ok"])
+        st = b["stats"].cpu().numpy()
+        assert st[nd.STAT_FRAMES] == b["llr"].shape[0]
+        assert st[nd.STAT_ITERATIONS] == int(b["iters"].sum())
+    first = [(b["hard_bits"].clone(), b["iters"].clone()) for b in batches]
+    for b in batches:
+        b["hard_bits"].zero_()
+        b["iters"].zero_()
+    rg.graph_launch()
+    rg.graph_launch()
+    torch.cuda.synchronize()
+    for b, (h, it) in zip(batches, first):
+        assert torch.equal(b["hard_bits"], h) and torch.equal(b["iters"], it)
+    for i, b in enumerate(batches):
+        c, F = b["c"], b["llr"].shape[0]
+        if F:
+            b["llr"].copy_(torch.from_numpy(I.channel_llr(c.N, F, MIX[i][1], I.design_rate(c), seed=900 + i,
+                                                          dtype=np.float32)))
+    rg.graph_launch()
+    torch.cuda.synchronize()
+    for b in batches:
+        if b["llr"].shape[0] == 0:
+            continue
+        hard, iters, _, _ = _default_alone(nd, torch, b, params)
+        torch.cuda.synchronize()
+        assert torch.equal(hard, b["hard_bits"]) and torch.equal(iters, b["iters"]), b["c"].name
+
+
+def test_ragged_autotune_considers_per_code(env):
+    """The ragged autotuner's winner is either a tile launch or the per-code mode, and the
+    launch it describes decodes every batch as the batch decoded alone would."""
+    nd, torch = env
+    params = nd.params_default(max_iter=20, msg_dtype=nd.F16)
+    batches = _setup(nd, torch, [400, 300, 200, 100], "f16", seed=5)
+    best, ms = nd.ragged_autotune(batches, params, sample_frames=64)
+    assert ms > 0 and best.variant in (nd.VARIANT_TILE, nd.VARIANT_RAGGED_PER_CODE)
+    rg = nd.Ragged(batches, best)
+    for b in batches:
+        b["hard_bits"].zero_()
+        b["iters"].zero_()
+    rg.launch()
+    torch.cuda.synchronize()
+    for b in batches:
+        if best.variant == nd.VARIANT_RAGGED_PER_CODE:
+            hard, iters, _, _ = _default_alone(nd, torch, b, best)
+        else:
+            hard, iters, _, _ = _alone(nd, torch, b, best, b["lanes_per_cn"])
+        torch.cuda.synchronize()
+        assert torch.equal(hard, b["hard_bits"]) and torch.equal(iters, b["iters"]), b["c"].name
