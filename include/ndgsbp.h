@@ -371,14 +371,17 @@ ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches,
  * directly) sized so that all pools fit hbm_budget_bytes (split in proportion to weights; NULL =
  * equal shares).  A staging thread of the library places the frames of queued
  * requests into free slots in arrival order (copying their LLRs while epochs run); a worker
- * thread runs epoch launches of the tile kernel in which
- * every running frame advances by at most epoch_iters iterations (its state stays in device
- * memory between epochs), and retires frames whose syndrome is zero (Step 4 b) or that reached
- * params->max_iter, freeing their slots for the next frames at once.  A request completes when
- * all its frames have retired.  Every frame is decoded exactly as by ndgsbp_decode with the
- * TILE variant, whatever else is in flight.
- * Errors: INVALID, BUDGET (a pool would get no slot), UNSUPPORTED (a code the tile kernel does
- * not take), CUDA, NOMEM. */
+ * thread runs epochs in which every running frame advances by at most epoch_iters iterations
+ * (its state stays in device memory between epochs), and retires frames whose syndrome is zero
+ * (Step 4 b) or that reached params->max_iter, freeing their slots for the next frames at once.
+ * A request completes when all its frames have retired.  An epoch is one serving launch of the
+ * layered QC kernel per pool whose plain decode would use that kernel (forked onto the pool's
+ * own stream) and one serving launch of the tile kernel over the other pools; with
+ * params->variant = NDGSBP_VARIANT_TILE every pool runs on the tile kernel.  Every frame is
+ * decoded exactly as by ndgsbp_decode with the same choice (variant AUTO, or TILE), whatever else
+ * is in flight.
+ * Errors: INVALID, BUDGET (a pool would get no slot), UNSUPPORTED (a code that is not QC in
+ * whole layers, or that the tile kernel does not take), CUDA, NOMEM. */
 typedef struct ndgsbp_server ndgsbp_server;
 
 typedef struct ndgsbp_server_stats {
@@ -391,6 +394,7 @@ typedef struct ndgsbp_server_stats {
     double admit_seconds;        /* staging-thread time copying admitted frames' LLRs (overlaps epochs) */
     double device_seconds;       /* host time from an epoch's first enqueue to its stream sync */
     double harvest_seconds;      /* host time copying retired frames' outputs to their requests */
+    int64_t launches;            /* kernels launched by the epochs (admit, QC and tile launches) */
 } ndgsbp_server_stats;
 
 ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_codes,

@@ -822,6 +822,38 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
     return NDGSBP_OK;
 }
 
+ndgsbp_status qc_serve_plan(const Groups& g, const ndgsbp_params* p, QcServePlan* out, bool* ok) {
+    *ok = false;
+    ndgsbp_status st = validate_params(p);
+    if (st) return st;
+    ndgsbp_params q = *p;
+    q.variant = NDGSBP_VARIANT_QC;
+    q.block_threads = 0;
+    q.ctas_per_sm = 0;
+    q.frames_per_cta = 0;
+    q.lanes_per_cn = 0;
+    DeviceInfo di;
+    st = device_info(di);
+    if (st) return st;
+    Plan plan;
+    bool qok = false;
+    st = make_qc_plan(g, &q, int64_t{1} << 30, /*flood=*/false, di, plan, &qok);
+    if (st || !qok || plan.qc_w2) return st;
+    const int maxdc = plan.pub.max_row_degree;
+    if (!qc_degrees_specialised(*plan.Q, maxdc)) return NDGSBP_OK;
+    QcKernelFn fn = pick_qc_serve_kernel(q.msg_dtype, maxdc, plan.msg_smem);
+    if (!fn) return NDGSBP_OK;
+    out->fn = fn;
+    out->threads = plan.pub.block_threads;
+    out->smem = static_cast<size_t>(plan.pub.smem_bytes);
+    out->msg_smem = plan.msg_smem;
+    out->msg_slots = plan.Q->msg_slots;
+    std::memset(&out->args, 0, sizeof(out->args));
+    fill_qc_args(out->args, *plan.Q, *plan.DQ, nullptr, false);
+    *ok = true;
+    return NDGSBP_OK;
+}
+
 Plan* plan_create(const Groups& g, const ndgsbp_params* p, int64_t n_frames, ndgsbp_status* st) {
     Plan* plan = new (std::nothrow) Plan;
     if (!plan) {

@@ -21,328 +21,9 @@
 // (MAXDC/2, MAXDC] (the usual QC case); other codes use the degree-generic instances.
 #include <cstring>
 
-#include "decode_qc.h"
-#include "qc_device.cuh"
+#include "qc_kernel.cuh"
 
 namespace ndgsbp {
-
-
-// ---- single-CN kernel ---------------------------------------------------------------------
-template <int D, int MAXDC, typename MsgT>
-__device__ __forceinline__ void qc_phase_a(const int2* __restrict__ et, int c, int c4, int Z4, float* __restrict__ P,
-                                           MsgT* __restrict__ m, float lim, int (&vb)[MAXDC], float (&dl)[MAXDC]) {
-    static_assert(D <= MAXDC, "degree above the bound");
-    float t[D], old[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        vb[k] = qc_vb(et[k], c, c4, Z4);
-        old[k] = to_f(m[k]);
-        t[k] = at_byte(P, vb[k]) - old[k];
-    }
-    check_node_update<D>(t, D, lim, [&](int k, float val) {
-        const MsgT q = from_f<MsgT>(val);
-        m[k] = q;
-        dl[k] = to_f(q) - old[k];
-    });
-}
-
-// Phase A for a window of 2 layers, with the write-back of every edge whose block column the
-// other layer of the window does not touch done at once: that VN is read by this CN alone in
-// this group, so P_n + change is final.  Of an edge in a shared block column, position 0
-// leaves its change in dx for the position-1 CN on the same VN, which adds both in phase B in
-// position order ((P + change_0) + change_1, the order of the two-round write-back), so results
-// do not change.
-template <int D, int MAXDC, typename MsgT, bool POS1>
-__device__ __forceinline__ void qc_phase_a_w2(const int2* __restrict__ et, unsigned shared, int c, int c4,
-                                              int Z4, float* __restrict__ P, MsgT* __restrict__ m,
-                                              float* __restrict__ dxc, float lim, int (&vb)[MAXDC],
-                                              float (&dl)[MAXDC]) {
-    static_assert(D <= MAXDC, "degree above the bound");
-    float t[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        vb[k] = qc_vb(et[k], c, c4, Z4);
-        t[k] = at_byte(P, vb[k]) - to_f(m[k]);
-    }
-    // the old message is read again from m[k] instead of held in a register (this path keeps
-    // more values live than the two-round one)
-    check_node_update<D>(t, D, lim, [&](int k, float val) {
-        const MsgT q = from_f<MsgT>(val);
-        const float d = to_f(q) - to_f(m[k]);
-        m[k] = q;
-        if ((shared >> k) & 1u) {
-            if (POS1)
-                dl[k] = d;
-            else
-                dxc[k] = d;
-        } else {
-            at_byte(P, vb[k]) += d;
-        }
-    });
-}
-
-// Phase B of a 2-layer window: position-1 CN c adds, on each shared VN, the position-0 change
-// (from dx) and then its own (kept in dl).  w2 (global memory, read through L1) gives, per
-// shared edge k, the position-0 edge k0 on the same block column and the CN offset s_1 - s_0.
-template <int D, int MAXDC>
-__device__ __forceinline__ void qc_phase_b_w2(const int2* __restrict__ et, const int2* __restrict__ w2, unsigned shared,
-                                              int c, int c4, int Z, int Z4, int dxs, float* __restrict__ P,
-                                              const float* __restrict__ dx, const float (&dl)[MAXDC]) {
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if ((shared >> k) & 1u) {
-            const int2 e = __ldg(w2 + k);
-            int c0 = c + e.y;
-            c0 -= c0 >= Z ? Z : 0;
-            float& p = at_byte(P, qc_vb(et[k], c, c4, Z4));
-            p = (p + dx[c0 * dxs + e.x]) + dl[k];
-        }
-    }
-}
-
-template <int MAXDC, typename MsgT>
-__device__ __forceinline__ void qc_phase_a_any(const int2* __restrict__ et, int c, int c4, int Z4, int d,
-                                               float* __restrict__ P, MsgT* __restrict__ m, float lim,
-                                               int (&vb)[MAXDC], float (&dl)[MAXDC]) {
-    float t[MAXDC], old[MAXDC];
-#pragma unroll
-    for (int k = 0; k < MAXDC; ++k) {
-        if (k < d) {
-            vb[k] = qc_vb(et[k], c, c4, Z4);
-            old[k] = to_f(m[k]);
-            t[k] = at_byte(P, vb[k]) - old[k];
-        }
-    }
-    check_node_update<MAXDC>(t, d, lim, [&](int k, float val) {
-        const MsgT q = from_f<MsgT>(val);
-        m[k] = q;
-        dl[k] = to_f(q) - old[k];
-    });
-}
-
-template <int D, int MAXDC>
-__device__ __forceinline__ void qc_phase_b(float* __restrict__ P, const int (&vb)[MAXDC], const float (&dl)[MAXDC]) {
-#pragma unroll
-    for (int k = 0; k < D; ++k) at_byte(P, vb[k]) += dl[k];
-}
-
-template <int D>
-__device__ __forceinline__ unsigned qc_parity(const int2* __restrict__ et, int c, int c4, int Z4, float* __restrict__ P) {
-    unsigned p = 0u;
-#pragma unroll
-    for (int k = 0; k < D; ++k) p ^= (at_byte(P, qc_vb(et[k], c, c4, Z4)) < 0.f) ? 1u : 0u;
-    return p;
-}
-
-
-// Shared-memory tables of a QC launch (loaded once per CTA).
-struct QcSmem {
-    float* P;
-    unsigned char* msg;   // used when messages are in shared memory
-    int2* tab;
-    int* ldeg;
-    int* lstride;
-    int* loff;
-    int* glay;
-    unsigned* w2mask;   // [G][2] bit k: edge k of that window position is on a shared block column
-    float* dx;   // [Z][dxs] position-0 changes on shared block columns
-    int dxs;     // odd stride >= maxdeg
-};
-
-template <typename MsgT, bool MSG_SMEM>
-__device__ __forceinline__ QcSmem qc_smem_layout(unsigned char* smem, const QcArgs& a) {
-    QcSmem s;
-    const RunArgs& r = a.r;
-    s.P = reinterpret_cast<float*>(smem);
-    size_t off = (static_cast<size_t>(r.N) * 4 + 15) & ~static_cast<size_t>(15);
-    s.msg = smem + off;
-    if (MSG_SMEM) off += (static_cast<size_t>(a.msg_slots) * sizeof(MsgT) + 15) & ~static_cast<size_t>(15);
-    s.tab = reinterpret_cast<int2*>(smem + off);
-    off += (static_cast<size_t>(a.nl) * a.maxdeg * 8 + 15) & ~static_cast<size_t>(15);
-    s.ldeg = reinterpret_cast<int*>(smem + off);
-    off += (static_cast<size_t>(a.nl) * 4 + 15) & ~static_cast<size_t>(15);
-    s.lstride = reinterpret_cast<int*>(smem + off);
-    off += (static_cast<size_t>(a.nl) * 4 + 15) & ~static_cast<size_t>(15);
-    s.loff = reinterpret_cast<int*>(smem + off);
-    off += (static_cast<size_t>(a.nl) * 4 + 15) & ~static_cast<size_t>(15);
-    s.glay = reinterpret_cast<int*>(smem + off);
-    off += (static_cast<size_t>(a.G) * a.window * 4 + 15) & ~static_cast<size_t>(15);
-    s.dxs = a.maxdeg | 1;
-    s.w2mask = reinterpret_cast<unsigned*>(smem + off);
-    if (a.win2) off += (static_cast<size_t>(a.G) * 2 * 4 + 15) & ~static_cast<size_t>(15);
-    s.dx = reinterpret_cast<float*>(smem + off);
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (a.win2) {
-        for (int i = tid; i < a.G * 2; i += nt) {
-            unsigned mk = 0u;
-            for (int k = 0; k < a.maxdeg; ++k) {
-                const int x = a.win2[i * a.maxdeg + k].x;
-                mk |= ((i & 1) ? x >= 0 : x != 0) ? 1u << k : 0u;
-            }
-            s.w2mask[i] = mk;
-        }
-    }
-    for (int i = tid; i < a.nl * a.maxdeg; i += nt) s.tab[i] = a.edge_tab[i];
-    for (int i = tid; i < a.nl; i += nt) {
-        s.ldeg[i] = a.layer_deg[i];
-        s.lstride[i] = a.layer_stride[i];
-        s.loff[i] = a.layer_off[i];
-    }
-    for (int i = tid; i < a.G * a.window * a.n_groupings; i += nt) s.glay[i] = a.group_layers[i];
-    return s;
-}
-
-template <typename MsgT>
-__device__ __forceinline__ void qc_frame_begin(const QcArgs& a, const QcSmem& s, MsgT* msg, long long f) {
-    const RunArgs& r = a.r;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (r.start_ns && tid == 0) r.start_ns[f] = global_timer_ns();
-    for (int n = tid; n < r.N; n += nt) s.P[n] = load_llr(r.llr, r.llr_dtype, f * r.N + n);
-    for (int e = tid; e < a.msg_slots; e += nt) msg[e] = from_f<MsgT>(0.f);
-}
-
-template <typename MsgT>
-__device__ __forceinline__ void qc_frame_messages_out(const QcArgs& a, const MsgT* msg, long long f) {
-    const RunArgs& r = a.r;
-    if (!r.msgs_out) return;
-    for (int e = threadIdx.x; e < a.msg_slots; e += blockDim.x) {
-        const int csr = __ldg(a.csr_of + e);
-        if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]);
-    }
-}
-
-// OCC > 0: an instance for blocks of at most kOccThreads threads compiled for OCC resident CTAs
-// per SM (fewer registers), for launches whose shared memory allows that many.
-constexpr int kOccThreads = 192;
-
-template <typename MsgT, bool MSG_SMEM, int MAXDC, bool SPEC, bool W2, int OCC = 0>
-__global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OCC ? OCC : 1)
-    qc_decode_kernel(const QcArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_frame;
-    __shared__ unsigned s_err;
-    const RunArgs& r = a.r;
-    const int tid = threadIdx.x;
-    const int Z = a.Z, W = a.window, nl = a.nl, md = a.maxdeg, Z4 = 4 * a.Z;
-    const QcSmem s = qc_smem_layout<MsgT, MSG_SMEM>(smem, a);
-    float* P = s.P;
-    MsgT* msg = MSG_SMEM ? reinterpret_cast<MsgT*>(s.msg)
-                         : static_cast<MsgT*>(a.ws_msgs) + static_cast<size_t>(blockIdx.x) * a.msg_slots;
-    const int j = tid / Z;
-    const int c = tid - j * Z, c4 = 4 * c;
-    const bool active = j < W;
-    const float lim = r.llr_max;
-    if (tid == 0) s_err = 0u;
-    for (;;) {
-        const long long f = next_frame(r, &s_frame);   // barrier: also orders the table loads
-        if (f >= r.n_frames) break;
-        qc_frame_begin(a, s, msg, f);
-        __syncthreads();
-        int it = 1, unsat = 1;
-        for (;; ++it) {
-            const int* gl = s.glay + ((it - 1) % a.n_groupings) * a.G * W;   // this iteration's grouping
-            for (int g = 0; g < a.G; ++g) {
-                float dl[MAXDC];
-                int vb[MAXDC];
-                int d = 0;
-                if constexpr (SPEC && W2) {
-                    // 2-layer window: direct write-back off the shared block columns, one
-                    // ordered round on them
-                    if (active) {
-                        const int l = gl[g * W + j];
-                        d = s.ldeg[l];
-                        const int2* et = s.tab + l * md;
-                        MsgT* m = msg + s.loff[l] + c * s.lstride[l];
-                        const unsigned mk = s.w2mask[g * 2 + j];
-                        float* dxc = s.dx + c * s.dxs;
-                        if (j == 0) {
-#define NDGSBP_CASE_W0(D) \
-    if (d == D) qc_phase_a_w2<NDGSBP_DD(D), MAXDC, MsgT, false>(et, mk, c, c4, Z4, P, m, dxc, lim, vb, dl);
-                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_W0)
-#undef NDGSBP_CASE_W0
-                        } else {
-#define NDGSBP_CASE_W1(D) \
-    if (d == D) qc_phase_a_w2<NDGSBP_DD(D), MAXDC, MsgT, true>(et, mk, c, c4, Z4, P, m, dxc, lim, vb, dl);
-                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_W1)
-#undef NDGSBP_CASE_W1
-                        }
-                    }
-                    __syncthreads();
-                    if (active && j == 1) {
-                        const int l = gl[g * W + 1];
-                        const int2* et = s.tab + l * md;
-                        const int2* w2 = a.win2 + (g * 2 + 1) * md;
-                        const unsigned mk = s.w2mask[g * 2 + 1];
-#define NDGSBP_CASE_WB(D) \
-    if (d == D) qc_phase_b_w2<NDGSBP_DD(D), MAXDC>(et, w2, mk, c, c4, Z, Z4, s.dxs, P, s.dx, dl);
-                        NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_WB)
-#undef NDGSBP_CASE_WB
-                    }
-                    __syncthreads();
-                    continue;
-                }
-                if (active) {
-                    const int l = gl[g * W + j];
-                    d = s.ldeg[l];
-                    const int2* et = s.tab + l * md;
-                    MsgT* m = msg + s.loff[l] + c * s.lstride[l];
-                    if constexpr (SPEC) {
-#define NDGSBP_CASE_A(D) \
-    if (d == D) qc_phase_a<NDGSBP_DD(D), MAXDC, MsgT>(et, c, c4, Z4, P, m, lim, vb, dl);
-                        NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_A)
-#undef NDGSBP_CASE_A
-                    } else {
-                        qc_phase_a_any<MAXDC, MsgT>(et, c, c4, Z4, d, P, m, lim, vb, dl);
-                    }
-                }
-                __syncthreads();
-                for (int jj = 0; jj < W; ++jj) {
-                    if (active && j == jj) {
-                        if constexpr (SPEC) {
-#define NDGSBP_CASE_B(D) \
-    if (d == D) qc_phase_b<NDGSBP_DD(D), MAXDC>(P, vb, dl);
-                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_B)
-#undef NDGSBP_CASE_B
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < MAXDC; ++k)
-                                if (k < d) at_byte(P, vb[k]) += dl[k];
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            const bool last = it >= r.max_iter;
-            if (r.early_stop || last) {
-                unsigned bad = 0u;
-                if (active) {
-                    for (int l = j; l < nl; l += W) {
-                        const int d = s.ldeg[l];
-                        const int2* et = s.tab + l * md;
-                        unsigned p = 0u;
-                        if constexpr (SPEC) {
-#define NDGSBP_CASE_S(D) \
-    if (d == D) p = qc_parity<NDGSBP_DD(D)>(et, c, c4, Z4, P);
-                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_S)
-#undef NDGSBP_CASE_S
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < MAXDC; ++k)
-                                if (k < d) p ^= (at_byte(P, qc_vb(et[k], c, c4, Z4)) < 0.f) ? 1u : 0u;
-                        }
-                        bad |= p;
-                    }
-                }
-                unsat = __syncthreads_or(bad);
-                if (!unsat && r.early_stop) break;
-            }
-            if (last) break;
-        }
-        qc_frame_messages_out(a, msg, f);
-        write_frame_outputs(r, P, f, it, unsat, &s_err);
-        __syncthreads();
-    }
-}
 
 // ---- pair kernel --------------------------------------------------------------------------
 

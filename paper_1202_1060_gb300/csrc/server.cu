@@ -9,15 +9,18 @@
 //      arrival order, take free slots of their code's pool and have their LLRs copied to the
 //      slots' staging, concurrently with the epochs) are listed for a small admit kernel that
 //      marks their slots new;
-//   2. run: one launch of the tile kernel in serving mode over the tiles of occupied slots of
-//      every pool; each running frame advances by at most epoch_iters iterations, then retires
+//   2. run: per pool whose code the layered QC kernel decodes (the plain decode's choice), one
+//      serving launch of that kernel over the pool's running slots, on the pool's own stream;
+//      for the other pools, one launch of the tile kernel in serving mode over the tiles of
+//      their occupied slots; all launches of the epoch run concurrently and join before the
+//      harvest.  Each running frame advances by at most epoch_iters iterations, then retires
 //      (zero syndrome or max_iter: outputs written, slot listed as done) or is parked with its
 //      state in device memory;
 //   3. harvest: the done lists come back (a count per pool); retired frames free their slots
 //      and their outputs are copied into their requests' buffers; a request completes when all
 //      its frames have retired.
 // Frames of different requests and codes share every launch, and new requests join as soon as
-// slots free up.  Each frame is computed exactly as by the tile kernel in a plain decode.
+// slots free up.  Each frame is computed exactly as by its pool's kernel in a plain decode.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -32,6 +35,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "decode_qc.h"
 #include "decode_tile.h"
 #include "ndgsbp_internal.h"
 
@@ -95,6 +99,15 @@ struct Pool {
     std::vector<std::pair<Request*, int64_t>> owner;   // frame held by each slot (staged or running)
     std::vector<uint8_t> running;   // the slot's frame has been launched
     std::vector<int> ready;         // staged slots waiting for the next epoch
+    // QC pools: advanced by the serving instance of the layered QC kernel (one launch per epoch
+    // over the listed running slots, on the pool's own stream); the others by the tile launch
+    bool qc = false;
+    QcServePlan qp;
+    QcArgs qargs{};
+    int qc_grid = 1, n_list = 0;
+    int* h_list = nullptr;          // pinned, mapped: this epoch's running slots
+    cudaStream_t qstream = nullptr;
+    cudaEvent_t qdone = nullptr;    // the pool's launch of this epoch has completed (join)
 };
 
 constexpr int kStageBatch = 512;   // frames the staging thread places per lock hold
@@ -122,8 +135,9 @@ struct ndgsbp_server {
     int* h_admit = nullptr;
     int* d_done_count = nullptr;
     int* h_done_count = nullptr;
-    unsigned long long* d_counter = nullptr;
+    unsigned long long* d_counter = nullptr;   // [0] the tile launch, [1 + i] QC pool i
     cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr;     // QC pool launches start after the epoch's admission
     std::mutex mu;
     std::condition_variable cv_work, cv_done, cv_stage;
     std::deque<Request*> queue;
@@ -162,6 +176,9 @@ ndgsbp_server::~ndgsbp_server() {
     if (cudaGetDevice(&cur) == cudaSuccess && cudaSetDevice(device) == cudaSuccess) {
         if (stream) cudaStreamSynchronize(stream);
         for (Pool& p : pools) {
+            if (p.qstream) cudaStreamDestroy(p.qstream);
+            if (p.qdone) cudaEventDestroy(p.qdone);
+            cudaFreeHost(p.h_list);
             cudaFree(p.flag);
             cudaFree(p.st_iter);
             cudaFree(p.st_P);
@@ -179,6 +196,7 @@ ndgsbp_server::~ndgsbp_server() {
         cudaFree(d_done_count);
         cudaFreeHost(h_done_count);
         cudaFree(d_counter);
+        if (fork) cudaEventDestroy(fork);
         if (stream) cudaStreamDestroy(stream);
         cudaSetDevice(cur);
     }
@@ -213,10 +231,16 @@ bool ndgsbp_server::epoch() {
             p.ready.clear();
         }
         n_ready = 0;
-        // tiles over the running slots of every pool: ranges holding up to tile_frames running
-        // slots (other slots inside a range are skipped by the kernel)
+        // QC pools: the list of running slots; tile pools: tiles over the running slots, ranges
+        // holding up to tile_frames running slots (other slots inside a range are skipped)
         for (int i = 0; i < static_cast<int>(pools.size()); ++i) {
-            const Pool& p = pools[i];
+            Pool& p = pools[i];
+            if (p.qc) {
+                p.n_list = 0;
+                for (int slot = 0; slot < p.slots; ++slot)
+                    if (p.running[slot]) p.h_list[p.n_list++] = slot;
+                continue;
+            }
             int first = -1, count = 0, last = -1;
             for (int slot = 0; slot < p.slots; ++slot) {
                 if (!p.running[slot]) continue;
@@ -232,7 +256,9 @@ bool ndgsbp_server::epoch() {
         }
     }
     const auto t1 = Clock::now();
-    if (n_tiles == 0) return true;
+    int n_qc = 0, n_launches = 0;
+    for (const Pool& p : pools) n_qc += p.qc ? p.n_list : 0;
+    if (n_tiles == 0 && n_qc == 0) return true;
     // 2. admit, then one serving launch over the occupied tiles
     if (n_admit) {
         SRV_CUDA(cudaMemcpyAsync(d_admit, h_admit, sizeof(int) * n_admit, cudaMemcpyHostToDevice, stream));
@@ -242,14 +268,32 @@ bool ndgsbp_server::epoch() {
         aa.n = n_admit;
         admit_kernel<<<std::min(1024, (n_admit + 255) / 256), 256, 0, stream>>>(aa);
         SRV_CUDA(cudaGetLastError());
+        ++n_launches;
     }
-    SRV_CUDA(cudaMemcpyAsync(d_tiles, h_tiles, sizeof(int4) * n_tiles, cudaMemcpyHostToDevice, stream));
     SRV_CUDA(cudaMemsetAsync(d_done_count, 0, sizeof(int) * pools.size(), stream));
-    SRV_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), stream));
-    TileArgs a = args;
-    a.n_tiles = n_tiles;
-    fn<<<std::min(max_grid, n_tiles), threads, smem, stream>>>(a);
-    SRV_CUDA(cudaGetLastError());
+    SRV_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long) * (1 + pools.size()), stream));
+    // fork: each QC pool's launch on its own stream, concurrent with the tile launch
+    SRV_CUDA(cudaEventRecord(fork, stream));
+    for (Pool& p : pools) {
+        if (!p.qc || p.n_list == 0) continue;
+        SRV_CUDA(cudaStreamWaitEvent(p.qstream, fork, 0));
+        QcArgs qa = p.qargs;
+        qa.r.n_frames = p.n_list;
+        p.qp.fn<<<std::min(p.qc_grid, p.n_list), p.qp.threads, p.qp.smem, p.qstream>>>(qa);
+        SRV_CUDA(cudaGetLastError());
+        ++n_launches;
+        SRV_CUDA(cudaEventRecord(p.qdone, p.qstream));
+    }
+    if (n_tiles > 0) {
+        SRV_CUDA(cudaMemcpyAsync(d_tiles, h_tiles, sizeof(int4) * n_tiles, cudaMemcpyHostToDevice, stream));
+        TileArgs a = args;
+        a.n_tiles = n_tiles;
+        fn<<<std::min(max_grid, n_tiles), threads, smem, stream>>>(a);
+        SRV_CUDA(cudaGetLastError());
+        ++n_launches;
+    }
+    for (Pool& p : pools)
+        if (p.qc && p.n_list > 0) SRV_CUDA(cudaStreamWaitEvent(stream, p.qdone, 0));
     SRV_CUDA(cudaMemcpyAsync(h_done_count, d_done_count, sizeof(int) * pools.size(), cudaMemcpyDeviceToHost, stream));
     SRV_CUDA(cudaStreamSynchronize(stream));
     const auto t2 = Clock::now();
@@ -288,6 +332,7 @@ bool ndgsbp_server::epoch() {
             stats.requests_completed += 1;
         }
         stats.epochs += 1;
+        stats.launches += n_launches;
         stats.device_seconds += std::chrono::duration<double>(t2 - t1).count();
         stats.harvest_seconds += std::chrono::duration<double>(t3 - t2).count();
         stats.busy_seconds += std::chrono::duration<double>(t3 - t0).count();
@@ -392,6 +437,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     if (!(wsum > 0.0)) return fail(NDGSBP_ERR_INVALID, "server_create: weights sum to zero");
     size_t table_max = 0;
     int threads = params->block_threads;
+    int n_tile_pools = 0;
     for (int i = 0; i < n_codes; ++i) {
         Pool& p = h->pools[i];
         if (!codes[i]) return fail(NDGSBP_ERR_INVALID, "server_create: code %d is null", i);
@@ -399,6 +445,13 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         if (!p.g->qc.ok) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d is not QC grouped in whole layers", i);
         ndgsbp_status st = device_qc_tables(*p.g, p.Q, p.D);
         if (st) return st;
+        // the QC kernel where the grouping's plain decode would use it (unless TILE is asked for)
+        if (params->variant != NDGSBP_VARIANT_TILE) {
+            bool ok = false;
+            st = qc_serve_plan(*p.g, params, &p.qp, &ok);
+            if (st) return st;
+            p.qc = ok;
+        }
         p.tpc = tile_lanes_per_cn(p.Q->max_deg);
         if (!p.tpc) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d has row degree above 32", i);
         p.le = (p.Q->max_deg + p.tpc - 1) / p.tpc;
@@ -411,11 +464,16 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         p.p_bytes = a16(static_cast<size_t>(p.N) * 4);
         p.m_bytes = a16(static_cast<size_t>(p.msg_slots) * ms);
         p.d_bytes = a16(static_cast<size_t>(shp.delta_floats) * 4);
+        if (p.qc) {
+            p.msg_slots = p.qp.msg_slots;
+            continue;
+        }
+        ++n_tile_pools;
         table_max = std::max(table_max, tile_table_bytes(*p.Q));
         if (!params->block_threads)
             threads = std::max(threads, std::min(512, std::max(128, (p.Q->window * p.Q->Z * p.tpc + 31) / 32 * 32)));
     }
-    if (threads <= 0 || threads > 1024 || threads % 32)
+    if (n_tile_pools > 0 && (threads <= 0 || threads > 1024 || threads % 32))
         return fail(NDGSBP_ERR_INVALID, "server_create: block_threads must be a multiple of 32 up to 1024");
     // Shared memory per CTA under a residency target of k CTAs per SM (as for ragged launches):
     // a code whose messages do not fit under the cap works on them in device memory, where a
@@ -426,7 +484,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     };
     auto fits = [&](size_t cap) {
         for (const Pool& p : h->pools)
-            if (table_max + p.p_bytes + p.d_bytes > cap) return false;
+            if (!p.qc && table_max + p.p_bytes + p.d_bytes > cap) return false;
         return true;
     };
     const int target = params->ctas_per_sm > 0 ? params->ctas_per_sm : (fits(cap_for(2)) ? 2 : 1);
@@ -434,15 +492,17 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     size_t smem = table_max;
     for (int i = 0; i < n_codes; ++i) {
         Pool& p = h->pools[i];
-        if (table_max + p.p_bytes + p.m_bytes + p.d_bytes > budget) p.m_bytes = 0;
-        p.slot_bytes = p.p_bytes + p.m_bytes + p.d_bytes;
-        if (table_max + p.slot_bytes > budget)
-            return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d does not fit at %d CTAs per SM", i, target);
-        const int per_slot = p.Q->window * p.Q->Z * p.tpc;
-        p.cta_slots = std::max(1, std::min<int>({16, std::max(1, threads / per_slot),
-                                                 static_cast<int>((budget - table_max) / p.slot_bytes)}));
-        p.tile_frames = 2 * p.cta_slots;
-        smem = std::max(smem, table_max + p.cta_slots * p.slot_bytes);
+        if (!p.qc) {
+            if (table_max + p.p_bytes + p.m_bytes + p.d_bytes > budget) p.m_bytes = 0;
+            p.slot_bytes = p.p_bytes + p.m_bytes + p.d_bytes;
+            if (table_max + p.slot_bytes > budget)
+                return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d does not fit at %d CTAs per SM", i, target);
+            const int per_slot = p.Q->window * p.Q->Z * p.tpc;
+            p.cta_slots = std::max(1, std::min<int>({16, std::max(1, threads / per_slot),
+                                                     static_cast<int>((budget - table_max) / p.slot_bytes)}));
+            p.tile_frames = 2 * p.cta_slots;
+            smem = std::max(smem, table_max + p.cta_slots * p.slot_bytes);
+        }
         // pool size from the budget share: posterior and messages of a running frame, LLR
         // staging, outputs and status per slot
         const double share = (weights ? std::max(0.0, weights[i]) : 1.0) / wsum;
@@ -456,11 +516,15 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     bool regb = true;
     for (int i = 0; i < n_codes; ++i) {
         const Pool& p = h->pools[i];
+        if (p.qc) continue;
         lane_width = std::max(lane_width, tile_lane_width(p.le));
         regb = regb && p.cta_slots * p.Q->window * p.Q->Z * p.tpc <= threads;
     }
-    TileKernelFn fn = pick_tile_kernel(params->msg_dtype, /*serve=*/true, lane_width, regb, false);
-    if (!fn) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: no kernel instance for lane width %d", lane_width);
+    TileKernelFn fn = nullptr;
+    if (n_tile_pools > 0) {
+        fn = pick_tile_kernel(params->msg_dtype, /*serve=*/true, lane_width, regb, false);
+        if (!fn) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: no kernel instance for lane width %d", lane_width);
+    }
     cudaError_t e = cudaSuccess;
     auto dmalloc = [&](void** ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
@@ -482,11 +546,16 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         hmalloc(reinterpret_cast<void**>(&p.h_iters), sizeof(int32_t) * p.slots);
         hmalloc(reinterpret_cast<void**>(&p.h_ok), p.slots);
         hmalloc(reinterpret_cast<void**>(&p.h_done), sizeof(int) * p.slots);
+        if (p.qc) {
+            hmalloc(reinterpret_cast<void**>(&p.h_list), sizeof(int) * p.slots);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p.qstream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.qdone, cudaEventDisableTiming);
+        }
         if (e != cudaSuccess) return fail(NDGSBP_ERR_NOMEM, "server_create: %s", cudaGetErrorString(e));
         p.owner.assign(p.slots, {nullptr, 0});
         p.running.assign(p.slots, 0);
         for (int s = p.slots - 1; s >= 0; --s) p.free_slots.push_back(s);
-        max_tiles += (p.slots + p.tile_frames - 1) / p.tile_frames;
+        if (!p.qc) max_tiles += (p.slots + p.tile_frames - 1) / p.tile_frames;
         h->stats.slots_total += p.slots;
     }
     dmalloc(reinterpret_cast<void**>(&h->d_tiles), sizeof(int4) * max_tiles);
@@ -497,15 +566,31 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     hmalloc(reinterpret_cast<void**>(&h->h_done_count), sizeof(int) * kTileMaxCodes);
     dmalloc(reinterpret_cast<void**>(&h->d_counter), 256);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem));
-    int per_sm = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), threads, smem);
-    if (e != cudaSuccess) return fail(NDGSBP_ERR_CUDA, "server_create: %s", cudaGetErrorString(e));
-    if (per_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: the launch does not fit on an SM");
-    per_sm = std::min(per_sm, target);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+    int per_sm = 1;
+    if (fn) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem));
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), threads, smem);
+        if (e != cudaSuccess) return fail(NDGSBP_ERR_CUDA, "server_create: %s", cudaGetErrorString(e));
+        if (per_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: the launch does not fit on an SM");
+        per_sm = std::min(per_sm, target);
+    }
+    for (Pool& p : h->pools) {
+        if (!p.qc) continue;
+        int q_sm = 0;
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(reinterpret_cast<const void*>(p.qp.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(p.qp.smem));
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_sm, reinterpret_cast<const void*>(p.qp.fn),
+                                                              p.qp.threads, p.qp.smem);
+        if (e != cudaSuccess) return fail(NDGSBP_ERR_CUDA, "server_create: %s", cudaGetErrorString(e));
+        if (q_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: a QC launch does not fit on an SM");
+        p.qc_grid = q_sm * sms;
+    }
     for (int i = 0; i < n_codes; ++i) {
         Pool& p = h->pools[i];
         TileCode& C = h->args.codes[i];
@@ -555,6 +640,21 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         r.synd_ok = device_view(p.h_ok);
         if (!C.done_list || !r.llr || !r.hard_bits || !r.iters || !r.synd_ok)
             return fail(NDGSBP_ERR_CUDA, "server_create: cannot map host buffers into the device");
+        if (p.qc) {
+            QcArgs& q = p.qargs;
+            q = p.qp.args;
+            q.r = r;
+            q.r.counter = h->d_counter + 1 + i;
+            q.serve_list = device_view(p.h_list);
+            q.state_flag = p.flag;
+            q.state_iter = p.st_iter;
+            q.state_P = p.st_P;
+            q.state_msgs = p.st_msgs;
+            q.epoch_iters = epoch_iters;
+            q.done_list = C.done_list;
+            q.done_count = C.done_count;
+            if (!q.serve_list) return fail(NDGSBP_ERR_CUDA, "server_create: cannot map host buffers into the device");
+        }
     }
     h->args.n_codes = n_codes;
     h->args.tiles = h->d_tiles;

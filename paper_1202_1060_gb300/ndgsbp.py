@@ -86,7 +86,7 @@ class ServerStats(ctypes.Structure):
                 ("epochs", ctypes.c_int64), ("iterations", ctypes.c_int64), ("busy_seconds", ctypes.c_double),
                 ("slots_total", ctypes.c_int64), ("slots_in_use", ctypes.c_int64),
                 ("admit_seconds", ctypes.c_double), ("device_seconds", ctypes.c_double),
-                ("harvest_seconds", ctypes.c_double)]
+                ("harvest_seconds", ctypes.c_double), ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1,9 +1,11 @@
 """Serving (continuous batching) through the C ABI server (needs a GB300).
 
 Every frame a server decodes must come out exactly as when its batch is decoded alone by the
-TILE variant: same hard decisions, iteration counts and syndrome flags, bit for bit, whatever
-else is in flight, however many slots the budget gives, and however the decoding is cut into
-epochs (its state stays in device memory between launches).
+kernel its pool runs on: the layered QC kernel for codes whose plain decode uses it (the
+default), the TILE kernel for the others or when the server is created with variant TILE.  Same
+hard decisions, iteration counts and syndrome flags, bit for bit, whatever else is in flight,
+however many slots the budget gives, and however the decoding is cut into epochs (its state
+stays in device memory between launches).
 """
 import numpy as np
 import pytest
@@ -32,10 +34,11 @@ def _grouped(nd, name):
 
 
 def _alone(nd, torch, g, c, llr, params):
-    """The batch decoded alone by the TILE variant."""
+    """The batch decoded alone by the kernel a server with these params uses for the code: the
+    plain decode's own choice (variant AUTO), or TILE when the server runs everything on it."""
     dev = torch.device("cuda")
     p = nd.params_default(**{f: getattr(params, f) for f, _ in params._fields_})
-    p.variant = nd.VARIANT_TILE
+    p.variant = nd.VARIANT_TILE if params.variant == nd.VARIANT_TILE else nd.VARIANT_AUTO
     F = llr.shape[0]
     d_llr = torch.from_numpy(np.ascontiguousarray(llr, np.float32)).to(dev)
     hard = torch.zeros((F, (c.N + 31) // 32), dtype=torch.int32, device=dev)
@@ -59,13 +62,15 @@ def _requests(codes, sizes, ebn0, seed):
 
 @pytest.mark.parametrize("msg", ["f32", "f16"])
 @pytest.mark.parametrize("epoch_iters,budget_mb", [(1, 2), (4, 8), (25, 64)])
-def test_served_equals_alone(env, msg, epoch_iters, budget_mb):
+@pytest.mark.parametrize("kernel", ["auto", "tile"])
+def test_served_equals_alone(env, msg, epoch_iters, budget_mb, kernel):
     nd, torch = env
     names = ["qc_n2304_r12", "qc_n1152_r23"]
     built = [_grouped(nd, n) for n in names]
     codes = [b[0] for b in built]
     groups = [b[2] for b in built]
-    params = nd.params_default(max_iter=25, msg_dtype={"f32": nd.F32, "f16": nd.F16}[msg])
+    params = nd.params_default(max_iter=25, msg_dtype={"f32": nd.F32, "f16": nd.F16}[msg],
+                               variant=nd.VARIANT_TILE if kernel == "tile" else nd.VARIANT_AUTO)
     srv = nd.Server(groups, params, budget_mb << 20, epoch_iters=epoch_iters)
     try:
         st0 = srv.stats()
@@ -88,6 +93,35 @@ def test_served_equals_alone(env, msg, epoch_iters, budget_mb):
     assert st["frames_completed"] == total
     assert st["requests_completed"] == len(reqs)
     assert st["iterations"] == sum(int(h.iters.sum()) for h in handles)
+    assert st["slots_in_use"] == 0
+
+
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_served_mixed_kernels(env, msg):
+    """A server whose pools run on different kernels (n=576 on the QC kernel, n=8192 on the tile
+    kernel: its 2-layer window does not fit one CTA of the QC kernel), with their launches
+    forked within each epoch: every frame equals its batch decoded alone."""
+    nd, torch = env
+    names = ["qc_n576_r12", "qc_n8192_r2732"]
+    built = [_grouped(nd, n) for n in names]
+    codes = [b[0] for b in built]
+    groups = [b[2] for b in built]
+    params = nd.params_default(max_iter=20, msg_dtype={"f32": nd.F32, "f16": nd.F16}[msg])
+    srv = nd.Server(groups, params, 48 << 20, epoch_iters=3)
+    try:
+        reqs = _requests(codes, [300, 40, 7, 120, 64, 33], [2.25, 3.25], seed=7300)
+        handles = [srv.submit(k, llr) for k, llr in reqs]
+        for h in handles:
+            h.wait(120000)
+        st = srv.stats()
+    finally:
+        srv.close()
+    for (k, llr), h in zip(reqs, handles):
+        hard, iters, ok = _alone(nd, torch, groups[k], codes[k], llr, params)
+        np.testing.assert_array_equal(h.hard_words, hard)
+        np.testing.assert_array_equal(h.iters, iters)
+        np.testing.assert_array_equal(h.syndrome_ok, ok)
+    assert st["frames_completed"] == sum(llr.shape[0] for _, llr in reqs)
     assert st["slots_in_use"] == 0
 
 
