@@ -148,7 +148,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-KERNEL_SOURCES = ("decode_qc.cu", "decode_qc.h", "qc_device.cuh", "device_common.cuh")
+KERNEL_SOURCES = ("qc_kernel.cuh", "decode_qc.cu", "decode_qc.h", "qc_device.cuh", "device_common.cuh")
 
 
 def kernel_source_hash():
