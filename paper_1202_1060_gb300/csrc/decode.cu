@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) decode_kernel(const De
         if (r.msgs_out) {
             for (int e = tid; e < a.Epad; e += nt) {
                 const int csr = __ldg(a.edge_csr + e);
-                if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]);
+                if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]) * kLn2;
             }
         }
         write_frame_outputs(r, P, f, it, unsat, &s_err);
@@ -693,7 +693,7 @@ static void fill_run(RunArgs& r, const Groups& g, const ndgsbp_params* params, c
     r.llr_dtype = llr_dtype;
     r.n_frames = n_frames;
     r.max_iter = params->max_iter;
-    r.llr_max = params->llr_max;
+    r.llr_max = kernel_llr_limit(params->llr_max);
     r.early_stop = params->early_stop ? 1 : 0;
     r.counter = static_cast<unsigned long long*>(ws);
     r.hard_bits = d_hard_bits;

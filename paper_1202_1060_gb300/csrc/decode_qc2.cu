@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(frames2_max_threads(MAXDC)) qc_frames2_kernel(
                 const MsgT* ml = reinterpret_cast<const MsgT*>(msg) + s;
                 for (int e = tid; e < a.msg_slots; e += nt) {
                     const int csr = __ldg(a.csr_of + e);
-                    if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(ml[2 * e]);
+                    if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(ml[2 * e]) * kLn2;
                 }
             }
             write_frame_outputs(r, reinterpret_cast<const float*>(P) + s, f, it, unsat, &s_err, 2);

@@ -47,7 +47,7 @@ __device__ __forceinline__ void lane_forward(const float (&t)[LE], int nreal, fl
         const float tk = real ? t[k] : 0.f;
         sbits |= (__float_as_uint(tk) >> 31) << k;
         const float x = fminf(fabsf(tk), lim);
-        const float u = real ? ex2_approx(x * -1.4426950408889634f) : 0.f;
+        const float u = real ? ex2_approx(-x) : 0.f;   // exp(-|L|) (log2 units)
         const float n = fmaf(-0.5f, u, 0.5f);
         xu[k] = u;
         pn[k] = cn;
@@ -68,12 +68,13 @@ __device__ __forceinline__ void lane_backward(const float (&xu)[LE], const float
         const float u = xu[k];
         const float n = fmaf(-0.5f, u, 0.5f);
         const float en = pn[k] * sn;
-        const float ee = fmaf(pe[k], sn + se, pn[k] * se);
+        const float ss = sn + se;
+        const float ee = fmaf(pe[k], ss, pn[k] * se);
         const float w = fmaf(en * rcp_approx(ee), 2.f, 1.f);
-        const float mag = fminf(0.69314718055994531f * lg2_approx(w), lim);
+        const float mag = fminf(lg2_approx(w), lim);
         const unsigned sgn = ((par ^ (sbits >> k)) & 1u) << 31;
         if (k < nreal) emit(k, __uint_as_float(__float_as_uint(mag) | sgn));
-        se = fmaf(se, n + u, sn * u);
+        se = fmaf(u, ss, se * n);   // se (n + u) + sn u, reusing sn + se
         sn = sn * n;
     }
 }
@@ -346,7 +347,8 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
                         const int d = ldeg[l];
                         for (int i = tid; i < Z * d; i += nt) {
                             const int cc = i / d, k = i - cc * d, pl = k / le, kl = k - pl * le;
-                            r.msgs_out[f * r.E + ebase + i] = to_f(msg[((l * Z + cc) * tpc + pl) * C.msg_stride + kl]);
+                            r.msgs_out[f * r.E + ebase + i] =
+                                to_f(msg[((l * Z + cc) * tpc + pl) * C.msg_stride + kl]) * kLn2;
                         }
                         ebase += Z * d;
                     }

@@ -19,7 +19,7 @@ struct RunArgs {
     int llr_dtype;
     long long n_frames;
     int max_iter;
-    float llr_max;
+    float llr_max;                 // clip limit of Eq. (1) inputs and outputs, in log2 units
     int early_stop;
     unsigned long long* counter;   // next-frame counter (workspace, zeroed per launch)
     uint32_t* hard_bits;
@@ -68,18 +68,29 @@ template <> __device__ __forceinline__ float from_f<float>(float v) { return v; 
 template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
+// The kernels keep posteriors and messages in log2 units (an LLR times log2 e): Eq. (1) then
+// takes exp(-x) as ex2(-x) and ln(w) as lg2(w) with no scaling, and Eqs. (2)-(3) are linear, so
+// scaling them changes nothing but the unit.  Channel LLRs are converted when a frame is loaded,
+// posteriors and messages are converted back when they are written out, and the clip limit is
+// given in log2 units (kernel_llr_limit on the host).
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.69314718055994531f;
+
+// Channel LLR i of the input, in log2 units.
 __device__ __forceinline__ float load_llr(const void* p, int dtype, long long i) {
     switch (dtype) {
-        case NDGSBP_F64: return static_cast<float>(static_cast<const double*>(p)[i]);
-        case NDGSBP_F16: return __half2float(static_cast<const __half*>(p)[i]);
-        case NDGSBP_BF16: return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
-        default: return static_cast<const float*>(p)[i];
+        case NDGSBP_F64: return static_cast<float>(static_cast<const double*>(p)[i]) * kLog2e;   // FP32 first
+        case NDGSBP_F16: return __half2float(static_cast<const __half*>(p)[i]) * kLog2e;
+        case NDGSBP_BF16: return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]) * kLog2e;
+        default: return static_cast<const float*>(p)[i] * kLog2e;
     }
 }
 
 // Eq. (1) on the d <= MAXDC edges of one CN, in the positive-pair tanh-product form.
-// Input: t[k] (VN->CN messages).  For every edge, emit(k, L_{m->n_k}) receives the signed
-// CN->VN message clipped to lim (called in descending k).
+// Input: t[k] (VN->CN messages, log2 units).  For every edge, emit(k, L_{m->n_k}) receives the
+// signed CN->VN message in log2 units, clipped to lim (log2 units; called in descending k).
+// With x = |t| ln 2 the natural magnitude: u = exp(-x) = 2^-|t| and the output ln(w) / ln 2 =
+// lg2(w), so neither transcendental needs a scaling multiply.
 // tanh(x/2) = N / (N + E) with, for u = exp(-x), (N, E) = ((1 - u) / 2, u); pairs combine as
 // (Na Nb, Ea (Eb + Nb) + Na Eb); 2 atanh(N / (N + E)) = ln(1 + 2 N / E).  Every term is
 // positive, so neither saturated nor tiny inputs lose relative accuracy.  The product over
@@ -94,8 +105,8 @@ __device__ __forceinline__ void check_node_update(const float (&t)[MAXDC], int d
         if (k < d) {
             sbits |= (__float_as_uint(t[k]) >> 31) << k;
             const float x = fminf(fabsf(t[k]), lim);
-            const float u = ex2_approx(x * -1.4426950408889634f);   // exp(-x)
-            const float n = fmaf(-0.5f, u, 0.5f);                   // (1 - u) / 2
+            const float u = ex2_approx(-x);            // exp(-|L|)
+            const float n = fmaf(-0.5f, u, 0.5f);      // (1 - u) / 2
             xu[k] = u;
             pn[k] = cn;
             pe[k] = ce;
@@ -112,12 +123,13 @@ __device__ __forceinline__ void check_node_update(const float (&t)[MAXDC], int d
             const float u = xu[k];
             const float n = fmaf(-0.5f, u, 0.5f);
             const float en = pn[k] * sn;
-            const float ee = fmaf(pe[k], sn + se, pn[k] * se);
+            const float ss = sn + se;
+            const float ee = fmaf(pe[k], ss, pn[k] * se);
             const float w = fmaf(en * rcp_approx(ee), 2.f, 1.f);
-            const float mag = fminf(0.69314718055994531f * lg2_approx(w), lim);
+            const float mag = fminf(lg2_approx(w), lim);
             const unsigned sgn = (sflip << (31 - k)) & 0x80000000u;
             emit(k, __uint_as_float(__float_as_uint(mag) | sgn));
-            se = fmaf(se, n + u, sn * u);
+            se = fmaf(u, ss, se * n);   // se (n + u) + sn u, reusing sn + se
             sn = sn * n;
         }
     }
@@ -151,7 +163,7 @@ __device__ __forceinline__ void write_frame_outputs(const RunArgs& a, const floa
         }
     }
     if (a.posterior)
-        for (int n = tid; n < a.N; n += nt) a.posterior[f * a.N + n] = P[n * pstride];
+        for (int n = tid; n < a.N; n += nt) a.posterior[f * a.N + n] = P[n * pstride] * kLn2;
     if (a.stats && lane == 0 && err) atomicAdd(s_err, err);
     __syncthreads();
     if (tid == 0) {

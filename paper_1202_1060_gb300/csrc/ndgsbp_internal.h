@@ -128,6 +128,9 @@ const Layout& flood_layout(const Groups& g);
 const QcLayout& flood_qc_layout(const Groups& g);
 void release_device_layouts(Groups& g);   // frees device copies (defined in the CUDA file)
 
+// The clip limit llr_max (natural LLR units) in the kernels' log2 units (LLR times log2 e).
+inline float kernel_llr_limit(float llr_max) { return llr_max * 1.4426950408889634f; }
+
 // A decode plan kept across launches (ragged launches in the per-code mode): what
 // ndgsbp_decode plans for (groups, params, n_frames), with the grouping's tables on the device.
 struct Plan;

@@ -32,9 +32,8 @@ __device__ __forceinline__ void check_node_update2(const float2 (&t)[D], float l
     for (int k = 0; k < D; ++k) {
         sb0 |= (__float_as_uint(t[k].x) >> 31) << k;
         sb1 |= (__float_as_uint(t[k].y) >> 31) << k;
-        const float2 x = __fmul2_rn(make_float2(fminf(fabsf(t[k].x), lim), fminf(fabsf(t[k].y), lim)),
-                                    f2(-1.4426950408889634f));
-        const float2 u = make_float2(ex2_approx(x.x), ex2_approx(x.y));   // exp(-|t|)
+        const float2 x = make_float2(fminf(fabsf(t[k].x), lim), fminf(fabsf(t[k].y), lim));
+        const float2 u = make_float2(ex2_approx(-x.x), ex2_approx(-x.y));   // exp(-|L|) (log2 units)
         const float2 n = __ffma2_rn(f2(-0.5f), u, f2(0.5f));             // (1 - u) / 2
         xu[k] = u;
         pn[k] = cn;
@@ -50,13 +49,14 @@ __device__ __forceinline__ void check_node_update2(const float2 (&t)[D], float l
         const float2 u = xu[k];
         const float2 n = __ffma2_rn(f2(-0.5f), u, f2(0.5f));
         const float2 en = __fmul2_rn(pn[k], sn);
-        const float2 ee = __ffma2_rn(pe[k], __fadd2_rn(sn, se), __fmul2_rn(pn[k], se));
+        const float2 ss = __fadd2_rn(sn, se);
+        const float2 ee = __ffma2_rn(pe[k], ss, __fmul2_rn(pn[k], se));
         const float2 w = __ffma2_rn(__fmul2_rn(en, make_float2(rcp_approx(ee.x), rcp_approx(ee.y))), f2(2.f), f2(1.f));
-        const float2 lg = __fmul2_rn(f2(0.69314718055994531f), make_float2(lg2_approx(w.x), lg2_approx(w.y)));
+        const float2 lg = make_float2(lg2_approx(w.x), lg2_approx(w.y));
         const float m0 = fminf(lg.x, lim), m1 = fminf(lg.y, lim);
         const unsigned g0 = (sf0 << (31 - k)) & 0x80000000u, g1 = (sf1 << (31 - k)) & 0x80000000u;
         emit(k, make_float2(__uint_as_float(__float_as_uint(m0) | g0), __uint_as_float(__float_as_uint(m1) | g1)));
-        se = __ffma2_rn(se, __fadd2_rn(n, u), __fmul2_rn(sn, u));
+        se = __ffma2_rn(u, ss, __fmul2_rn(se, n));   // se (n + u) + sn u, reusing sn + se
         sn = __fmul2_rn(sn, n);
     }
 }

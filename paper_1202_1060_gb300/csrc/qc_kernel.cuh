@@ -189,7 +189,7 @@ __device__ __forceinline__ void qc_frame_messages_out(const QcArgs& a, const Msg
     if (!r.msgs_out) return;
     for (int e = threadIdx.x; e < a.msg_slots; e += blockDim.x) {
         const int csr = __ldg(a.csr_of + e);
-        if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]);
+        if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]) * kLn2;
     }
 }
 

@@ -267,7 +267,7 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         r.llr_dtype = b.llr_dtype;
         r.n_frames = b.n_frames;
         r.max_iter = params->max_iter;
-        r.llr_max = params->llr_max;
+        r.llr_max = kernel_llr_limit(params->llr_max);
         r.early_stop = params->early_stop ? 1 : 0;
         r.hard_bits = b.d_hard_bits;
         r.iters = b.d_iters;

@@ -633,7 +633,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         r.llr_dtype = NDGSBP_F32;
         r.n_frames = p.slots;
         r.max_iter = params->max_iter;
-        r.llr_max = params->llr_max;
+        r.llr_max = kernel_llr_limit(params->llr_max);
         r.early_stop = params->early_stop ? 1 : 0;
         r.hard_bits = device_view(p.h_hard);
         r.iters = device_view(p.h_iters);
