@@ -52,7 +52,7 @@ __device__ __forceinline__ void lane_forward(const float (&t)[LE], int nreal, fl
         xu[k] = u;
         pn[k] = cn;
         pe[k] = ce;
-        ce = fmaf(ce, n + u, cn * u);
+        ce = fmaf(ce, fmaf(0.5f, u, 0.5f), cn * u);   // n + u = (1 + u) / 2
         cn = cn * n;
     }
 }

@@ -97,37 +97,40 @@ __device__ __forceinline__ float load_llr(const void* p, int dtype, long long i)
 // "all edges but k" is prefix(k) (x) suffix(k + 1); no division.
 template <int MAXDC, typename Emit>
 __device__ __forceinline__ void check_node_update(const float (&t)[MAXDC], int d, float lim, Emit emit) {
-    float xu[MAXDC], pn[MAXDC], pe[MAXDC];
-    unsigned sbits = 0u;
+    // xs[k]: u_k = exp(-|L_k|) >= 0 carrying the sign of t[k] in its sign bit (every use of u
+    // takes |xs|, a free operand modifier); par: bit 31 = parity of the input signs
+    float xs[MAXDC], pn[MAXDC], pe[MAXDC];
+    unsigned par = 0u;
     float cn = 1.f, ce = 0.f;
 #pragma unroll
     for (int k = 0; k < MAXDC; ++k) {
         if (k < d) {
-            sbits |= (__float_as_uint(t[k]) >> 31) << k;
+            const unsigned tb = __float_as_uint(t[k]);
+            par ^= tb;
             const float x = fminf(fabsf(t[k]), lim);
             const float u = ex2_approx(-x);            // exp(-|L|)
             const float n = fmaf(-0.5f, u, 0.5f);      // (1 - u) / 2
-            xu[k] = u;
+            xs[k] = __uint_as_float(__float_as_uint(u) | (tb & 0x80000000u));
             pn[k] = cn;
             pe[k] = ce;
-            ce = fmaf(ce, n + u, cn * u);
+            ce = fmaf(ce, fmaf(0.5f, u, 0.5f), cn * u);   // n + u = (1 + u) / 2
             cn = cn * n;
         }
     }
-    // bit k of sflip = sign of output k: the parity of all input signs xor sign k
-    const unsigned sflip = sbits ^ (0u - (__popc(sbits) & 1u));
+    // sign of output k: the parity of all input signs xor sign k
+    const unsigned pm = par & 0x80000000u;
     float sn = 1.f, se = 0.f;
 #pragma unroll
     for (int k = MAXDC - 1; k >= 0; --k) {
         if (k < d) {
-            const float u = xu[k];
+            const float u = fabsf(xs[k]);
             const float n = fmaf(-0.5f, u, 0.5f);
             const float en = pn[k] * sn;
             const float ss = sn + se;
             const float ee = fmaf(pe[k], ss, pn[k] * se);
             const float w = fmaf(en * rcp_approx(ee), 2.f, 1.f);
             const float mag = fminf(lg2_approx(w), lim);
-            const unsigned sgn = (sflip << (31 - k)) & 0x80000000u;
+            const unsigned sgn = (__float_as_uint(xs[k]) ^ pm) & 0x80000000u;
             emit(k, __uint_as_float(__float_as_uint(mag) | sgn));
             se = fmaf(u, ss, se * n);   // se (n + u) + sn u, reusing sn + se
             sn = sn * n;

@@ -38,7 +38,7 @@ __device__ __forceinline__ void check_node_update2(const float2 (&t)[D], float l
         xu[k] = u;
         pn[k] = cn;
         pe[k] = ce;
-        ce = __ffma2_rn(ce, __fadd2_rn(n, u), __fmul2_rn(cn, u));
+        ce = __ffma2_rn(ce, __ffma2_rn(f2(0.5f), u, f2(0.5f)), __fmul2_rn(cn, u));   // n + u = (1 + u) / 2
         cn = __fmul2_rn(cn, n);
     }
     // bit k of sf0 / sf1 = sign of output k: the parity of all input signs xor sign k
