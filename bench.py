@@ -424,7 +424,8 @@ def run_ours(args):
 def run_e2e(args, nd, torch, code, c, groups, params, F, W, dev, rank, world):
     """Same metric through the public API with host buffers: every step copies each point's
     LLRs from pinned host memory, decodes, and copies decisions, iteration counts and syndrome
-    flags back.  Copies of the next point overlap the current decode (two streams)."""
+    flags back.  Host-to-device copies, decodes and device-to-host copies run on three streams
+    over two device buffers, so the next point's LLRs arrive while the current point decodes."""
     import numpy as np
     import torch.distributed as dist
     n_pts = len(EBN0)
@@ -444,26 +445,37 @@ def run_e2e(args, nd, torch, code, c, groups, params, F, W, dev, rank, world):
     d_iters = [torch.empty(F, dtype=torch.int32, device=dev) for _ in range(2)]
     d_ok = [torch.empty(F, dtype=torch.uint8, device=dev) for _ in range(2)]
     ws = torch.zeros(max(256, groups.workspace_size(params, F)), dtype=torch.uint8, device=dev)
-    copy_s = torch.cuda.Stream(device=dev)
+    h2d_s = torch.cuda.Stream(device=dev)
     comp_s = torch.cuda.Stream(device=dev)
+    d2h_s = torch.cuda.Stream(device=dev)
+    # buffers alternate by a point counter that runs across steps; free[b] marks the end of the
+    # device-to-host copies of the last point that used buffer b (its LLRs and outputs may then
+    # be overwritten), so no copy overtakes a decode or a read-back of an earlier step
+    ring = {"n": 0, "free": [None, None]}
 
     def one_step():
-        loaded = [torch.cuda.Event() for _ in range(n_pts)]
-        done = [torch.cuda.Event() for _ in range(n_pts)]
         for i in range(n_pts):
-            b = i % 2
-            with torch.cuda.stream(copy_s):
-                if i >= 2:
-                    copy_s.wait_event(done[i - 2])
+            b = ring["n"] % 2
+            ring["n"] += 1
+            with torch.cuda.stream(h2d_s):
+                if ring["free"][b] is not None:
+                    h2d_s.wait_event(ring["free"][b])
                 d_llr[b].copy_(host_llr[i], non_blocking=True)
-                loaded[i].record(copy_s)
+                loaded = torch.cuda.Event()
+                loaded.record(h2d_s)
             with torch.cuda.stream(comp_s):
-                comp_s.wait_event(loaded[i])
+                comp_s.wait_event(loaded)
                 nd.decode_plain(groups, params, d_llr[b], ws, d_hard[b], d_iters[b], d_ok[b], stream=comp_s)
+                decoded = torch.cuda.Event()
+                decoded.record(comp_s)
+            with torch.cuda.stream(d2h_s):
+                d2h_s.wait_event(decoded)
                 host_hard[i].copy_(d_hard[b], non_blocking=True)
                 host_iters[i].copy_(d_iters[b], non_blocking=True)
                 host_ok[i].copy_(d_ok[b], non_blocking=True)
-                done[i].record(comp_s)
+                freed = torch.cuda.Event()
+                freed.record(d2h_s)
+            ring["free"][b] = freed
 
     for _ in range(max(1, args.warmup)):
         one_step()
@@ -481,9 +493,17 @@ def run_e2e(args, nd, torch, code, c, groups, params, F, W, dev, rank, world):
     h2d = n_pts * F * c.N * 4
     d2h = n_pts * F * (W * 4 + 4 + 1)
     ok_frac = float(host_ok.float().mean())
+    # the read-back of the last point equals a device-resident decode of the same LLRs
+    chk_llr = host_llr[n_pts - 1].to(dev)
+    chk_hard = torch.empty((F, W), dtype=torch.int32, device=dev)
+    chk_iters = torch.empty(F, dtype=torch.int32, device=dev)
+    nd.decode_plain(groups, params, chk_llr, ws, chk_hard, chk_iters)
+    torch.cuda.synchronize()
+    match = bool(torch.equal(chk_hard.cpu(), host_hard[n_pts - 1]) and torch.equal(chk_iters.cpu(), host_iters[n_pts - 1]))
     return {"value": frames * 1152 / dt / 1e9, "unit": "Gbit/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / args.steps,
-            "timer": "host wall clock around all steps, synchronised", "syndrome_ok_fraction": ok_frac}
+            "timer": "host wall clock around all steps, synchronised", "syndrome_ok_fraction": ok_frac,
+            "readback_matches_device_decode": match}
 
 
 # ------------------------------------------------------------------------------------------
