@@ -218,6 +218,8 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
     const int c = tid - j * Z, c4 = 4 * c;
     const bool active = j < W;
     const float lim = r.llr_max;
+    // every warp full and every lane through the same layers: the syndrome loop may vote per warp
+    const bool warp_vote = (W * Z) % 32 == 0 && blockDim.x == W * Z && nl % W == 0;
     if (tid == 0) s_err = 0u;
     for (;;) {
         const long long fi = next_frame(r, &s_frame);   // barrier: also orders the table loads
@@ -340,6 +342,9 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
                                 if (k < d) p ^= (at_byte(P, qc_vb(et[k], c, c4, Z4)) < 0.f) ? 1u : 0u;
                         }
                         bad |= p;
+                        // once a lane of the warp has found an unsatisfied check the frame's
+                        // syndrome is decided (the OR below), so the warp stops checking
+                        if (warp_vote && __any_sync(0xffffffffu, bad)) break;
                     }
                 }
                 unsat = __syncthreads_or(bad);
