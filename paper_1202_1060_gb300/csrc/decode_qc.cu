@@ -207,7 +207,7 @@ static size_t a16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 size_t qc_table_bytes(const QcLayout& Q, bool w2) {
     const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;
     size_t b = a16(static_cast<size_t>(Q.n_layers) * Q.max_deg * 8) + 3 * a16(static_cast<size_t>(Q.n_layers) * 4) +
-               a16(G * Q.window * 4);
+               a16(G * Q.window * 4) + G * Q.window * 16;
     if (w2) b += a16(G * 2 * 4) + a16(static_cast<size_t>(Q.Z) * (Q.max_deg | 1) * 4);
     return b;
 }

@@ -308,7 +308,10 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
                 const int i = rr * nt + tid;
                 const int s = fast_div(i, C.div_syn);
                 unsigned pbit = 0u;
-                const bool live = i < swork && sh.frame[s] >= 0 && (r.early_stop || sh.iter[s] >= r.max_iter);
+                // a slot already found unsatisfied is decided: its remaining checks are skipped (the
+                // flag only goes from 0 to 1 in this pass; the lanes of a CN read it together)
+                const bool live = i < swork && sh.frame[s] >= 0 && (r.early_stop || sh.iter[s] >= r.max_iter) &&
+                                  !(r.early_stop && *reinterpret_cast<volatile unsigned*>(&sh.unsat[s]));
                 const int w = i - s * per_s;
                 const int cn_i = w >> tsh, p = w & (tpc - 1);
                 if (live) {

@@ -126,6 +126,7 @@ struct QcSmem {
     int* lstride;
     int* loff;
     int* glay;
+    int4* gtab;         // per (grouping, group, position): (l maxdeg, d_l, layer_off[l], layer_stride[l])
     unsigned* w2mask;   // [G][2] bit k: edge k of that window position is on a shared block column
     float* dx;   // [Z][dxs] position-0 changes on shared block columns
     int dxs;     // odd stride >= maxdeg
@@ -147,8 +148,11 @@ __device__ __forceinline__ QcSmem qc_smem_layout(unsigned char* smem, const QcAr
     off += (static_cast<size_t>(a.nl) * 4 + 15) & ~static_cast<size_t>(15);
     s.loff = reinterpret_cast<int*>(smem + off);
     off += (static_cast<size_t>(a.nl) * 4 + 15) & ~static_cast<size_t>(15);
+    const int gw = a.G * a.window * a.n_groupings;
     s.glay = reinterpret_cast<int*>(smem + off);
-    off += (static_cast<size_t>(a.G) * a.window * 4 + 15) & ~static_cast<size_t>(15);
+    off += (static_cast<size_t>(gw) * 4 + 15) & ~static_cast<size_t>(15);
+    s.gtab = reinterpret_cast<int4*>(smem + off);
+    off += static_cast<size_t>(gw) * 16;
     s.dxs = a.maxdeg | 1;
     s.w2mask = reinterpret_cast<unsigned*>(smem + off);
     if (a.win2) off += (static_cast<size_t>(a.G) * 2 * 4 + 15) & ~static_cast<size_t>(15);
@@ -170,7 +174,11 @@ __device__ __forceinline__ QcSmem qc_smem_layout(unsigned char* smem, const QcAr
         s.lstride[i] = a.layer_stride[i];
         s.loff[i] = a.layer_off[i];
     }
-    for (int i = tid; i < a.G * a.window * a.n_groupings; i += nt) s.glay[i] = a.group_layers[i];
+    for (int i = tid; i < gw; i += nt) {
+        const int l = a.group_layers[i];
+        s.glay[i] = l;
+        s.gtab[i] = make_int4(l * a.maxdeg, a.layer_deg[l], a.layer_off[l], a.layer_stride[l]);
+    }
     return s;
 }
 
@@ -252,6 +260,7 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
         bool park = false;
         for (;; ++it) {
             const int* gl = s.glay + ((it - 1) % a.n_groupings) * a.G * W;   // this iteration's grouping
+            const int4* gt = s.gtab + ((it - 1) % a.n_groupings) * a.G * W;
             for (int g = 0; g < a.G; ++g) {
                 float dl[MAXDC];
                 int vb[MAXDC];
@@ -293,10 +302,10 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
                     continue;
                 }
                 if (active) {
-                    const int l = gl[g * W + j];
-                    d = s.ldeg[l];
-                    const int2* et = s.tab + l * md;
-                    MsgT* m = msg + s.loff[l] + c * s.lstride[l];
+                    const int4 ge = gt[g * W + j];   // one 16-byte load: table offset, degree, message offset, stride
+                    d = ge.y;
+                    const int2* et = s.tab + ge.x;
+                    MsgT* m = msg + ge.z + c * ge.w;
                     if constexpr (SPEC) {
 #define NDGSBP_CASE_A(D) \
     if (d == D) qc_phase_a<NDGSBP_DD(D), MAXDC, MsgT>(et, c, c4, Z4, P, m, lim, vb, dl);
