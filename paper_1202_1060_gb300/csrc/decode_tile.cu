@@ -81,6 +81,14 @@ __device__ __forceinline__ void lane_backward(const float (&xu)[LE], const float
     }
 }
 
+// A code's tables at the start of shared memory: edge table [nl][md] (int2), layer degrees,
+// strides and offsets [nl] each, group layers [gwk], then, 16-byte aligned, one record per
+// (grouping, group, position): (l md, d_l, l Z tpc msg_stride, 0).
+__device__ __forceinline__ int4* tile_group_records(int2* tab, int nl, int md, int gwk) {
+    const size_t off = static_cast<size_t>(nl) * md * 8 + 3 * static_cast<size_t>(nl) * 4 + static_cast<size_t>(gwk) * 4;
+    return reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(tab) + ((off + 15) & ~static_cast<size_t>(15)));
+}
+
 // Shared state of a CTA (static part).
 struct TileShared {
     long long frame[kMaxSlots];
@@ -180,7 +188,7 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
     const int Z = C.Z, Z4 = 4 * C.Z, W = C.window, nl = C.nl, md = C.maxdeg, tpc = C.tpc, le = C.le;
     const int tsh = tpc == 1 ? 0 : (tpc == 2 ? 1 : 2);
     const int* ldeg = reinterpret_cast<const int*>(tab + nl * md);
-    const int* glay = ldeg + 3 * nl;
+    const int4* gtab = tile_group_records(const_cast<int2*>(tab), nl, md, C.G * W * C.n_groupings);
     const int per_slot = W * Z * tpc;           // CN-lanes of one group in one slot
     const int work = C.slots * per_slot;
     const int rounds = REGB ? 1 : (work + nt - 1) / nt;
@@ -211,12 +219,13 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
                 if (live) {
                     unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
                     P = reinterpret_cast<float*>(base);
-                    const int l = glay[sh.gofs[s] + g * W + j];
+                    // (l maxdeg, d_l, first message of layer l) of this slot's grouping, position j
+                    const int4 ge = gtab[sh.gofs[s] + g * W + j];
                     const int k0 = p * le;
-                    L = min(max(ldeg[l] - k0, 0), le);
-                    m = slot_msgs<MsgT, SERVE>(C, base, s, sh.frame[s]) + ((l * Z + c) * tpc + p) * C.msg_stride;
+                    L = min(max(ge.y - k0, 0), le);
+                    m = slot_msgs<MsgT, SERVE>(C, base, s, sh.frame[s]) + ge.z + (c * tpc + p) * C.msg_stride;
                     dl = reinterpret_cast<float*>(base + C.p_bytes + C.m_bytes) + (cnl * tpc + p) * C.delta_stride;
-                    et = tab + l * md + k0;
+                    et = tab + ge.x + k0;
 #pragma unroll
                     for (int k = 0; k < LE; ++k) {
                         if (k < L) {
@@ -276,14 +285,14 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
                         const int w = i - s * per_pos;
                         const int cb = w >> tsh, p = w & (tpc - 1);
                         const int cnl = jj * Z + cb;
-                        const int l = glay[sh.gofs[s] + g * W + jj];
+                        const int4 ge = gtab[sh.gofs[s] + g * W + jj];
                         const int k0 = p * le;
-                        const int Lb = min(max(ldeg[l] - k0, 0), le);
+                        const int Lb = min(max(ge.y - k0, 0), le);
                         unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
                         float* Pb = reinterpret_cast<float*>(base);
                         const float* dl = reinterpret_cast<const float*>(base + C.p_bytes + C.m_bytes) +
                                           (cnl * tpc + p) * C.delta_stride;
-                        const int2* eb = tab + l * md + k0;
+                        const int2* eb = tab + ge.x + k0;
 #pragma unroll
                         for (int k = 0; k < LE; ++k)
                             if (k < Lb) at_b(Pb, tile_vb(eb[k], cb, Z4)) += dl[k];
@@ -420,6 +429,8 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
         int* lstride = ldeg + nl;
         int* loff = lstride + nl;
         int* glay = loff + nl;
+        const int gwk = C.G * C.window * C.n_groupings;
+        int4* gtab = tile_group_records(tab, nl, md, gwk);
         if (sh.cur_code != tile.x) {
             for (int i = tid; i < nl * md; i += nt) tab[i] = C.edge_tab[i];
             for (int i = tid; i < nl; i += nt) {
@@ -427,7 +438,11 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
                 lstride[i] = C.layer_stride[i];
                 loff[i] = C.layer_off[i];
             }
-            for (int i = tid; i < C.G * C.window * C.n_groupings; i += nt) glay[i] = C.group_layers[i];
+            for (int i = tid; i < gwk; i += nt) {
+                const int l = C.group_layers[i];
+                glay[i] = l;
+                gtab[i] = make_int4(l * md, C.layer_deg[l], l * C.Z * C.tpc * C.msg_stride, 0);
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -477,9 +492,10 @@ TileKernelFn pick_tile_kernel(int msg_dtype, bool serve, int lane_width, bool re
 int tile_lane_width(int le) { return le < 1 ? 0 : le <= 4 ? 4 : le <= 6 ? 6 : le <= 8 ? 8 : 0; }
 
 size_t tile_table_bytes(const QcLayout& Q) {
-    const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;
-    const size_t b = static_cast<size_t>(Q.n_layers) * Q.max_deg * 8 + 3 * static_cast<size_t>(Q.n_layers) * 4 + G * Q.window * 4;
-    return (b + 15) & ~static_cast<size_t>(15);
+    const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;   // groups of every grouping
+    size_t b = static_cast<size_t>(Q.n_layers) * Q.max_deg * 8 + 3 * static_cast<size_t>(Q.n_layers) * 4 + G * Q.window * 4;
+    b = (b + 15) & ~static_cast<size_t>(15);   // the per-group records (tile_group_records)
+    return b + G * Q.window * 16;
 }
 
 TileShape tile_shape(const QcLayout& Q, int tpc, int msg_dtype) {

@@ -257,10 +257,12 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
         }
         __syncthreads();
         int it = it0 + 1, unsat = 1;
+        const int gw1 = a.G * W, gwk = gw1 * a.n_groupings;
+        int gsel = (it0 % a.n_groupings) * gw1;   // iteration it uses grouping (it - 1) mod n_groupings
         bool park = false;
         for (;; ++it) {
-            const int* gl = s.glay + ((it - 1) % a.n_groupings) * a.G * W;   // this iteration's grouping
-            const int4* gt = s.gtab + ((it - 1) % a.n_groupings) * a.G * W;
+            const int* gl = s.glay + gsel;   // this iteration's grouping
+            const int4* gt = s.gtab + gsel;
             for (int g = 0; g < a.G; ++g) {
                 float dl[MAXDC];
                 int vb[MAXDC];
@@ -364,6 +366,8 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
                 park = true;
                 break;
             }
+            gsel += gw1;
+            if (gsel == gwk) gsel = 0;
         }
         if constexpr (SERVE) {
             if (park) {
