@@ -769,8 +769,6 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
         C.delta_stride = plan.tile_delta_stride;
         C.edge_tab = reinterpret_cast<const int2*>(D.edge_tab);
         C.layer_deg = D.layer_deg;
-        C.layer_stride = D.layer_stride;
-        C.layer_off = D.layer_off;
         C.group_layers = D.group_layers;
         C.csr_of = D.csr_of;
         tile_code_finish(C);

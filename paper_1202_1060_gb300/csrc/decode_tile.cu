@@ -81,11 +81,11 @@ __device__ __forceinline__ void lane_backward(const float (&xu)[LE], const float
     }
 }
 
-// A code's tables at the start of shared memory: edge table [nl][md] (int2), layer degrees,
-// strides and offsets [nl] each, group layers [gwk], then, 16-byte aligned, one record per
-// (grouping, group, position): (l md, d_l, l Z tpc msg_stride, 0).
-__device__ __forceinline__ int4* tile_group_records(int2* tab, int nl, int md, int gwk) {
-    const size_t off = static_cast<size_t>(nl) * md * 8 + 3 * static_cast<size_t>(nl) * 4 + static_cast<size_t>(gwk) * 4;
+// A code's tables at the start of shared memory: edge table [nl][md] (int2), layer degrees
+// [nl], then, 16-byte aligned, one record per (grouping, group, position):
+// (l md, d_l, l Z tpc msg_stride, 0).
+__device__ __forceinline__ int4* tile_group_records(int2* tab, int nl, int md) {
+    const size_t off = static_cast<size_t>(nl) * md * 8 + static_cast<size_t>(nl) * 4;
     return reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(tab) + ((off + 15) & ~static_cast<size_t>(15)));
 }
 
@@ -188,7 +188,7 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
     const int Z = C.Z, Z4 = 4 * C.Z, W = C.window, nl = C.nl, md = C.maxdeg, tpc = C.tpc, le = C.le;
     const int tsh = tpc == 1 ? 0 : (tpc == 2 ? 1 : 2);
     const int* ldeg = reinterpret_cast<const int*>(tab + nl * md);
-    const int4* gtab = tile_group_records(const_cast<int2*>(tab), nl, md, C.G * W * C.n_groupings);
+    const int4* gtab = tile_group_records(const_cast<int2*>(tab), nl, md);
     const int per_slot = W * Z * tpc;           // CN-lanes of one group in one slot
     const int work = C.slots * per_slot;
     const int rounds = REGB ? 1 : (work + nt - 1) / nt;
@@ -424,23 +424,15 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
         }
         const TileCode& C = SINGLE ? a.codes[0] : a.codes[tile.x];
         const int nl = C.nl, md = C.maxdeg;
-        // code tables: (4 (b Z + s), Z - s) per edge, degrees, strides, offsets, group layers
+        // code tables: (4 (b Z + s), Z - s) per edge, layer degrees, per-group records
         int* ldeg = reinterpret_cast<int*>(tab + nl * md);
-        int* lstride = ldeg + nl;
-        int* loff = lstride + nl;
-        int* glay = loff + nl;
         const int gwk = C.G * C.window * C.n_groupings;
-        int4* gtab = tile_group_records(tab, nl, md, gwk);
+        int4* gtab = tile_group_records(tab, nl, md);
         if (sh.cur_code != tile.x) {
             for (int i = tid; i < nl * md; i += nt) tab[i] = C.edge_tab[i];
-            for (int i = tid; i < nl; i += nt) {
-                ldeg[i] = C.layer_deg[i];
-                lstride[i] = C.layer_stride[i];
-                loff[i] = C.layer_off[i];
-            }
+            for (int i = tid; i < nl; i += nt) ldeg[i] = C.layer_deg[i];
             for (int i = tid; i < gwk; i += nt) {
                 const int l = C.group_layers[i];
-                glay[i] = l;
                 gtab[i] = make_int4(l * md, C.layer_deg[l], l * C.Z * C.tpc * C.msg_stride, 0);
             }
         }
@@ -493,7 +485,7 @@ int tile_lane_width(int le) { return le < 1 ? 0 : le <= 4 ? 4 : le <= 6 ? 6 : le
 
 size_t tile_table_bytes(const QcLayout& Q) {
     const size_t G = Q.window ? Q.group_layers.size() / Q.window : 0;   // groups of every grouping
-    size_t b = static_cast<size_t>(Q.n_layers) * Q.max_deg * 8 + 3 * static_cast<size_t>(Q.n_layers) * 4 + G * Q.window * 4;
+    size_t b = static_cast<size_t>(Q.n_layers) * Q.max_deg * 8 + static_cast<size_t>(Q.n_layers) * 4;
     b = (b + 15) & ~static_cast<size_t>(15);   // the per-group records (tile_group_records)
     return b + G * Q.window * 16;
 }

@@ -41,8 +41,6 @@ struct TileCode {
                           // so the lanes of a warp hit distinct shared-memory banks
     const int2* edge_tab;
     const int32_t* layer_deg;
-    const int32_t* layer_stride;
-    const int32_t* layer_off;
     const int32_t* group_layers;
     const int32_t* csr_of;
     RunArgs r;            // this code's batch, parameters and outputs (r.counter unused)

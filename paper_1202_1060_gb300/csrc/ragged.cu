@@ -253,8 +253,6 @@ ndgsbp_status ndgsbp_ragged_create(const ndgsbp_batch* batches, int32_t n_batche
         C.delta_stride = c.ds;
         C.edge_tab = reinterpret_cast<const int2*>(c.D->edge_tab);
         C.layer_deg = c.D->layer_deg;
-        C.layer_stride = c.D->layer_stride;
-        C.layer_off = c.D->layer_off;
         C.group_layers = c.D->group_layers;
         C.csr_of = c.D->csr_of;
         tile_code_finish(C);

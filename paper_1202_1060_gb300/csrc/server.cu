@@ -613,8 +613,6 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         C.delta_stride = p.ds;
         C.edge_tab = reinterpret_cast<const int2*>(p.D->edge_tab);
         C.layer_deg = p.D->layer_deg;
-        C.layer_stride = p.D->layer_stride;
-        C.layer_off = p.D->layer_off;
         C.group_layers = p.D->group_layers;
         C.csr_of = p.D->csr_of;
         tile_code_finish(C);
