@@ -26,6 +26,8 @@ import sys
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# scratch files of a bench run (clock samples, the autotuner's cache); not part of the results
+OUT_DIR = os.environ.get("NDGSBP_BENCH_OUT", os.path.join(ROOT, "bench_out"))
 sys.path.insert(0, ROOT)
 
 METRIC = "NDGSBP decoded Gbit/s and p50/p99 frame latency at oracle-matched FER"
@@ -95,7 +97,8 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(OUT_DIR, exist_ok=True)
+        self.path = os.path.join(OUT_DIR, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -581,7 +584,7 @@ def run_ragged(args):
     p0 = nd.params_default(max_iter=imax, msg_dtype=nd.F16)
     t0 = time.perf_counter()
     params, tuned_ms = nd.ragged_autotune(batches, p0, sample_frames=8192,
-                                          cache_path=os.path.join(ROOT, "gpurun_out", "tune_cache.txt"))
+                                          cache_path=os.path.join(OUT_DIR, "tune_cache.txt"))
     tune_s = time.perf_counter() - t0
     per_code_mode = params.variant == nd.VARIANT_RAGGED_PER_CODE
     # the other mode, timed on the same frames (tile: the library's default shape)
@@ -923,6 +926,7 @@ def main():
     ap.add_argument("--epoch-iters", type=int, default=4)
     ap.add_argument("--arrival-seed", type=int, default=20260)
     args = ap.parse_args()
+    os.makedirs(OUT_DIR, exist_ok=True)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -113,3 +113,29 @@ def test_fixed_vs_cycled_groupings_fer(env):
             print(f"Eb/N0 {ebn0} groupings {K}: FER {fe / n:.3e} [{lo:.3e}, {hi:.3e}], mean iterations "
                   f"{s[nd.STAT_ITERATIONS] / n:.2f}")
             assert 0 < fe / n < 0.1
+
+
+@pytest.mark.parametrize("kernel", ["auto", "tile"])
+def test_cycled_groupings_served_equal_alone(env, kernel):
+    """Serving with groupings cycled by iteration: frames parked every 2 iterations resume with
+    the grouping of their next iteration (3 groupings, so parking and the cycle fall out of
+    step); every frame equals its batch decoded alone by the same kernel."""
+    nd, torch = env
+    c = I.code_by_name("qc_n2304_r12")
+    code = nd.Code.from_inputs(c)
+    g = nd.Groups.build(code, 12, 0.5, 7, unit=nd.UNIT_LAYER, flags=nd.GROUPS_CYCLIC, n_groupings=3)
+    v = nd.VARIANT_TILE if kernel == "tile" else nd.VARIANT_AUTO
+    params = nd.params_default(max_iter=20, variant=v)
+    reqs = [I.channel_llr(c.N, F, 1.5, 0.5, seed=900 + i).astype(np.float32) for i, F in enumerate((50, 7, 120))]
+    srv = nd.Server([g], params, 8 << 20, epoch_iters=2)
+    try:
+        hs = [srv.submit(0, x) for x in reqs]
+        for h in hs:
+            h.wait(120000)
+    finally:
+        srv.close()
+    for x, h in zip(reqs, hs):
+        r = _run(nd, torch, g, c, x, max_iter=20, variant=v)
+        np.testing.assert_array_equal(h.iters, r["iters"])
+        np.testing.assert_array_equal(h.hard_words, r["hard"].view(np.uint32))
+        np.testing.assert_array_equal(h.syndrome_ok, r["ok"])
