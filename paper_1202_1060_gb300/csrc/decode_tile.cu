@@ -13,10 +13,14 @@
 // lanes' totals, so the exclusion "all edges but k" costs nothing extra per edge.  With tpc = 1
 // the operations are those of the other kernels, in the same order.
 //
-// A group's CNs are processed in rounds over the block; the message changes go to a per-slot
-// delta buffer in shared memory, and phase B adds them to the posterior layer position by
+// A group's CNs are processed in rounds over the block.  When one round covers the group (the
+// REGB instances) every lane keeps its message changes in registers; otherwise they go to a
+// per-slot delta buffer in shared memory.  Phase B adds them to the posterior layer position by
 // layer position (the fixed order of the other kernels).  Posteriors, messages (when they fit)
-// and deltas of every slot live in shared memory, after the code's tables.
+// and deltas of every slot live in shared memory, after the code's tables.  Kernel instances
+// differ in the unrolled lane width LE (4, 6, 8), REGB, and SINGLE (a launch over one code,
+// whose parameters are then read at fixed offsets).  Posteriors and messages are in log2 units
+// (see load_llr).
 #include <cstring>
 
 #include "decode_tile.h"

@@ -1,5 +1,8 @@
 // The single-CN layered QC decode kernel (qc_decode_kernel) and its device helpers, included by
-// decode_qc.cu (decode instances) and decode_qc_serve.cu (serving instances).
+// decode_qc.cu (decode instances) and decode_qc_serve.cu (serving instances).  The index
+// scheme, phases and write-back order are described at the top of decode_qc.cu.  Per group a
+// CN reads one 16-byte record (table offset, degree, message offset, stride) for its layer;
+// the syndrome check of Step 4 stops per warp once a lane has found an unsatisfied check.
 #pragma once
 
 #include "decode_qc.h"
