@@ -42,11 +42,20 @@ __global__ void awgn_kernel(int N, long long n_frames, float scale, float scale_
                             uint32_t k1, const uint32_t* __restrict__ cw, int cw_per_frame, T* __restrict__ out) {
     const int nb = (N + 3) >> 2;
     const int W = (N + 31) >> 5;
-    const long long total = n_frames * nb;
-    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
-         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long f = idx / nb;
-        const int b = static_cast<int>(idx - f * nb);
+    // flat index idx = f nb + b, stepped by the grid stride: one division per thread, then the
+    // (frame, block) pair advances by (stride / nb, stride % nb) with a carry
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    const long long idx0 = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    const long long step_f = stride / nb;
+    const int step_b = static_cast<int>(stride - step_f * nb);
+    long long f = idx0 / nb;
+    int b = static_cast<int>(idx0 - f * nb);
+    for (; f < n_frames; f += step_f, b += step_b) {
+        if (b >= nb) {
+            b -= nb;
+            ++f;
+            if (f >= n_frames) break;
+        }
         uint32_t c[4] = {static_cast<uint32_t>(b), static_cast<uint32_t>(f), static_cast<uint32_t>(f >> 32), 0u};
         philox4x32_10(c, k0, k1);
         float u[4];
