@@ -923,7 +923,7 @@ def main():
     ap.add_argument("--serve-budget-mb", type=int, default=2048)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-backlog", type=int, default=400)
-    ap.add_argument("--epoch-iters", type=int, default=4)
+    ap.add_argument("--epoch-iters", type=int, default=8)
     ap.add_argument("--arrival-seed", type=int, default=20260)
     args = ap.parse_args()
     os.makedirs(OUT_DIR, exist_ok=True)
