@@ -358,10 +358,7 @@ def run_ours(args):
     peak_clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = MUFU_PER_CLK_PER_SM * sms * peak_clock_mhz * 1e6 / 1e12
     kname = {nd.VARIANT_QC: "qc_decode_kernel", nd.VARIANT_QC_GLOBAL: "qc_decode_kernel",
-             nd.VARIANT_QC_PAIR: "qc_pair_kernel", nd.VARIANT_QC_PAIR_GLOBAL: "qc_pair_kernel",
-             nd.VARIANT_QC_FRAMES2: "qc_frames2_kernel", nd.VARIANT_QC_FRAMES2_GLOBAL: "qc_frames2_kernel",
-             nd.VARIANT_TILE: "tile_decode_kernel", nd.VARIANT_QC_DIRECT: "qc_decode_kernel"}.get(plan.variant,
-                                                                                            "decode_kernel")
+             nd.VARIANT_TILE: "tile_decode_kernel"}.get(plan.variant, "decode_kernel")
     traffic, traffic_rec = profiled_traffic(kname)
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,

@@ -70,14 +70,8 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_VARIANT_GLOBAL 2  /* edge messages in per-CTA global-memory slots */
 #define NDGSBP_VARIANT_QC 3      /* layered QC kernel: circulant index arithmetic, no tables */
 #define NDGSBP_VARIANT_QC_GLOBAL 4 /* layered QC kernel with messages in global-memory slots */
-#define NDGSBP_VARIANT_QC_PAIR 5   /* layered QC kernel, two CNs per thread, packed FP32 arithmetic */
-#define NDGSBP_VARIANT_QC_PAIR_GLOBAL 6 /* the pair kernel with messages in global-memory slots */
+/* values 5, 6, 8, 9 and 10 are unused (INVALID) */
 #define NDGSBP_VARIANT_TILE 7      /* tile kernel: any QC window, degree <= 32, several frames per CTA */
-#define NDGSBP_VARIANT_QC_FRAMES2 8 /* layered QC kernel, two frames per thread, packed FP32 arithmetic */
-#define NDGSBP_VARIANT_QC_FRAMES2_GLOBAL 9 /* the two-frame kernel with messages in global-memory slots */
-#define NDGSBP_VARIANT_QC_DIRECT 10 /* layered QC kernel, 2-layer windows: edges off the block
-                                      columns both layers touch are written back at once, one
-                                      ordered round for the rest (same results as QC) */
 #define NDGSBP_VARIANT_RAGGED_PER_CODE 11 /* ragged launches only: every code runs its own
                                       ndgsbp_decode plan (the library's choice for it), the launches
                                       forked onto concurrent streams and joined (same results as
@@ -90,6 +84,8 @@ typedef int32_t ndgsbp_status;
 #define NDGSBP_STAT_UNDETECTED 3     /* syndrome satisfied but decoded word != transmitted word */
 #define NDGSBP_STAT_ITERATIONS 4     /* sum of iterations used */
 #define NDGSBP_STAT_UNSATISFIED 5    /* frames that stopped with a nonzero syndrome */
+#define NDGSBP_STAT_INVALID 6        /* frames not decoded: a NaN or an infinity among their LLRs
+                                        (counted here only, not in the counters above) */
 #define NDGSBP_STATS_LEN 8
 
 typedef struct ndgsbp_code ndgsbp_code;
@@ -191,7 +187,7 @@ ndgsbp_status ndgsbp_groups_from_lists(const ndgsbp_code* code, const int32_t* g
 /* Several groupings cycled by iteration -- the literal "go to Step 1" of Step 4 b), which draws
  * the groups again for every iteration: n_groupings (1..64) groupings are drawn as by
  * ndgsbp_groups_build with the seeds seed, seed + 1, ..., and iteration l of a decode uses
- * grouping (l - 1) mod n_groupings.  Decoded by the QC kernels (QC, QC_GLOBAL, QC_PAIR, TILE,
+ * grouping (l - 1) mod n_groupings.  Decoded by the QC kernels (QC, QC_GLOBAL, TILE,
  * ragged launches, serving) when every grouping is made of whole layers with one window size;
  * the other plans return UNSUPPORTED.  ndgsbp_groups_query describes grouping 0.
  * Errors: as ndgsbp_groups_build. */
@@ -218,8 +214,9 @@ ndgsbp_status ndgsbp_groups_destroy(ndgsbp_groups* groups);
  * [n_frames][W] or one [W]).  sigma^2 = 1 / (2 rate 10^(ebn0_db/10)).  Normals come from
  * Philox4x32-10 keyed by seed with counter (b, frame low, frame high, 0) for VNs 4b..4b+3,
  * u = ((x >> 9) + 1/2) 2^-23 (exact in FP32), and Box-Muller on (u0, u1) and (u2, u3) (cos
- * then sin).
- * Errors: INVALID (rate <= 0, bad dtype), CUDA. */
+ * then sin).  d_llr needs the alignment of its element type (any offset into a buffer that
+ * keeps it is accepted: 16-byte stores are used only where every row is 16-byte aligned).
+ * Errors: INVALID (rate <= 0, bad dtype, misaligned d_llr), CUDA. */
 ndgsbp_status ndgsbp_awgn_llr(const ndgsbp_code* code, int64_t n_frames, double ebn0_db,
                               double rate, uint64_t seed, const uint32_t* d_codeword_bits,
                               int32_t codeword_per_frame, void* d_llr, int32_t dtype, void* stream);
@@ -248,6 +245,10 @@ ndgsbp_status ndgsbp_workspace_size(const ndgsbp_groups* groups, const ndgsbp_pa
  * Outputs: d_hard_bits [n_frames][W], W = ceil(N/32), bit n%32 of word n/32 is d_n (required);
  * d_iters [n_frames] iterations used in 1..max_iter; d_syndrome_ok [n_frames] 1 if D H^T = 0 at
  * exit; d_posterior [n_frames][N] P_n at exit (FP32).  The last three may be NULL.
+ * A frame whose channel LLRs hold a NaN or an infinity is not decoded: its hard bits and
+ * posterior are 0, its iteration count 0 (outside 1..max_iter) and its syndrome flag 0 -- the
+ * per-frame status word the caller reads after synchronising -- and NDGSBP_STAT_INVALID counts
+ * it.  The other frames of the batch are decoded as usual.
  * d_workspace: device buffer of at least ndgsbp_workspace_size bytes, 256-byte aligned.
  * Frames are independent: a frame's result does not depend on the others in the batch.
  * Errors: INVALID, WORKSPACE, UNSUPPORTED, CUDA (launch errors; execution errors surface at
@@ -323,9 +324,10 @@ ndgsbp_status ndgsbp_ragged_destroy(ndgsbp_ragged* ragged);
  * [n_frames][N] (a representative sample: the iteration counts follow its noise level) and
  * returns the fastest in result->best: params with variant, block_threads, ctas_per_sm,
  * frames_per_cta and lanes_per_cn filled in (the other fields as given).  Candidates are the
- * library's default choice, the QC kernels at 0/1/2 CTAs per SM (single-frame, two-frame, pair
- * and direct write-back forms), and tile shapes (1, 2 or 4 lanes per CN x 1..16 frames per CTA
- * x 128..512 threads, at the default residency and at 1 CTA per SM) that the plan accepts.  Each
+ * library's default choice, the QC kernel at 0/1/2 CTAs per SM (messages in shared memory) and
+ * at 0/2/3/4 CTAs per SM (messages in global memory), and tile shapes (1, 2 or 4 lanes per CN x
+ * 1..16 frames per CTA x 128..512 threads, at the default residency and at 1 CTA per SM) that
+ * the plan accepts.  Each
  * candidate is an ordinary decode into the tuner's own scratch buffers: one untimed call, then
  * the median of three timed by CUDA events on a private stream.  Shapes with the same lanes
  * per CN give bit-identical results; more lanes per CN split a CN's edges between lanes and so
@@ -458,7 +460,9 @@ ndgsbp_status ndgsbp_ga_flood_threshold(const double* lambda, int32_t dv_max, co
  * NDGSBP_STATIC_SCRATCH_BYTES bytes inside this library, which every GPU that loads the library
  * holds until the process exits.
  *   - The first call on a device looks up the array's device address (a one-time set-up per
- *     device); make that first call before any stream capture.
+ *     device); make that first call before any stream capture.  The library keeps that address,
+ *     like the grouping tables it uploads, for the life of the process: after a device reset
+ *     (cudaDeviceReset) neither is valid, so do not reset a device while this library uses it.
  *   - The grouping's tables must already be on the device: call ndgsbp_decode_plan with the same
  *     parameters, on that device, during set-up (that call uploads them).  Otherwise INVALID.
  *   - A launch that needs more scratch than the array holds is rejected with WORKSPACE (lower

@@ -4,7 +4,8 @@
 // Shaw, SC'11) keyed by the seed with counter (b, frame low, frame high, 0) gives four 32-bit
 // words; u = ((x >> 9) + 1/2) 2^-23 is exact in FP32; Box-Muller turns (u0, u1) and (u2, u3) into
 // two normal pairs (cos, then sin); y = (1 - 2 c) + sigma z and L = (2 / sigma^2) y.  The
-// kernel writes HBM once per LLR (16-byte stores when N is a multiple of 4), but its time goes
+// kernel writes HBM once per LLR (16-byte stores for FP32 when N is a multiple of 4 and the
+// output is 16-byte aligned, element stores otherwise), but its time goes
 // to the arithmetic: the ten Philox rounds and the accurate logarithm, sine and cosine of
 // Box-Muller (about a fifth of the HBM store bandwidth on the n=2304 sweep; 2 % of its step).
 #include <cuda_bf16.h>
@@ -38,7 +39,9 @@ template <> __device__ __forceinline__ float cvt<float>(float v) { return v; }
 template <> __device__ __forceinline__ __half cvt<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-template <typename T>
+// VEC4: every row starts on a 16-byte boundary (FP32, N % 4 == 0, 16-byte aligned output), so
+// each thread's four LLRs go out as one 16-byte store.
+template <typename T, bool VEC4>
 __global__ void awgn_kernel(int N, long long n_frames, float scale, float scale_sigma, uint32_t k0,
                             uint32_t k1, const uint32_t* __restrict__ cw, int cw_per_frame, T* __restrict__ out) {
     const int nb = (N + 3) >> 2;
@@ -79,7 +82,7 @@ __global__ void awgn_kernel(int N, long long n_frames, float scale, float scale_
             L[i] = fmaf(scale_sigma, z[i], scale * x);
         }
         T* row = out + f * N;
-        if ((N & 3) == 0 && sizeof(T) == 4) {
+        if constexpr (VEC4) {
             reinterpret_cast<float4*>(row)[b] = make_float4(L[0], L[1], L[2], L[3]);
         } else {
 #pragma unroll
@@ -130,17 +133,30 @@ ndgsbp_status ndgsbp_awgn_llr(const ndgsbp_code* code, int64_t n_frames, double 
     const int threads = 256;
     const int grid = grid_for(work, threads);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (dtype != NDGSBP_F32 && dtype != NDGSBP_F16 && dtype != NDGSBP_BF16)
+        return fail(NDGSBP_ERR_INVALID, "awgn_llr: dtype must be F32, F16 or BF16");
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(d_llr);
+    const size_t esize = dtype == NDGSBP_F32 ? 4 : 2;
+    if (addr % esize) return fail(NDGSBP_ERR_INVALID, "awgn_llr: d_llr is not aligned to its element size");
+    // 16-byte stores only when every row starts on a 16-byte boundary
+    const bool vec4 = dtype == NDGSBP_F32 && (N & 3) == 0 && addr % 16 == 0;
     switch (dtype) {
         case NDGSBP_F32:
-            awgn_kernel<float><<<grid, threads, 0, s>>>(N, n_frames, scale, scale_sigma, k0, k1, d_codeword_bits,
-                                                        codeword_per_frame, static_cast<float*>(d_llr));
+            if (vec4)
+                awgn_kernel<float, true><<<grid, threads, 0, s>>>(N, n_frames, scale, scale_sigma, k0, k1,
+                                                                  d_codeword_bits, codeword_per_frame,
+                                                                  static_cast<float*>(d_llr));
+            else
+                awgn_kernel<float, false><<<grid, threads, 0, s>>>(N, n_frames, scale, scale_sigma, k0, k1,
+                                                                   d_codeword_bits, codeword_per_frame,
+                                                                   static_cast<float*>(d_llr));
             break;
         case NDGSBP_F16:
-            awgn_kernel<__half><<<grid, threads, 0, s>>>(N, n_frames, scale, scale_sigma, k0, k1, d_codeword_bits,
+            awgn_kernel<__half, false><<<grid, threads, 0, s>>>(N, n_frames, scale, scale_sigma, k0, k1, d_codeword_bits,
                                                          codeword_per_frame, static_cast<__half*>(d_llr));
             break;
         case NDGSBP_BF16:
-            awgn_kernel<__nv_bfloat16><<<grid, threads, 0, s>>>(N, n_frames, scale, scale_sigma, k0, k1,
+            awgn_kernel<__nv_bfloat16, false><<<grid, threads, 0, s>>>(N, n_frames, scale, scale_sigma, k0, k1,
                                                                 d_codeword_bits, codeword_per_frame,
                                                                 static_cast<__nv_bfloat16*>(d_llr));
             break;

@@ -119,11 +119,10 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) decode_kernel(const De
         if (f >= r.n_frames) break;
         if (r.start_ns && tid == 0) r.start_ns[f] = global_timer_ns();
         // initialisation: P_n = L_n, L_{m->n} = 0
-        for (int n = tid; n < r.N; n += nt) P[n] = load_llr(r.llr, r.llr_dtype, f * r.N + n);
         for (int e = tid; e < a.Epad; e += nt) msg[e] = from_f<MsgT>(0.f);
-        __syncthreads();
+        const bool invalid = load_frame_llrs(r, P, f);
         int it = 1, unsat = 1;
-        for (;; ++it) {
+        for (; !invalid; ++it) {
             for (int g = 0; g < a.G; ++g) {
                 const int gb = __ldg(a.grp_ptr + g), ge = __ldg(a.grp_ptr + g + 1);
                 for (int i = gb + tid; i < ge; i += nt) cn_update_entry<MAXDC, MsgT>(a, P, msg, delta, i);
@@ -150,7 +149,7 @@ __global__ void __launch_bounds__(max_threads_for(MAXDC)) decode_kernel(const De
                 if (csr >= 0) r.msgs_out[f * r.E + csr] = to_f(msg[e]) * kLn2;
             }
         }
-        write_frame_outputs(r, P, f, it, unsat, &s_err);
+        write_frame_outputs(r, P, f, it, unsat, &s_err, 1, invalid);
         __syncthreads();
     }
 }
@@ -252,7 +251,6 @@ static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     BlobBuilder b;
     const size_t o_tab = b.add(Q.edge_tab), o_deg = b.add(Q.layer_deg), o_off = b.add(Q.layer_off);
     const size_t o_gl = b.add(Q.group_layers), o_csr = b.add(Q.csr_of), o_str = b.add(Q.layer_stride);
-    const size_t o_w2 = b.add(Q.win2);
     void* blob = nullptr;
     ndgsbp_status st = b.upload(&blob);
     if (st) return st;
@@ -264,7 +262,6 @@ static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     D.layer_off = reinterpret_cast<const int32_t*>(p + o_off);
     D.group_layers = reinterpret_cast<const int32_t*>(p + o_gl);
     D.csr_of = reinterpret_cast<const int32_t*>(p + o_csr);
-    D.win2 = Q.win2.empty() ? nullptr : reinterpret_cast<const int32_t*>(p + o_w2);
     return NDGSBP_OK;
 }
 
@@ -344,7 +341,6 @@ struct Plan {
     int tile_tpc = 1, tile_le = 1, tile_slots = 1, tile_slot_bytes = 0, tile_p_bytes = 0, tile_m_bytes = 0;
     int tile_delta_stride = 1, tile_frames = 1, tile_table_bytes = 0, n_tiles = 0;
     bool msg_smem = false, delta_smem = false;
-    bool qc_w2 = false;   // QC kernel with the 2-layer window tables
     const Layout* L = nullptr;
     const DeviceLayout* D = nullptr;
     const QcLayout* Q = nullptr;
@@ -366,8 +362,12 @@ static ndgsbp_status validate_params(const ndgsbp_params* p) {
         return fail(NDGSBP_ERR_INVALID, "frames_per_cta must be in [0, 16]");
     if (p->lanes_per_cn != 0 && p->lanes_per_cn != 1 && p->lanes_per_cn != 2 && p->lanes_per_cn != 4)
         return fail(NDGSBP_ERR_INVALID, "lanes_per_cn must be 0, 1, 2 or 4");
-    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_QC_DIRECT)
+    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_RAGGED_PER_CODE ||
+        (p->variant > NDGSBP_VARIANT_QC_GLOBAL && p->variant < NDGSBP_VARIANT_TILE) ||
+        (p->variant > NDGSBP_VARIANT_TILE && p->variant < NDGSBP_VARIANT_RAGGED_PER_CODE))
         return fail(NDGSBP_ERR_INVALID, "unknown variant %d", p->variant);
+    if (p->variant == NDGSBP_VARIANT_RAGGED_PER_CODE)
+        return fail(NDGSBP_ERR_INVALID, "variant RAGGED_PER_CODE applies to ragged launches only");
     return NDGSBP_OK;
 }
 
@@ -396,52 +396,8 @@ static ndgsbp_status finish_grid(const void* fn, int threads, size_t smem, const
     return NDGSBP_OK;
 }
 
-// Two-frames-per-thread QC kernel: interleaved posteriors and messages, so every per-frame
-// buffer doubles; persistent CTAs take frames two at a time.
-static ndgsbp_status make_qc_frames2_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
-                                          const QcLayout& Q, int maxdc, bool spec, bool force_global,
-                                          const DeviceInfo& di, Plan& plan, bool* ok, bool allow_upload) {
-    if (!spec || maxdc > 16 || Q.n_groupings > 1) return NDGSBP_OK;
-    const int active = Q.window * Q.Z;
-    const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
-    if (threads < active || threads > qc_frames2_max_threads(maxdc)) return NDGSBP_OK;
-    const size_t budget = static_cast<size_t>(di.smem_optin) - 96;
-    const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 8);
-    const size_t m_bytes = align16(static_cast<size_t>(Q.msg_slots) * 2 * msg_size(p->msg_dtype));
-    const size_t t_bytes = qc_table_bytes(Q);
-    if (p_bytes + t_bytes > budget) return NDGSBP_OK;
-    const bool msg_smem = !force_global && p_bytes + m_bytes + t_bytes <= budget;
-    const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
-    QcKernelFn fn = pick_qc_frames2_kernel(p->msg_dtype, maxdc, msg_smem);
-    if (!fn) return NDGSBP_OK;
-    int per_sm = 0;
-    int64_t grid = 0;
-    ndgsbp_status st = finish_grid(reinterpret_cast<const void*>(fn), threads, smem, p, (n_frames + 1) / 2, di, per_sm,
-                                   grid);
-    if (st) return st;
-    st = device_qc(g, flood, plan.Q, plan.DQ, allow_upload);
-    if (st) return st;
-    plan.qc = true;
-    plan.qfn = fn;
-    plan.msg_smem = msg_smem;
-    ndgsbp_plan& o = plan.pub;
-    o.variant = msg_smem ? NDGSBP_VARIANT_QC_FRAMES2 : NDGSBP_VARIANT_QC_FRAMES2_GLOBAL;
-    o.block_threads = threads;
-    o.grid = static_cast<int32_t>(grid);
-    o.ctas_per_sm = per_sm;
-    o.max_row_degree = maxdc;
-    o.delta_in_smem = 0;
-    o.smem_bytes = static_cast<int64_t>(smem);
-    o.workspace_bytes = static_cast<int64_t>(
-        kHeaderBytes + (msg_smem ? 0 : align256(static_cast<size_t>(grid) * Q.msg_slots * 2 * msg_size(p->msg_dtype))));
-    o.stored_edges = Q.msg_slots;
-    o.edge_updates_per_iter = flood ? g.code->E : g.edge_updates;
-    *ok = true;
-    return NDGSBP_OK;
-}
-
-// Layered QC kernel plan, when the grouping is made of whole layers and a window fits a CTA.
-// QC / QC_GLOBAL (and AUTO) run the single-CN kernel, QC_PAIR / QC_PAIR_GLOBAL the pair kernel.
+// Layered QC kernel plan, when the grouping is made of whole layers and a window fits a CTA
+// with one thread per CN (QC, QC_GLOBAL and AUTO).
 static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
                                   const DeviceInfo& di, Plan& plan, bool* ok, bool allow_upload = true) {
     *ok = false;
@@ -450,48 +406,25 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     const int maxdc = degree_bound(Q.max_deg);
     if (!maxdc) return NDGSBP_OK;
     const bool spec = qc_degrees_specialised(Q, maxdc);
-    const bool want_single = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL ||
-                             p->variant == NDGSBP_VARIANT_QC_DIRECT;
-    const bool want_pair = p->variant == NDGSBP_VARIANT_QC_PAIR || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL;
-    const bool want_f2 = p->variant == NDGSBP_VARIANT_QC_FRAMES2 || p->variant == NDGSBP_VARIANT_QC_FRAMES2_GLOBAL;
-    const bool force_global = p->variant == NDGSBP_VARIANT_QC_GLOBAL || p->variant == NDGSBP_VARIANT_QC_PAIR_GLOBAL ||
-                              p->variant == NDGSBP_VARIANT_QC_FRAMES2_GLOBAL;
-    if (want_f2) return make_qc_frames2_plan(g, p, n_frames, flood, Q, maxdc, spec, force_global, di, plan, ok,
-                                             allow_upload);
-    const int active_pair = Q.window * (Q.Z / 2);
-    const bool pair_ok = spec && Q.Z % 2 == 0 && (p->block_threads ? p->block_threads : (active_pair + 31) / 32 * 32) <=
-                                                      qc_pair_max_threads(maxdc);
-    // AUTO keeps the single-CN kernel: on GB300 it is the faster of the two for the codes
-    // measured (the pair kernel halves the FP instructions but also the resident warps).
-    bool pair = false;
-    if (want_pair) {
-        if (!pair_ok) return NDGSBP_OK;
-        pair = true;
-    }
-    (void)want_single;
-    const int active = pair ? active_pair : Q.window * Q.Z;
+    const bool force_global = p->variant == NDGSBP_VARIANT_QC_GLOBAL;
+    const int active = Q.window * Q.Z;
     const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
-    if (threads < active || threads > (pair ? qc_pair_max_threads(maxdc) : max_threads_for(maxdc))) return NDGSBP_OK;
-    // direct write-back for 2-layer windows only on request: on GB300 the two-round kernel is
-    // faster (3.37 vs 3.05 Gbit/s on the n=2304 sweep) although it runs one barrier more
-    const bool want_direct = p->variant == NDGSBP_VARIANT_QC_DIRECT;
-    if (want_direct && !(spec && Q.window == 2 && !Q.win2.empty() && Q.n_groupings == 1)) return NDGSBP_OK;
-    const bool w2 = !pair && want_direct;
+    if (threads < active || threads > max_threads_for(maxdc)) return NDGSBP_OK;
     const size_t budget = static_cast<size_t>(di.smem_optin) - 64;
     const size_t p_bytes = align16(static_cast<size_t>(g.code->N) * 4);
     const size_t m_bytes = align16(static_cast<size_t>(Q.msg_slots) * msg_size(p->msg_dtype));
-    const size_t t_bytes = qc_table_bytes(Q, w2);
+    const size_t t_bytes = qc_table_bytes(Q);
     if (p_bytes + t_bytes > budget) return NDGSBP_OK;
     const bool msg_smem = !force_global && p_bytes + m_bytes + t_bytes <= budget;
     const size_t smem = p_bytes + t_bytes + (msg_smem ? m_bytes : 0);
     // 16-bit messages halve the shared memory of a frame: when 6 CTAs fit, use the instance
     // compiled for 6 resident CTAs (56 registers) instead of the 64-register one (5 CTAs)
     QcKernelFn fn = nullptr;
-    const bool occ_ok = !pair && !w2 && spec && maxdc == 8 && msg_smem && p->msg_dtype != NDGSBP_F32 &&
+    const bool occ_ok = spec && maxdc == 8 && msg_smem && p->msg_dtype != NDGSBP_F32 &&
                         threads <= qc_occ_threads() && (p->ctas_per_sm == 0 || p->ctas_per_sm >= 6) &&
                         6 * (smem + static_cast<size_t>(di.smem_reserved) + 1024) <= static_cast<size_t>(di.smem_sm);
-    if (occ_ok) fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair, w2, true);
-    if (!fn) fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, pair, w2);
+    if (occ_ok) fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec, true);
+    if (!fn) fn = pick_qc_kernel(p->msg_dtype, maxdc, msg_smem, spec);
     if (!fn) return NDGSBP_OK;
     int per_sm = 0;
     int64_t grid = 0;
@@ -502,10 +435,8 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     plan.qc = true;
     plan.qfn = fn;
     plan.msg_smem = msg_smem;
-    plan.qc_w2 = w2;
     ndgsbp_plan& o = plan.pub;
-    o.variant = pair ? (msg_smem ? NDGSBP_VARIANT_QC_PAIR : NDGSBP_VARIANT_QC_PAIR_GLOBAL)
-                     : (w2 ? NDGSBP_VARIANT_QC_DIRECT : (msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL));
+    o.variant = msg_smem ? NDGSBP_VARIANT_QC : NDGSBP_VARIANT_QC_GLOBAL;
     o.block_threads = threads;
     o.grid = static_cast<int32_t>(grid);
     o.ctas_per_sm = per_sm;
@@ -785,7 +716,7 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
         std::memset(&a, 0, sizeof(a));
         fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior,
                  extras);
-        fill_qc_args(a, *plan.Q, *plan.DQ, plan.msg_smem ? nullptr : ws + kHeaderBytes, plan.qc_w2);
+        fill_qc_args(a, *plan.Q, *plan.DQ, plan.msg_smem ? nullptr : ws + kHeaderBytes);
         plan.qfn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
     } else {
         const Layout& L = *plan.L;
@@ -836,7 +767,7 @@ ndgsbp_status qc_serve_plan(const Groups& g, const ndgsbp_params* p, QcServePlan
     Plan plan;
     bool qok = false;
     st = make_qc_plan(g, &q, int64_t{1} << 30, /*flood=*/false, di, plan, &qok);
-    if (st || !qok || plan.qc_w2) return st;
+    if (st || !qok) return st;
     const int maxdc = plan.pub.max_row_degree;
     if (!qc_degrees_specialised(*plan.Q, maxdc)) return NDGSBP_OK;
     QcKernelFn fn = pick_qc_serve_kernel(q.msg_dtype, maxdc, plan.msg_smem);
@@ -847,7 +778,7 @@ ndgsbp_status qc_serve_plan(const Groups& g, const ndgsbp_params* p, QcServePlan
     out->msg_smem = plan.msg_smem;
     out->msg_slots = plan.Q->msg_slots;
     std::memset(&out->args, 0, sizeof(out->args));
-    fill_qc_args(out->args, *plan.Q, *plan.DQ, nullptr, false);
+    fill_qc_args(out->args, *plan.Q, *plan.DQ, nullptr);
     *ok = true;
     return NDGSBP_OK;
 }
@@ -882,6 +813,17 @@ ndgsbp_status plan_enqueue(const Groups& g, const Plan& plan, const ndgsbp_param
 }  // namespace ndgsbp
 
 using namespace ndgsbp;
+
+// Element alignment of the caller's buffers (the kernels read and write them element by element).
+static ndgsbp_status check_alignment(const char* who, const void* d_llr, int32_t llr_dtype, const uint32_t* d_hard_bits,
+                                     const int32_t* d_iters, const float* d_posterior) {
+    const size_t le = llr_dtype == NDGSBP_F64 ? 8 : llr_dtype == NDGSBP_F32 ? 4 : 2;
+    if (reinterpret_cast<uintptr_t>(d_llr) % le) return fail(NDGSBP_ERR_INVALID, "%s: d_llr not aligned to its element", who);
+    if (reinterpret_cast<uintptr_t>(d_hard_bits) % 4 || reinterpret_cast<uintptr_t>(d_iters) % 4 ||
+        reinterpret_cast<uintptr_t>(d_posterior) % 4)
+        return fail(NDGSBP_ERR_INVALID, "%s: output buffers must be 4-byte aligned", who);
+    return NDGSBP_OK;
+}
 
 extern "C" {
 
@@ -918,6 +860,8 @@ ndgsbp_status ndgsbp_decode_ex(const ndgsbp_groups* groups, const ndgsbp_params*
     if (llr_dtype != NDGSBP_F32 && llr_dtype != NDGSBP_F64 && llr_dtype != NDGSBP_F16 && llr_dtype != NDGSBP_BF16)
         return fail(NDGSBP_ERR_INVALID, "decode: unknown llr_dtype %d", llr_dtype);
     if (n_frames > 0 && (!d_llr || !d_hard_bits)) return fail(NDGSBP_ERR_INVALID, "decode: d_llr and d_hard_bits are required");
+    ndgsbp_status sa = check_alignment("decode", d_llr, llr_dtype, d_hard_bits, d_iters, d_posterior);
+    if (sa) return sa;
     const Groups& g = groups->g;
     Plan plan;
     ndgsbp_status st = make_plan(g, params, n_frames, plan);
@@ -955,6 +899,8 @@ ndgsbp_status ndgsbp_decode_static(const ndgsbp_groups* groups, const ndgsbp_par
         return fail(NDGSBP_ERR_INVALID, "decode_static: unknown llr_dtype %d", llr_dtype);
     if (n_frames > 0 && (!d_llr || !d_hard_bits))
         return fail(NDGSBP_ERR_INVALID, "decode_static: d_llr and d_hard_bits are required");
+    ndgsbp_status sa = check_alignment("decode_static", d_llr, llr_dtype, d_hard_bits, d_iters, d_posterior);
+    if (sa) return sa;
     const Groups& g = groups->g;
     Plan plan;
     ndgsbp_status st = make_plan(g, params, n_frames, plan, /*allow_upload=*/false);

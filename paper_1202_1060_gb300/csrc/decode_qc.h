@@ -16,7 +16,6 @@ struct QcArgs {
     const int32_t* group_layers;  // [G][window]
     const int32_t* csr_of;        // [msg_slots] CSR position of each stored message, -1 = padding
     void* ws_msgs;                // per-CTA message slots when messages are not in shared memory
-    const int2* win2;             // [G][2][maxdeg] block columns shared by 2-layer windows, or null
     int n_groupings;              // group -> layer tables cycled by iteration (group_layers holds all)
     // serving instances: frame i of the launch (r.n_frames of them) is pool slot serve_list[i],
     // whose decoding state persists in the pool between launches (as for the tile kernel)
@@ -32,20 +31,14 @@ struct QcArgs {
 
 typedef void (*QcKernelFn)(const QcArgs);
 
-// w2: the 2-layer-window instance (direct write-back off shared block columns; needs win2).
 // occ6: the instance compiled for 6 resident CTAs of at most qc_occ_threads() threads (16-bit
 // messages in shared memory, degree <= 8); nullptr when it does not apply.
-QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool pair, bool w2 = false,
-                          bool occ6 = false);
+QcKernelFn pick_qc_kernel(int msg_dtype, int maxdc, bool msg_smem, bool spec, bool occ6 = false);
 int qc_occ_threads();
-// Two frames per thread (decode_qc2.cu); degree-specialised codes with MAXDC 8 or 16 only.
-QcKernelFn pick_qc_frames2_kernel(int msg_dtype, int maxdc, bool msg_smem);
-int qc_frames2_max_threads(int maxdc);
 bool qc_degrees_specialised(const QcLayout& Q, int maxdc);
 // Serving instance of the single-CN kernel (decode_qc_serve.cu): degree-specialised codes with
 // MAXDC 8 or 16; nullptr otherwise.
 QcKernelFn pick_qc_serve_kernel(int msg_dtype, int maxdc, bool msg_smem);
-int qc_pair_max_threads(int maxdc);
 // The serving form of a grouping's QC plan (server pools): the single-CN kernel's serving
 // instance with the block, shared bytes and table arguments ndgsbp_decode would use for the
 // grouping (variant QC, the library's shape).  *ok = false when that plan does not apply (window
@@ -60,8 +53,8 @@ struct QcServePlan {
 };
 ndgsbp_status qc_serve_plan(const Groups& g, const ndgsbp_params* p, QcServePlan* out, bool* ok);
 
-// Shared bytes of a launch's tables (w2: with the 2-layer window masks and change buffer).
-size_t qc_table_bytes(const QcLayout& Q, bool w2 = false);
-void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs, bool w2 = false);
+// Shared bytes of a launch's tables.
+size_t qc_table_bytes(const QcLayout& Q);
+void fill_qc_args(QcArgs& a, const QcLayout& Q, const DeviceQc& D, void* ws_msgs);
 
 }  // namespace ndgsbp

@@ -10,11 +10,11 @@ template <typename MsgT>
 static QcKernelFn pick_serve(int maxdc, bool msg_smem) {
     switch (maxdc) {
         case 8:
-            return msg_smem ? qc_decode_kernel<MsgT, true, 8, true, false, 0, true>
-                            : qc_decode_kernel<MsgT, false, 8, true, false, 0, true>;
+            return msg_smem ? qc_decode_kernel<MsgT, true, 8, true, 0, true>
+                            : qc_decode_kernel<MsgT, false, 8, true, 0, true>;
         case 16:
-            return msg_smem ? qc_decode_kernel<MsgT, true, 16, true, false, 0, true>
-                            : qc_decode_kernel<MsgT, false, 16, true, false, 0, true>;
+            return msg_smem ? qc_decode_kernel<MsgT, true, 16, true, 0, true>
+                            : qc_decode_kernel<MsgT, false, 16, true, 0, true>;
         default: return nullptr;
     }
 }

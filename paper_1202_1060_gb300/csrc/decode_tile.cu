@@ -100,6 +100,7 @@ struct TileShared {
     int epoch[kMaxSlots];
     int gofs[kMaxSlots];        // offset of the slot's grouping for its next iteration in the group tables
     unsigned unsat[kMaxSlots];
+    int bad[kMaxSlots];         // the slot's frame had a NaN or an infinity among its LLRs (see load_frame)
     unsigned err;
     int tile, code, cur_code, next, end, active;
 };
@@ -144,13 +145,17 @@ __device__ __forceinline__ void fill_slot(TileShared& sh, const TileCode& C, int
 }
 
 // Load frame f into slot s (all threads): a fresh frame starts from P = L, messages 0; in
-// serving mode a running frame resumes from its saved state.
+// serving mode a running frame resumes from its saved state.  A fresh frame whose LLRs hold a
+// NaN or an infinity starts from P = 0 instead and is marked bad: its messages stay 0, it
+// retires after its first iteration and its outputs mark it invalid (write_frame_outputs).
 template <typename MsgT, bool SERVE>
-__device__ __forceinline__ void load_frame(const TileCode& C, unsigned char* base, int s, long long f, int saved_iter) {
+__device__ __forceinline__ void load_frame(const TileCode& C, TileShared& sh, unsigned char* base, int s, long long f,
+                                           int saved_iter) {
     const RunArgs& r = C.r;
     const int tid = threadIdx.x, nt = blockDim.x;
     float* P = reinterpret_cast<float*>(base);
     MsgT* msg = slot_msgs<MsgT, SERVE>(C, base, s, f);
+    if (tid == 0) sh.bad[s] = 0;
     if (SERVE && saved_iter > 0) {
         const float* sp = C.state_P + static_cast<size_t>(f) * r.N;
         for (int n = tid; n < r.N; n += nt) P[n] = sp[n];
@@ -161,8 +166,8 @@ __device__ __forceinline__ void load_frame(const TileCode& C, unsigned char* bas
         return;
     }
     if (r.start_ns && tid == 0) r.start_ns[f] = global_timer_ns();
-    for (int n = tid; n < r.N; n += nt) P[n] = load_llr(r.llr, r.llr_dtype, f * r.N + n);
     for (int e = tid; e < C.msg_slots; e += nt) msg[e] = from_f<MsgT>(0.f);
+    if (load_frame_llrs(r, P, f) && tid == 0) sh.bad[s] = 1;
 }
 
 // Serving mode: save a running frame's state at the end of its share of the launch.
@@ -350,7 +355,7 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
             const long long f = sh.frame[s];
             if (f < 0) continue;
             const int it = sh.iter[s];
-            const bool done = (r.early_stop && !sh.unsat[s]) || it >= r.max_iter;
+            const bool done = (r.early_stop && !sh.unsat[s]) || it >= r.max_iter || sh.bad[s];
             const bool park = SERVE && !done && sh.epoch[s] >= C.epoch_iters;
             if (!done && !park) continue;
             unsigned char* base = slots_base + static_cast<size_t>(s) * C.slot_bytes;
@@ -371,7 +376,7 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
                         ebase += Z * d;
                     }
                 }
-                write_frame_outputs(r, P, f, it, sh.unsat[s] ? 1 : 0, &sh.err);
+                write_frame_outputs(r, P, f, it, sh.unsat[s] ? 1 : 0, &sh.err, 1, sh.bad[s] != 0);
                 if (SERVE && tid == 0) {
                     C.state_flag[f] = kSlotDone;
                     if (C.done_list) C.done_list[atomicAdd(C.done_count, 1)] = static_cast<int>(f);
@@ -384,7 +389,7 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
             if (tid == 0) fill_slot<SERVE>(sh, C, s);
             __syncthreads();
             const long long nf = sh.frame[s];
-            if (nf >= 0) load_frame<MsgT, SERVE>(C, base, s, nf, sh.iter[s]);
+            if (nf >= 0) load_frame<MsgT, SERVE>(C, sh, base, s, nf, sh.iter[s]);
             __syncthreads();
         }
         if (tid == 0) {
@@ -452,7 +457,7 @@ __global__ void __launch_bounds__(1024) tile_decode_kernel(const TileArgs a) {
         for (int s = 0; s < C.slots; ++s) {
             const long long f = sh.frame[s];
             if (f < 0) continue;
-            load_frame<MsgT, SERVE>(C, slots_base + static_cast<size_t>(s) * C.slot_bytes, s, f, sh.iter[s]);
+            load_frame<MsgT, SERVE>(C, sh, slots_base + static_cast<size_t>(s) * C.slot_bytes, s, f, sh.iter[s]);
         }
         __syncthreads();
         run_tile<MsgT, SERVE, LE, REGB>(C, tab, slots_base, sh);

@@ -76,14 +76,37 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.69314718055994531f;
 
-// Channel LLR i of the input, in log2 units.
-__device__ __forceinline__ float load_llr(const void* p, int dtype, long long i) {
+// Channel LLR i of the input, in log2 units.  A NaN or an infinity sets `bad` (the frame is then
+// not decoded: see load_frame_llrs).
+__device__ __forceinline__ float load_llr(const void* p, int dtype, long long i, bool& bad) {
+    float v;
     switch (dtype) {
-        case NDGSBP_F64: return static_cast<float>(static_cast<const double*>(p)[i]) * kLog2e;   // FP32 first
-        case NDGSBP_F16: return __half2float(static_cast<const __half*>(p)[i]) * kLog2e;
-        case NDGSBP_BF16: return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]) * kLog2e;
-        default: return static_cast<const float*>(p)[i] * kLog2e;
+        case NDGSBP_F64: {
+            const double d = static_cast<const double*>(p)[i];
+            bad |= !isfinite(d);
+            v = static_cast<float>(d);   // FP32 first
+            break;
+        }
+        case NDGSBP_F16: v = __half2float(static_cast<const __half*>(p)[i]); break;
+        case NDGSBP_BF16: v = __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]); break;
+        default: v = static_cast<const float*>(p)[i]; break;
     }
+    bad |= !isfinite(v);
+    return v * kLog2e;
+}
+
+// P[n] = L_n (log2 units) for the N channel LLRs of frame f (all threads; ends with a barrier).
+// Returns, in every thread, whether any of them is a NaN or an infinity; such a frame gets P = 0
+// (all messages stay 0 and it retires after one iteration) and its outputs mark it invalid
+// (write_frame_outputs with invalid = true).
+__device__ __forceinline__ bool load_frame_llrs(const RunArgs& r, float* __restrict__ P, long long f) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    bool bad = false;
+    for (int n = tid; n < r.N; n += nt) P[n] = load_llr(r.llr, r.llr_dtype, f * r.N + n, bad);
+    if (!__syncthreads_or(bad)) return false;
+    for (int n = tid; n < r.N; n += nt) P[n] = 0.f;
+    __syncthreads();
+    return true;
 }
 
 // Eq. (1) on the d <= MAXDC edges of one CN, in the positive-pair tanh-product form.
@@ -147,9 +170,15 @@ __device__ __forceinline__ long long next_frame(const RunArgs& r, long long* slo
 
 // Frame epilogue: hard decisions (packed), optional posterior, per-frame outputs and the fused
 // statistics (errors against the transmitted word, iteration histogram, timestamps).  The
-// frame's posterior of VN n is P[n * pstride] (pstride 2 when two frames are interleaved).
+// frame's posterior of VN n is P[n * pstride].  invalid: the frame's channel LLRs held a NaN or
+// an infinity (P = 0): iteration count 0, syndrome flag 0, counted in NDGSBP_STAT_INVALID only.
 __device__ __forceinline__ void write_frame_outputs(const RunArgs& a, const float* __restrict__ P, long long f,
-                                                    int iters, int unsat, unsigned* s_err, int pstride = 1) {
+                                                    int iters, int unsat, unsigned* s_err, int pstride = 1,
+                                                    bool invalid = false) {
+    if (invalid) {
+        iters = 0;
+        unsat = 1;
+    }
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int W = a.W;
     unsigned err = 0u;
@@ -172,7 +201,10 @@ __device__ __forceinline__ void write_frame_outputs(const RunArgs& a, const floa
     if (tid == 0) {
         if (a.iters) a.iters[f] = iters;
         if (a.synd_ok) a.synd_ok[f] = unsat ? 0 : 1;
-        if (a.stats) {
+        if (a.stats && invalid) {
+            atomicAdd(a.stats + NDGSBP_STAT_INVALID, 1ull);
+            *s_err = 0u;
+        } else if (a.stats) {
             const unsigned e = *s_err;
             atomicAdd(a.stats + NDGSBP_STAT_FRAMES, 1ull);
             atomicAdd(a.stats + NDGSBP_STAT_ITERATIONS, static_cast<unsigned long long>(iters));
@@ -184,7 +216,7 @@ __device__ __forceinline__ void write_frame_outputs(const RunArgs& a, const floa
             if (unsat) atomicAdd(a.stats + NDGSBP_STAT_UNSATISFIED, 1ull);
             *s_err = 0u;
         }
-        if (a.iter_hist) atomicAdd(a.iter_hist + iters, 1ull);
+        if (a.iter_hist && !invalid) atomicAdd(a.iter_hist + iters, 1ull);
         if (a.retire_ns) a.retire_ns[f] = global_timer_ns();
     }
 }

@@ -342,30 +342,6 @@ void compile_qc_layout(const Code& c, const std::vector<int32_t>& gp, const std:
     if (window < 1 || window > 1024 / 32) return;   // at most 32 layers per group for the kernel
     Q.window = window;
     Q.ok = true;
-    // 2-layer windows: which block columns the two layers share, and for each shared one the
-    // position-0 CN that meets a position-1 CN on the same VN (c0 = c1 + s_1 - s_0 mod Z)
-    if (window == 2) {
-        const size_t md = Q.max_deg;
-        Q.win2.assign(static_cast<size_t>(G) * 2 * md * 2, 0);
-        for (int g = 0; g < G; ++g) {
-            const int la = Q.group_layers[2 * g], lb = Q.group_layers[2 * g + 1];
-            if (la == lb) {
-                Q.win2.clear();
-                break;
-            }
-            const auto& A = circ[la];
-            const auto& B = circ[lb];
-            for (size_t kb = 0; kb < B.size(); ++kb) {
-                int k0 = -1;
-                for (size_t ka = 0; ka < A.size(); ++ka)
-                    if (A[ka].first == B[kb].first) k0 = static_cast<int>(ka);
-                int32_t* e1 = &Q.win2[((static_cast<size_t>(g) * 2 + 1) * md + kb) * 2];
-                e1[0] = k0;
-                e1[1] = k0 >= 0 ? ((B[kb].second - A[k0].second) % Z + Z) % Z : 0;
-                if (k0 >= 0) Q.win2[((static_cast<size_t>(g) * 2) * md + k0) * 2] = 1;
-            }
-        }
-    }
 }
 
 const Layout& flood_layout(const Groups& g) {

@@ -82,10 +82,6 @@ struct QcLayout {
     int n_groupings = 1;                // groupings cycled by iteration (all with this window)
     std::vector<int32_t> group_layers;  // [n_groupings][G][window] layer ids in group order
     std::vector<int32_t> csr_of;        // [msg_slots] CSR position of message layer_off[l] + c S_l + k, -1 = pad
-    // Windows of 2 layers: [G][2][max_deg][2].  Position 0, edge k: (1 if the other layer of the
-    // window has an edge in the same block column, 0).  Position 1, edge k: (edge k0 of the
-    // position-0 layer in the same block column or -1, (s_1 - s_0) mod Z).  Empty otherwise.
-    std::vector<int32_t> win2;
 };
 
 // Device copy of a QcLayout.
@@ -97,7 +93,6 @@ struct DeviceQc {
     const int32_t* layer_off = nullptr;
     const int32_t* group_layers = nullptr;
     const int32_t* csr_of = nullptr;
-    const int32_t* win2 = nullptr;   // null when the layout has no 2-layer window table
 };
 
 struct Groups {

@@ -31,60 +31,6 @@ __device__ __forceinline__ void qc_phase_a(const int2* __restrict__ et, int c, i
     });
 }
 
-// Phase A for a window of 2 layers, with the write-back of every edge whose block column the
-// other layer of the window does not touch done at once: that VN is read by this CN alone in
-// this group, so P_n + change is final.  Of an edge in a shared block column, position 0
-// leaves its change in dx for the position-1 CN on the same VN, which adds both in phase B in
-// position order ((P + change_0) + change_1, the order of the two-round write-back), so results
-// do not change.
-template <int D, int MAXDC, typename MsgT, bool POS1>
-__device__ __forceinline__ void qc_phase_a_w2(const int2* __restrict__ et, unsigned shared, int c, int c4,
-                                              int Z4, float* __restrict__ P, MsgT* __restrict__ m,
-                                              float* __restrict__ dxc, float lim, int (&vb)[MAXDC],
-                                              float (&dl)[MAXDC]) {
-    static_assert(D <= MAXDC, "degree above the bound");
-    float t[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        vb[k] = qc_vb(et[k], c, c4, Z4);
-        t[k] = at_byte(P, vb[k]) - to_f(m[k]);
-    }
-    // the old message is read again from m[k] instead of held in a register (this path keeps
-    // more values live than the two-round one)
-    check_node_update<D>(t, D, lim, [&](int k, float val) {
-        const MsgT q = from_f<MsgT>(val);
-        const float d = to_f(q) - to_f(m[k]);
-        m[k] = q;
-        if ((shared >> k) & 1u) {
-            if (POS1)
-                dl[k] = d;
-            else
-                dxc[k] = d;
-        } else {
-            at_byte(P, vb[k]) += d;
-        }
-    });
-}
-
-// Phase B of a 2-layer window: position-1 CN c adds, on each shared VN, the position-0 change
-// (from dx) and then its own (kept in dl).  w2 (global memory, read through L1) gives, per
-// shared edge k, the position-0 edge k0 on the same block column and the CN offset s_1 - s_0.
-template <int D, int MAXDC>
-__device__ __forceinline__ void qc_phase_b_w2(const int2* __restrict__ et, const int2* __restrict__ w2, unsigned shared,
-                                              int c, int c4, int Z, int Z4, int dxs, float* __restrict__ P,
-                                              const float* __restrict__ dx, const float (&dl)[MAXDC]) {
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if ((shared >> k) & 1u) {
-            const int2 e = __ldg(w2 + k);
-            int c0 = c + e.y;
-            c0 -= c0 >= Z ? Z : 0;
-            float& p = at_byte(P, qc_vb(et[k], c, c4, Z4));
-            p = (p + dx[c0 * dxs + e.x]) + dl[k];
-        }
-    }
-}
-
 template <int MAXDC, typename MsgT>
 __device__ __forceinline__ void qc_phase_a_any(const int2* __restrict__ et, int c, int c4, int Z4, int d,
                                                float* __restrict__ P, MsgT* __restrict__ m, float lim,
@@ -130,9 +76,6 @@ struct QcSmem {
     int* loff;
     int* glay;
     int4* gtab;         // per (grouping, group, position): (l maxdeg, d_l, layer_off[l], layer_stride[l])
-    unsigned* w2mask;   // [G][2] bit k: edge k of that window position is on a shared block column
-    float* dx;   // [Z][dxs] position-0 changes on shared block columns
-    int dxs;     // odd stride >= maxdeg
 };
 
 template <typename MsgT, bool MSG_SMEM>
@@ -155,22 +98,7 @@ __device__ __forceinline__ QcSmem qc_smem_layout(unsigned char* smem, const QcAr
     s.glay = reinterpret_cast<int*>(smem + off);
     off += (static_cast<size_t>(gw) * 4 + 15) & ~static_cast<size_t>(15);
     s.gtab = reinterpret_cast<int4*>(smem + off);
-    off += static_cast<size_t>(gw) * 16;
-    s.dxs = a.maxdeg | 1;
-    s.w2mask = reinterpret_cast<unsigned*>(smem + off);
-    if (a.win2) off += (static_cast<size_t>(a.G) * 2 * 4 + 15) & ~static_cast<size_t>(15);
-    s.dx = reinterpret_cast<float*>(smem + off);
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (a.win2) {
-        for (int i = tid; i < a.G * 2; i += nt) {
-            unsigned mk = 0u;
-            for (int k = 0; k < a.maxdeg; ++k) {
-                const int x = a.win2[i * a.maxdeg + k].x;
-                mk |= ((i & 1) ? x >= 0 : x != 0) ? 1u << k : 0u;
-            }
-            s.w2mask[i] = mk;
-        }
-    }
     for (int i = tid; i < a.nl * a.maxdeg; i += nt) s.tab[i] = a.edge_tab[i];
     for (int i = tid; i < a.nl; i += nt) {
         s.ldeg[i] = a.layer_deg[i];
@@ -185,13 +113,15 @@ __device__ __forceinline__ QcSmem qc_smem_layout(unsigned char* smem, const QcAr
     return s;
 }
 
+// Start frame f: P = L, messages 0 (all threads; ends with a barrier).  Returns whether the
+// frame's LLRs hold a NaN or an infinity (see load_frame_llrs).
 template <typename MsgT>
-__device__ __forceinline__ void qc_frame_begin(const QcArgs& a, const QcSmem& s, MsgT* msg, long long f) {
+__device__ __forceinline__ bool qc_frame_begin(const QcArgs& a, const QcSmem& s, MsgT* msg, long long f) {
     const RunArgs& r = a.r;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (r.start_ns && tid == 0) r.start_ns[f] = global_timer_ns();
-    for (int n = tid; n < r.N; n += nt) s.P[n] = load_llr(r.llr, r.llr_dtype, f * r.N + n);
     for (int e = tid; e < a.msg_slots; e += nt) msg[e] = from_f<MsgT>(0.f);
+    return load_frame_llrs(r, s.P, f);
 }
 
 template <typename MsgT>
@@ -212,7 +142,7 @@ constexpr int kOccThreads = 192;
 // staged LLRs, a running one resumes from its saved posterior and messages; a frame runs until
 // it retires (zero syndrome or I_max: outputs written, slot marked done and listed) or has run
 // epoch_iters iterations in this launch (state saved, slot stays running).
-template <typename MsgT, bool MSG_SMEM, int MAXDC, bool SPEC, bool W2, int OCC = 0, bool SERVE = false>
+template <typename MsgT, bool MSG_SMEM, int MAXDC, bool SPEC, int OCC = 0, bool SERVE = false>
 __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OCC ? OCC : 1)
     qc_decode_kernel(const QcArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -237,13 +167,14 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
         if (fi >= r.n_frames) break;
         long long f = fi;
         int it0 = 0;   // iterations done before this launch
+        bool invalid = false;   // NaN or infinity among the frame's LLRs: not decoded
         if constexpr (SERVE) {
             f = a.serve_list[fi];
             const int fl = a.state_flag[f];
             if (fl != kSlotNew && fl != kSlotRunning) continue;   // uniform: every thread read the same flag
             if (!MSG_SMEM) msg = static_cast<MsgT*>(a.state_msgs) + static_cast<size_t>(f) * a.msg_slots;
             if (fl == kSlotNew) {
-                qc_frame_begin(a, s, msg, f);
+                invalid = qc_frame_begin(a, s, msg, f);
             } else {
                 it0 = a.state_iter[f];
                 const float* sp = a.state_P + static_cast<size_t>(f) * r.N;
@@ -256,56 +187,20 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
             __syncthreads();   // every thread has read the flag before it changes
             if (tid == 0) a.state_flag[f] = kSlotRunning;
         } else {
-            qc_frame_begin(a, s, msg, f);
+            invalid = qc_frame_begin(a, s, msg, f);
         }
         __syncthreads();
         int it = it0 + 1, unsat = 1;
         const int gw1 = a.G * W, gwk = gw1 * a.n_groupings;
         int gsel = (it0 % a.n_groupings) * gw1;   // iteration it uses grouping (it - 1) mod n_groupings
         bool park = false;
-        for (;; ++it) {
+        for (; !invalid; ++it) {
             const int* gl = s.glay + gsel;   // this iteration's grouping
             const int4* gt = s.gtab + gsel;
             for (int g = 0; g < a.G; ++g) {
                 float dl[MAXDC];
                 int vb[MAXDC];
                 int d = 0;
-                if constexpr (SPEC && W2) {
-                    // 2-layer window: direct write-back off the shared block columns, one
-                    // ordered round on them
-                    if (active) {
-                        const int l = gl[g * W + j];
-                        d = s.ldeg[l];
-                        const int2* et = s.tab + l * md;
-                        MsgT* m = msg + s.loff[l] + c * s.lstride[l];
-                        const unsigned mk = s.w2mask[g * 2 + j];
-                        float* dxc = s.dx + c * s.dxs;
-                        if (j == 0) {
-#define NDGSBP_CASE_W0(D) \
-    if (d == D) qc_phase_a_w2<NDGSBP_DD(D), MAXDC, MsgT, false>(et, mk, c, c4, Z4, P, m, dxc, lim, vb, dl);
-                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_W0)
-#undef NDGSBP_CASE_W0
-                        } else {
-#define NDGSBP_CASE_W1(D) \
-    if (d == D) qc_phase_a_w2<NDGSBP_DD(D), MAXDC, MsgT, true>(et, mk, c, c4, Z4, P, m, dxc, lim, vb, dl);
-                            NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_W1)
-#undef NDGSBP_CASE_W1
-                        }
-                    }
-                    __syncthreads();
-                    if (active && j == 1) {
-                        const int l = gl[g * W + 1];
-                        const int2* et = s.tab + l * md;
-                        const int2* w2 = a.win2 + (g * 2 + 1) * md;
-                        const unsigned mk = s.w2mask[g * 2 + 1];
-#define NDGSBP_CASE_WB(D) \
-    if (d == D) qc_phase_b_w2<NDGSBP_DD(D), MAXDC>(et, w2, mk, c, c4, Z, Z4, s.dxs, P, s.dx, dl);
-                        NDGSBP_DEGREE_CASES(MAXDC, NDGSBP_CASE_WB)
-#undef NDGSBP_CASE_WB
-                    }
-                    __syncthreads();
-                    continue;
-                }
                 if (active) {
                     const int4 ge = gt[g * W + j];   // one 16-byte load: table offset, degree, message offset, stride
                     d = ge.y;
@@ -386,7 +281,7 @@ __global__ void __launch_bounds__(OCC ? kOccThreads : max_threads_for(MAXDC), OC
             }
         }
         qc_frame_messages_out(a, msg, f);
-        write_frame_outputs(r, P, f, it, unsat, &s_err);
+        write_frame_outputs(r, P, f, it, unsat, &s_err, 1, invalid);
         if (SERVE && tid == 0) {
             a.state_flag[f] = kSlotDone;
             a.done_list[atomicAdd(a.done_count, 1)] = static_cast<int>(f);

@@ -26,13 +26,12 @@ UNIT_CN, UNIT_LAYER = 0, 1
 GROUPS_CYCLIC, GROUPS_NATURAL, GROUPS_STRUCTURED = 1, 2, 4
 SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
 VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1, 2, 3, 4
-VARIANT_QC_PAIR, VARIANT_QC_PAIR_GLOBAL, VARIANT_TILE = 5, 6, 7
-VARIANT_QC_FRAMES2, VARIANT_QC_FRAMES2_GLOBAL, VARIANT_QC_DIRECT = 8, 9, 10
+VARIANT_TILE = 7
 VARIANT_RAGGED_PER_CODE = 11   # ragged launches: each code on its own plan, forked streams
 TUNE_TILE_ONLY = 1
 GA_PHI_EXACT, GA_PHI_CLOSED = 0, 1
 STAT_FRAMES, STAT_FRAME_ERRORS, STAT_BIT_ERRORS, STAT_UNDETECTED = 0, 1, 2, 3
-STAT_ITERATIONS, STAT_UNSATISFIED, STATS_LEN = 4, 5, 8
+STAT_ITERATIONS, STAT_UNSATISFIED, STAT_INVALID, STATS_LEN = 4, 5, 6, 8
 
 
 class NdgsbpError(RuntimeError):

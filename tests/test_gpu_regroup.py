@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_1202_1060_gb300 import inputs as I
+from parity_rules import check_full
 
 pytestmark = pytest.mark.gpu
 MSG_TOL = 1e-4
@@ -68,9 +69,8 @@ def test_cycled_groupings_match_oracle(env, oracle_mod, variant):
         assert err.max() <= MSG_TOL, (k, err.max())
     full = _run(nd, torch, g, c, llr, max_iter=25, variant=v)
     ref = oracle_mod.ndgsbp_decode(c, gp, gc, l64, 25)
-    stable = ~(np.abs(ref.total) < 1e-3).any(axis=1) & (ref.synd_ok == 1)
-    assert (full["iters"][stable] == ref.iters[stable]).all()
-    assert (full["bits"][stable] == ref.hard[stable]).all()
+    check_full(f"cycled groupings {variant}", full["bits"], full["iters"], full["ok"], ref, l64,
+               lambda x: oracle_mod.ndgsbp_decode(c, gp, gc, x, 25))
 
 
 def test_cycled_qc_and_tile_agree_bitwise_and_refusals(env):
@@ -82,7 +82,7 @@ def test_cycled_qc_and_tile_agree_bitwise_and_refusals(env):
     a = _run(nd, torch, g, c, llr, max_iter=20, variant=nd.VARIANT_QC)
     b = _run(nd, torch, g, c, llr, max_iter=20, variant=nd.VARIANT_TILE, lanes_per_cn=1)
     assert (a["post"] == b["post"]).all() and (a["iters"] == b["iters"]).all()
-    for v in (nd.VARIANT_QC_FRAMES2, nd.VARIANT_QC_DIRECT, nd.VARIANT_SMEM):
+    for v in (nd.VARIANT_SMEM,):
         with pytest.raises(nd.NdgsbpError) as e:
             g.plan(nd.params_default(variant=v), 64)
         assert e.value.status == nd.ERR_UNSUPPORTED

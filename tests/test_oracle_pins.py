@@ -323,6 +323,25 @@ def test_awgn_llr_statistics(oracle_mod):
     assert abs(L1[:, cw == 1].mean() + 2 / s2) < 0.05 * 2 / s2
 
 
+def test_philox_matches_curand_host_generator(oracle_mod):
+    """The oracle's Philox4x32-10 (Salmon et al., SC'11) equals cuRAND's host implementation of
+    the same generator, block for block, over keys and counters that exercise every key bit and
+    counter words 0-2 (see tests/curand_host.py).  A wrong multiplier, Weyl constant, round count
+    or word order fails here."""
+    import curand_host as CH
+    lib = CH.library()
+    if lib is None:
+        pytest.skip("cuRAND is not installed")
+    for seed, j0 in CH.CASES:
+        got = CH.blocks(lib, seed, j0, 8)
+        for i in range(8):
+            want = oracle_mod.philox4x32_10(CH.counter_of(j0 + i), CH.key_of(seed))
+            assert (want == got[i]).all(), (hex(seed), j0 + i, want, got[i])
+    # counter 0 under key 0: the generator's very first block
+    assert [hex(x) for x in oracle_mod.philox4x32_10([0, 0, 0, 0], [0, 0])] == \
+        [hex(x) for x in CH.blocks(lib, 0, 0, 1)[0]]
+
+
 def test_philox_properties(oracle_mod):
     key = [0x1234, 0x5678]
     outs = np.array([oracle_mod.philox4x32_10([i, 0, 0, 0], key) for i in range(4096)])
@@ -362,6 +381,9 @@ MUTANTS = {
     # Step 1: take the overlap from the front of the previous group instead of its new part
     "overlap_from_front": ("for (int j = prev_len - o; j < prev_len; ++j) units[w++] = units[prev_begin + j];",
                            "for (int j = 0; j < o; ++j) units[w++] = units[prev_begin + j];"),
+    # channel generator: a wrong Weyl increment, and counter words 1 and 3 swapped in a round
+    "philox_weyl": ("W1 = 0xBB67AE85u;", "W1 = 0xBB67AE86u;"),
+    "philox_word_swap": ("uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;", "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c3 ^ k0;"),
 }
 
 
@@ -373,6 +395,7 @@ def _pins_pass(oracle_mod):
             test_fig1_message_sets(oracle_mod, x)
         test_step1_structure(oracle_mod, 60, 4, 0.4)
         test_one_group_is_flooding(oracle_mod)
+        test_philox_matches_curand_host_generator(oracle_mod)
     except AssertionError:
         return False
     return True

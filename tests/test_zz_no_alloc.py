@@ -8,7 +8,10 @@ ndgsbp_decode_static serves them with scratch held in a static device array of t
 These tests call it through the C ABI, twice in a row on different batches, and compare each
 result with ndgsbp_decode (which takes a caller-allocated workspace) on the same frames.  The two
 run the same kernels, so the tolerance is the one the parity tests use for identical
-arithmetic: equality.  The file is collected last so that a failure here does not hide others.
+arithmetic: equality.  They also check the property the entry point exists for: after the
+set-up (the plan and one first call), the device's free memory (cudaMemGetInfo) is the same
+before and after the two calls.  The file is collected last so that a failure here does not
+hide others.
 """
 import ctypes
 
@@ -45,9 +48,9 @@ def _outputs(torch, F, N, dev):
             torch.full((F, N), float("nan"), dtype=torch.float32, device=dev))
 
 
-def _static(nd, torch, fn, groups, params, llr):
+def _static(nd, torch, fn, groups, params, llr, out=None):
     dev = llr.device
-    hard, iters, ok, post = _outputs(torch, llr.shape[0], groups.code.N, dev)
+    hard, iters, ok, post = out if out is not None else _outputs(torch, llr.shape[0], groups.code.N, dev)
     stream = torch.cuda.current_stream().cuda_stream
     st = fn(groups.handle, ctypes.byref(params), ctypes.c_void_p(llr.data_ptr()), nd.F32, llr.shape[0],
             ctypes.c_void_p(hard.data_ptr()), ctypes.c_void_p(iters.data_ptr()), ctypes.c_void_p(ok.data_ptr()),
@@ -83,12 +86,24 @@ def test_static_decode_matches_workspace_decode(env, name, kind, pkw):
         groups = nd.Groups.build(code, 4, 0.4, 7)
     params = nd.params_default(max_iter=25, **pkw)
     F = 3000
-    groups.plan(params, F)          # set-up: puts the grouping's tables on this device
     dev = torch.device("cuda")
-    for call, (ebn0, seed) in enumerate([(1.25, 11), (1.75, 12)]):
-        llr = torch.from_numpy(I.channel_llr(c.N, F, ebn0, I.design_rate(c), seed, dtype=np.float32)).to(dev)
-        st, got = _static(nd, torch, fn, groups, params, llr)
+    llrs = [torch.from_numpy(I.channel_llr(c.N, F, ebn0, I.design_rate(c), seed, dtype=np.float32)).to(dev)
+            for ebn0, seed in [(1.25, 11), (1.75, 12)]]
+    outs = [_outputs(torch, F, c.N, dev) for _ in llrs]
+    # set-up: the plan puts the grouping's tables on this device; the first call looks up the
+    # static array's address and loads the kernel
+    groups.plan(params, F)
+    st, _ = _static(nd, torch, fn, groups, params, llrs[0])
+    assert st == nd.OK, nd.last_error()
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    for llr, out in zip(llrs, outs):
+        st, _ = _static(nd, torch, fn, groups, params, llr, out)
         assert st == nd.OK, nd.last_error()
+    torch.cuda.synchronize()
+    free_after = torch.cuda.mem_get_info()[0]
+    assert free_after == free_before, f"device free memory changed by {free_before - free_after} bytes"
+    for call, (llr, got) in enumerate(zip(llrs, outs)):
         want = _workspace(nd, torch, groups, params, llr)
         torch.cuda.synchronize()
         for g, w in zip(got, want):
