@@ -358,7 +358,9 @@ def run_ours(args):
     peak_clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = MUFU_PER_CLK_PER_SM * sms * peak_clock_mhz * 1e6 / 1e12
     kname = {nd.VARIANT_QC: "qc_decode_kernel", nd.VARIANT_QC_GLOBAL: "qc_decode_kernel",
-             nd.VARIANT_TILE: "tile_decode_kernel"}.get(plan.variant, "decode_kernel")
+             nd.VARIANT_TILE: "tile_decode_kernel", nd.VARIANT_STREAM_SMEM: "stream_decode_kernel",
+             nd.VARIANT_STREAM_GLOBAL: "stream_decode_kernel",
+             nd.VARIANT_STREAM_BULK: "stream_decode_kernel"}.get(plan.variant, "decode_kernel")
     traffic, traffic_rec = profiled_traffic(kname)
     roofline = {
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,

@@ -76,6 +76,15 @@ typedef int32_t ndgsbp_status;
                                       ndgsbp_decode plan (the library's choice for it), the launches
                                       forked onto concurrent streams and joined (same results as
                                       decoding each batch alone) */
+#define NDGSBP_VARIANT_STREAM 12   /* stream kernel (QC windows too large for one thread per CN,
+                                      degree <= 22): a thread per CN (or 2 lanes per CN) of a layer
+                                      steps through the window's layers; messages edge-major per
+                                      layer, where they live chosen by the library */
+#define NDGSBP_VARIANT_STREAM_SMEM 13   /* stream kernel, all messages of a frame in shared memory */
+#define NDGSBP_VARIANT_STREAM_GLOBAL 14 /* stream kernel, messages in per-CTA global-memory slots */
+#define NDGSBP_VARIANT_STREAM_BULK 15   /* stream kernel, messages in per-CTA global slots with each
+                                      layer's slab staged in shared memory by bulk copies (cyclic
+                                      windows advancing one layer per group only) */
 
 /* stats counters accumulated by ndgsbp_decode_ex (uint64 each) */
 #define NDGSBP_STAT_FRAMES 0
@@ -259,6 +268,13 @@ ndgsbp_status ndgsbp_decode(const ndgsbp_groups* groups, const ndgsbp_params* pa
                             int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
                             void* stream);
 
+/* Status word of the last decode launched with d_workspace (read after it on `stream`, which
+ * this call synchronises): 0 when every kernel completed its frames; bit 0 set when a bounded
+ * wait on a bulk copy of the stream kernel (variant STREAM_BULK) gave up -- that CTA stopped and
+ * the frame it held has no outputs (iteration count and flags as before the call).  Every decode
+ * clears the word when it starts.  Errors: INVALID, CUDA. */
+ndgsbp_status ndgsbp_workspace_status(const void* d_workspace, uint32_t* status, void* stream);
+
 /* ndgsbp_decode plus the fused statistics epilogue and debug outputs of ndgsbp_extras
  * (FER/BER counters against the transmitted word, iteration histogram, retire timestamps,
  * final CN->VN messages).  extras may be NULL. */
@@ -380,8 +396,8 @@ ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches,
  * layered QC kernel per pool whose plain decode would use that kernel (forked onto the pool's
  * own stream) and one serving launch of the tile kernel over the other pools; with
  * params->variant = NDGSBP_VARIANT_TILE every pool runs on the tile kernel.  Every frame is
- * decoded exactly as by ndgsbp_decode with the same choice (variant AUTO, or TILE), whatever else
- * is in flight.
+ * decoded exactly as by ndgsbp_decode with the kernel of its pool (variant QC for a pool on the
+ * layered QC kernel, TILE for the others), whatever else is in flight.
  * Errors: INVALID, BUDGET (a pool would get no slot), UNSUPPORTED (a code that is not QC in
  * whole layers, or that the tile kernel does not take), CUDA, NOMEM. */
 typedef struct ndgsbp_server ndgsbp_server;

@@ -22,6 +22,7 @@
 #include <new>
 
 #include "decode_qc.h"
+#include "decode_stream.h"
 #include "decode_tile.h"
 #include "device_common.cuh"
 #include "ndgsbp_internal.h"
@@ -187,7 +188,8 @@ static int msg_size(int dt) { return dt == NDGSBP_F32 ? 4 : 2; }
 static size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 static int degree_bound(int d) { return d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : 0; }
-static constexpr size_t kHeaderBytes = 256;
+static constexpr size_t kHeaderBytes = 256;   // workspace header: frame counter (bytes 0-7), status word (8-11)
+static constexpr size_t kStatusEnd = 16;
 
 #define CUDA_TRY(expr)                                                                         \
     do {                                                                                       \
@@ -247,10 +249,60 @@ static ndgsbp_status upload_layout(const Layout& L, DeviceLayout& D) {
     return NDGSBP_OK;
 }
 
+// Tables of the stream kernel for a layered QC grouping (decode_stream.cu): messages edge-major
+// per layer (edge k of CN c of layer l at layer_base[l] + k Z + c), which group of grouping 0
+// first uses each layer, the CSR position of each layer's first edge (negative, -(pos + 1), for a
+// layer no group holds), and -- when the groups are cyclic windows advancing one layer per group
+// (G = n_layers, one grouping, group g = ring positions g .. g + W - 1) -- the layer ring.
+struct StreamLayout {
+    std::vector<int32_t> layer_base, first_use, layer_csr, ring;
+    int msg_elems = 0, slab_elems = 0;
+    bool ring_ok = false;
+};
+
+static void stream_layout(const QcLayout& Q, StreamLayout& S) {
+    const int nl = Q.n_layers, Z = Q.Z, W = Q.window;
+    const int G = W ? static_cast<int>(Q.group_layers.size() / (static_cast<size_t>(W) * Q.n_groupings)) : 0;
+    S.layer_base.assign(nl, 0);
+    int off = 0;
+    for (int l = 0; l < nl; ++l) {
+        S.layer_base[l] = off;
+        off += Q.layer_deg[l] * Z;
+        S.slab_elems = std::max(S.slab_elems, Q.layer_deg[l] * Z);
+    }
+    S.msg_elems = off;
+    std::vector<char> seen(nl, 0), used(nl, 0);
+    S.first_use.assign(static_cast<size_t>(G) * W, 0);
+    for (int g = 0; g < G; ++g)
+        for (int j = 0; j < W; ++j) {
+            const int l = Q.group_layers[static_cast<size_t>(g) * W + j];
+            if (!seen[l]) S.first_use[static_cast<size_t>(g) * W + j] = 1;
+            seen[l] = 1;
+        }
+    for (int l : Q.group_layers) used[l] = 1;
+    S.layer_csr.assign(nl, 0);
+    for (int l = 0; l < nl; ++l) {
+        const int csr = Q.csr_of[Q.layer_off[l]];
+        S.layer_csr[l] = used[l] ? csr : -(csr + 1);
+    }
+    S.ring.assign(nl, 0);
+    S.ring_ok = Q.n_groupings == 1 && G == nl && W >= 1;
+    for (int g = 0; S.ring_ok && g < G; ++g)
+        for (int j = 0; j < W; ++j)
+            if (Q.group_layers[static_cast<size_t>(g) * W + j] != Q.group_layers[static_cast<size_t>((g + j) % G) * W])
+                S.ring_ok = false;
+    if (S.ring_ok)
+        for (int i = 0; i < nl; ++i) S.ring[i] = Q.group_layers[static_cast<size_t>(i) * W];
+}
+
 static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
+    StreamLayout SL;
+    stream_layout(Q, SL);
     BlobBuilder b;
     const size_t o_tab = b.add(Q.edge_tab), o_deg = b.add(Q.layer_deg), o_off = b.add(Q.layer_off);
     const size_t o_gl = b.add(Q.group_layers), o_csr = b.add(Q.csr_of), o_str = b.add(Q.layer_stride);
+    const size_t o_lb = b.add(SL.layer_base), o_fu = b.add(SL.first_use), o_lc = b.add(SL.layer_csr);
+    const size_t o_ring = b.add(SL.ring);
     void* blob = nullptr;
     ndgsbp_status st = b.upload(&blob);
     if (st) return st;
@@ -262,6 +314,10 @@ static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     D.layer_off = reinterpret_cast<const int32_t*>(p + o_off);
     D.group_layers = reinterpret_cast<const int32_t*>(p + o_gl);
     D.csr_of = reinterpret_cast<const int32_t*>(p + o_csr);
+    D.layer_base = reinterpret_cast<const int32_t*>(p + o_lb);
+    D.first_use = reinterpret_cast<const int32_t*>(p + o_fu);
+    D.layer_csr = reinterpret_cast<const int32_t*>(p + o_lc);
+    D.ring = reinterpret_cast<const int32_t*>(p + o_ring);
     return NDGSBP_OK;
 }
 
@@ -338,6 +394,9 @@ struct Plan {
     KernelFn fn = nullptr;
     QcKernelFn qfn = nullptr;
     TileKernelFn tfn = nullptr;
+    bool stream = false;
+    StreamKernelFn sfn = nullptr;
+    int stream_mode = 0, stream_tpc = 1, stream_le = 1, stream_slabs = 0, stream_ws_stride = 0;
     int tile_tpc = 1, tile_le = 1, tile_slots = 1, tile_slot_bytes = 0, tile_p_bytes = 0, tile_m_bytes = 0;
     int tile_delta_stride = 1, tile_frames = 1, tile_table_bytes = 0, n_tiles = 0;
     bool msg_smem = false, delta_smem = false;
@@ -362,7 +421,7 @@ static ndgsbp_status validate_params(const ndgsbp_params* p) {
         return fail(NDGSBP_ERR_INVALID, "frames_per_cta must be in [0, 16]");
     if (p->lanes_per_cn != 0 && p->lanes_per_cn != 1 && p->lanes_per_cn != 2 && p->lanes_per_cn != 4)
         return fail(NDGSBP_ERR_INVALID, "lanes_per_cn must be 0, 1, 2 or 4");
-    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_RAGGED_PER_CODE ||
+    if (p->variant < NDGSBP_VARIANT_AUTO || p->variant > NDGSBP_VARIANT_STREAM_BULK ||
         (p->variant > NDGSBP_VARIANT_QC_GLOBAL && p->variant < NDGSBP_VARIANT_TILE) ||
         (p->variant > NDGSBP_VARIANT_TILE && p->variant < NDGSBP_VARIANT_RAGGED_PER_CODE))
         return fail(NDGSBP_ERR_INVALID, "unknown variant %d", p->variant);
@@ -446,6 +505,101 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
     o.workspace_bytes = static_cast<int64_t>(
         kHeaderBytes + (msg_smem ? 0 : align256(static_cast<size_t>(grid) * Q.msg_slots * msg_size(p->msg_dtype))));
     o.stored_edges = Q.msg_slots;
+    o.edge_updates_per_iter = flood ? g.code->E : g.edge_updates;
+    *ok = true;
+    return NDGSBP_OK;
+}
+
+// Stream kernel plan: a QC grouping in whole layers whose window does not fit one CTA with one
+// thread per CN, CN degree <= 22 (one or two lanes per CN).  The message storage mode is the
+// variant's (STREAM_SMEM / _GLOBAL / _BULK) or, for AUTO and STREAM, the one that keeps the most
+// CTAs resident per SM (ties: shared memory, then bulk-staged slabs, then global).
+static ndgsbp_status make_stream_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
+                                      const DeviceInfo& di, Plan& plan, bool* ok, bool allow_upload = true) {
+    *ok = false;
+    const QcLayout& Q = flood ? flood_qc_layout(g) : g.qc;
+    if (!Q.ok) return NDGSBP_OK;
+    const int tpc = p->lanes_per_cn ? p->lanes_per_cn : (Q.max_deg <= 11 ? 1 : 2);
+    if (tpc != 1 && tpc != 2) return NDGSBP_OK;
+    const int LE = stream_lane_width((Q.max_deg + tpc - 1) / tpc, tpc);
+    if (!LE || LE * tpc < Q.max_deg) return NDGSBP_OK;
+    const int active = Q.Z * tpc;
+    const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
+    if (threads < active || threads > stream_max_threads(tpc)) return NDGSBP_OK;
+    StreamLayout SL;
+    stream_layout(Q, SL);
+    const int msz = msg_size(p->msg_dtype);
+    StreamArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.r.N = g.code->N;
+    a.Z = Q.Z;
+    a.nl = Q.n_layers;
+    a.window = Q.window;
+    a.n_groupings = Q.n_groupings;
+    a.G = static_cast<int>(Q.group_layers.size() / (static_cast<size_t>(Q.window) * Q.n_groupings));
+    a.maxdeg = Q.max_deg;
+    a.tpc = tpc;
+    a.le = (Q.max_deg + tpc - 1) / tpc;
+    a.msg_elems = SL.msg_elems;
+    a.slab_elems = SL.slab_elems;
+    a.n_slabs = Q.window + 2;
+    const bool bulk_ok = SL.ring_ok && Q.n_layers >= Q.window + 2 && a.n_slabs <= kStreamMaxSlabs &&
+                         (static_cast<size_t>(Q.Z) * msz) % 16 == 0;
+    int want = -1;
+    if (p->variant == NDGSBP_VARIANT_STREAM_SMEM) want = kStreamSmem;
+    if (p->variant == NDGSBP_VARIANT_STREAM_GLOBAL) want = kStreamGlobal;
+    if (p->variant == NDGSBP_VARIANT_STREAM_BULK) want = kStreamBulk;
+    if (want == kStreamBulk && !bulk_ok) return NDGSBP_OK;
+    const size_t budget = static_cast<size_t>(di.smem_optin) - 64;
+    int best_mode = -1, best_per_sm = 0;
+    size_t best_smem = 0;
+    for (int mode : {kStreamSmem, kStreamBulk, kStreamGlobal}) {
+        if (want >= 0 && mode != want) continue;
+        if (mode == kStreamBulk && !bulk_ok) continue;
+        const size_t smem = stream_smem_bytes(a, msz, mode);
+        if (smem > budget) continue;
+        StreamKernelFn fn = pick_stream_kernel(p->msg_dtype, LE, tpc, mode);
+        if (!fn) continue;
+        CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem)));
+        int per_sm = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(fn), threads, smem));
+        if (p->ctas_per_sm > 0) per_sm = std::min(per_sm, p->ctas_per_sm);
+        if (per_sm > best_per_sm) {
+            best_per_sm = per_sm;
+            best_mode = mode;
+            best_smem = smem;
+        }
+    }
+    if (best_mode < 0) return NDGSBP_OK;
+    StreamKernelFn fn = pick_stream_kernel(p->msg_dtype, LE, tpc, best_mode);
+    int per_sm = 0;
+    int64_t grid = 0;
+    ndgsbp_status st = finish_grid(reinterpret_cast<const void*>(fn), threads, best_smem, p, n_frames, di, per_sm, grid);
+    if (st) return st;
+    st = device_qc(g, flood, plan.Q, plan.DQ, allow_upload);
+    if (st) return st;
+    const int ws_stride = static_cast<int>(align256(static_cast<size_t>(SL.msg_elems) * msz) / msz);
+    plan.stream = true;
+    plan.sfn = fn;
+    plan.stream_mode = best_mode;
+    plan.stream_tpc = tpc;
+    plan.stream_le = LE;
+    plan.stream_slabs = a.n_slabs;
+    plan.stream_ws_stride = ws_stride;
+    plan.msg_smem = best_mode == kStreamSmem;
+    ndgsbp_plan& o = plan.pub;
+    o.variant = best_mode == kStreamSmem ? NDGSBP_VARIANT_STREAM_SMEM
+                                         : (best_mode == kStreamBulk ? NDGSBP_VARIANT_STREAM_BULK : NDGSBP_VARIANT_STREAM_GLOBAL);
+    o.block_threads = threads;
+    o.grid = static_cast<int32_t>(grid);
+    o.ctas_per_sm = per_sm;
+    o.max_row_degree = Q.max_deg;
+    o.delta_in_smem = 1;
+    o.smem_bytes = static_cast<int64_t>(best_smem);
+    o.workspace_bytes = static_cast<int64_t>(
+        kHeaderBytes + (best_mode == kStreamSmem ? 0 : align256(static_cast<size_t>(grid) * ws_stride * msz)));
+    o.stored_edges = SL.msg_elems;
     o.edge_updates_per_iter = flood ? g.code->E : g.edge_updates;
     *ok = true;
     return NDGSBP_OK;
@@ -542,7 +696,15 @@ static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t 
         if (ok) return NDGSBP_OK;
         return fail(NDGSBP_ERR_UNSUPPORTED, "TILE variant needs a QC code grouped in whole layers, row degree <= 32");
     }
-    const bool want_qc = p->variant >= NDGSBP_VARIANT_QC;
+    if (p->variant >= NDGSBP_VARIANT_STREAM && p->variant <= NDGSBP_VARIANT_STREAM_BULK) {
+        bool ok = false;
+        st = make_stream_plan(g, p, n_frames, flood, di, plan, &ok, allow_upload);
+        if (st) return st;
+        if (ok) return NDGSBP_OK;
+        return fail(NDGSBP_ERR_UNSUPPORTED, "STREAM variant needs a QC code grouped in whole layers, row degree "
+                                            "<= 22 (bulk staging: cyclic windows advancing one layer per group)");
+    }
+    const bool want_qc = p->variant == NDGSBP_VARIANT_QC || p->variant == NDGSBP_VARIANT_QC_GLOBAL;
     if (p->variant == NDGSBP_VARIANT_AUTO || want_qc) {
         bool ok = false;
         st = make_qc_plan(g, p, n_frames, flood, di, plan, &ok, allow_upload);
@@ -551,7 +713,11 @@ static ndgsbp_status make_plan(const Groups& g, const ndgsbp_params* p, int64_t 
         if (want_qc)
             return fail(NDGSBP_ERR_UNSUPPORTED, "QC variant needs a QC code grouped in whole layers with a window "
                                                 "that fits one CTA");
-        // QC code whose window does not fit one CTA with one CN per thread: tile kernel
+        // QC code whose window does not fit one CTA with one CN per thread: stream kernel, else
+        // tile kernel
+        st = make_stream_plan(g, p, n_frames, flood, di, plan, &ok, allow_upload);
+        if (st) return st;
+        if (ok) return NDGSBP_OK;
         st = make_tile_plan(g, p, n_frames, flood, di, plan, &ok, allow_upload);
         if (st) return st;
         if (ok) return NDGSBP_OK;
@@ -672,7 +838,41 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
                                  int32_t llr_dtype, int64_t n_frames, unsigned char* ws, uint32_t* d_hard_bits,
                                  int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
                                  const ndgsbp_extras* extras, cudaStream_t s) {
-    if (plan.tile) {
+    if (plan.stream) {
+        StreamArgs a;
+        std::memset(&a, 0, sizeof(a));
+        fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior,
+                 extras);
+        const QcLayout& Q = *plan.Q;
+        const DeviceQc& D = *plan.DQ;
+        a.Z = Q.Z;
+        a.nl = Q.n_layers;
+        a.window = Q.window;
+        a.n_groupings = Q.n_groupings;
+        a.G = static_cast<int>(Q.group_layers.size() / (static_cast<size_t>(Q.window) * Q.n_groupings));
+        a.maxdeg = Q.max_deg;
+        a.tpc = plan.stream_tpc;
+        a.le = (Q.max_deg + plan.stream_tpc - 1) / plan.stream_tpc;
+        a.msg_elems = static_cast<int>(plan.pub.stored_edges);
+        a.edge_tab = reinterpret_cast<const int2*>(D.edge_tab);
+        a.layer_deg = D.layer_deg;
+        a.layer_base = D.layer_base;
+        a.group_layers = D.group_layers;
+        a.first_use = D.first_use;
+        a.layer_csr = D.layer_csr;
+        a.ring = D.ring;
+        // per-CTA message slots are ws_stride elements apart (256-byte multiples)
+        a.ws_msgs = plan.stream_mode == kStreamSmem ? nullptr : ws + kHeaderBytes;
+        a.status = reinterpret_cast<unsigned*>(ws + 8);
+        a.n_slabs = plan.stream_slabs;
+        int slab = 0;
+        for (int d : Q.layer_deg) slab = std::max(slab, d * Q.Z);
+        a.slab_elems = slab;
+        a.ws_stride = plan.stream_ws_stride;
+        a.wait_limit = 1u << 22;
+        a.test_skip_load = 0;
+        plan.sfn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
+    } else if (plan.tile) {
         TileArgs a;
         std::memset(&a, 0, sizeof(a));
         TileCode& C = a.codes[0];
@@ -805,7 +1005,7 @@ ndgsbp_status plan_enqueue(const Groups& g, const Plan& plan, const ndgsbp_param
                            int32_t llr_dtype, int64_t n_frames, void* ws, uint32_t* d_hard_bits, int32_t* d_iters,
                            uint8_t* d_syndrome_ok, float* d_posterior, const ndgsbp_extras* extras, cudaStream_t s) {
     if (n_frames == 0) return NDGSBP_OK;
-    CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), s));
+    CUDA_TRY(cudaMemsetAsync(ws, 0, kStatusEnd, s));   // frame counter and status word
     return launch_plan(g, plan, p, d_llr, llr_dtype, n_frames, static_cast<unsigned char*>(ws), d_hard_bits, d_iters,
                        d_syndrome_ok, d_posterior, extras, s);
 }
@@ -874,7 +1074,7 @@ ndgsbp_status ndgsbp_decode_ex(const ndgsbp_groups* groups, const ndgsbp_params*
         return fail(NDGSBP_ERR_WORKSPACE, "decode: workspace must be 256-byte aligned");
     auto* ws = static_cast<unsigned char*>(d_workspace);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), s));
+    CUDA_TRY(cudaMemsetAsync(ws, 0, kStatusEnd, s));   // frame counter and status word
     return launch_plan(g, plan, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok,
                        d_posterior, extras, s);
 }
@@ -886,6 +1086,15 @@ ndgsbp_status ndgsbp_decode(const ndgsbp_groups* groups, const ndgsbp_params* pa
                             void* stream) {
     return ndgsbp_decode_ex(groups, params, d_llr, llr_dtype, n_frames, d_workspace, workspace_bytes,
                             d_hard_bits, d_iters, d_syndrome_ok, d_posterior, nullptr, stream);
+}
+
+ndgsbp_status ndgsbp_workspace_status(const void* d_workspace, uint32_t* status, void* stream) {
+    clear_error();
+    if (!d_workspace || !status) return fail(NDGSBP_ERR_INVALID, "workspace_status: null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemcpyAsync(status, static_cast<const unsigned char*>(d_workspace) + 8, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return NDGSBP_OK;
 }
 
 ndgsbp_status ndgsbp_decode_static(const ndgsbp_groups* groups, const ndgsbp_params* params,
@@ -916,7 +1125,7 @@ ndgsbp_status ndgsbp_decode_static(const ndgsbp_groups* groups, const ndgsbp_par
     if (st) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the frame counter must start at zero; message and delta slots are written before read
-    CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), s));
+    CUDA_TRY(cudaMemsetAsync(ws, 0, kStatusEnd, s));   // frame counter and status word
     return launch_plan(g, plan, params, d_llr, llr_dtype, n_frames, static_cast<unsigned char*>(ws), d_hard_bits,
                        d_iters, d_syndrome_ok, d_posterior, nullptr, s);
 }

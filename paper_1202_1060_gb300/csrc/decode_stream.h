@@ -1,0 +1,57 @@
+// Stream decode kernel interface (decode_stream.cu): layered QC codes whose window of W layers
+// is too large for one thread per CN of the window (the QC kernel), e.g. n=16200 (Z = 360) and
+// n=8192 (Z = 256, degree 22).
+#pragma once
+
+#include "device_common.cuh"
+#include "ndgsbp_internal.h"
+
+namespace ndgsbp {
+
+// Where a frame's CN->VN messages live.
+constexpr int kStreamSmem = 0;     // all of the frame's messages in shared memory
+constexpr int kStreamGlobal = 1;   // in the CTA's workspace slot, read and written in place
+constexpr int kStreamBulk = 2;     // in the CTA's workspace slot, layer slabs staged in shared memory
+                                   // by cp.async.bulk (see decode_stream.cu)
+
+// Largest number of layer slabs a bulk-staged launch keeps in shared memory.
+constexpr int kStreamMaxSlabs = 8;
+
+struct StreamArgs {
+    RunArgs r;
+    int Z, nl, G, window, maxdeg, n_groupings;
+    int tpc;                      // lanes per CN (1 or 2)
+    int le;                       // edges per lane, ceil(maxdeg / tpc) (<= the instance's width)
+    int msg_elems;                // messages per frame: sum over layers of d_l Z
+    const int2* edge_tab;         // [nl][maxdeg]: (4 (b Z + s), Z - s) of edge k of the layer
+    const int32_t* layer_deg;     // [nl]
+    const int32_t* layer_base;    // [nl] first message of layer l: edge k of CN c at base + k Z + c
+    const int32_t* group_layers;  // [n_groupings][G][window]
+    const int32_t* first_use;     // [G][window] 1: grouping 0's group g is the first to use that
+                                  // layer (iteration 1 reads no messages there: they are 0)
+    const int32_t* layer_csr;     // [nl] CSR position of the layer's first edge, -1 for a layer no
+                                  // group holds (its messages stay 0)
+    void* ws_msgs;                // [grid][ws_stride] message slots (GLOBAL and BULK)
+    int ws_stride;                // elements between CTAs' slots (msg_elems rounded up to 256 bytes)
+    unsigned* status;             // workspace word: bit 0 set when a bounded wait gave up (BULK)
+    // BULK only: group g of an iteration holds ring positions g .. g + window - 1 (mod nl)
+    const int32_t* ring;          // [nl] layer at each ring position
+    int n_slabs;                  // window + 2 slab buffers in shared memory
+    int slab_elems;               // elements per slab buffer (the largest d_l Z)
+    unsigned wait_limit;          // polls before a bounded wait gives up
+    int test_skip_load;           // test hook: 1 = arm the first load's barrier but issue no copy
+};
+
+typedef void (*StreamKernelFn)(const StreamArgs);
+
+// Kernel instance for `le` edges per lane (a compiled width >= the code's: stream_lane_width),
+// lanes per CN (1 or 2) and message storage mode; nullptr when no instance exists.
+StreamKernelFn pick_stream_kernel(int msg_dtype, int le, int tpc, int mode);
+// Compiled edges-per-lane width for le edges per lane at tpc lanes per CN (0 when none).
+int stream_lane_width(int le, int tpc);
+// Largest block of an instance at tpc lanes per CN (instances are compiled for 2 CTAs per SM).
+int stream_max_threads(int tpc);
+// Dynamic shared memory of a launch (a filled in; msg_size 2 or 4 bytes).
+size_t stream_smem_bytes(const StreamArgs& a, int msg_size, int mode);
+
+}  // namespace ndgsbp

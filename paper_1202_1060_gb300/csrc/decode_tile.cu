@@ -24,66 +24,11 @@
 #include <cstring>
 
 #include "decode_tile.h"
+#include "lane_cnu.cuh"
 
 namespace ndgsbp {
 
 constexpr int kMaxSlots = 16;   // largest number of frame slots per CTA
-
-__device__ __forceinline__ int tile_vb(int2 e, int c, int Z4) { return e.x + 4 * c - (c >= e.y ? Z4 : 0); }
-
-__device__ __forceinline__ float& at_b(float* P, int vb) {
-    return *reinterpret_cast<float*>(reinterpret_cast<char*>(P) + vb);
-}
-
-// Forward pass over the lane's LE edge positions, of which the first nreal are edges: prefix
-// pairs, lane total (cn, ce), and the signs: xu[k] = exp(-|L_k|) >= 0 carries the sign of t[k]
-// in its sign bit (every use takes |xu|, a free operand modifier), and bit 31 of par collects
-// the parity of the lane's input signs.  Every lane runs the same LE, the kernel instance's
-// compile-time width (no divergence between lanes holding different edge counts, no dispatch
-// on the width at run time); a position past nreal is the neutral factor
-// tanh = 1, i.e. u = 0 and (N, E) = (1/2, 0), which only scales the lane's pairs by exactly 1/2
-// (t = +0 there, so no sign either): the outputs of the real edges do not change.
-template <int LE>
-__device__ __forceinline__ void lane_forward(const float (&t)[LE], int nreal, float lim, float (&xu)[LE],
-                                             float (&pn)[LE], float (&pe)[LE], float& cn, float& ce,
-                                             unsigned& par) {
-#pragma unroll
-    for (int k = 0; k < LE; ++k) {
-        const bool real = k < nreal;
-        const float tk = real ? t[k] : 0.f;
-        const unsigned tb = __float_as_uint(tk);
-        par ^= tb;
-        const float x = fminf(fabsf(tk), lim);
-        const float u = real ? ex2_approx(-x) : 0.f;   // exp(-|L|) (log2 units)
-        const float n = fmaf(-0.5f, u, 0.5f);
-        xu[k] = __uint_as_float(__float_as_uint(u) | (tb & 0x80000000u));
-        pn[k] = cn;
-        pe[k] = ce;
-        ce = fmaf(ce, fmaf(0.5f, u, 0.5f), cn * u);   // n + u = (1 + u) / 2
-        cn = cn * n;
-    }
-}
-
-// Backward pass: the suffix starts from (sn, se), the product over the other lanes' edges;
-// pm = bit 31 of the CN's sign parity (all lanes); outputs for the nreal real positions only.
-template <int LE, typename Emit>
-__device__ __forceinline__ void lane_backward(const float (&xu)[LE], const float (&pn)[LE], const float (&pe)[LE],
-                                              int nreal, float sn, float se, unsigned pm, float lim, Emit emit) {
-#pragma unroll
-    for (int k = LE - 1; k >= 0; --k) {
-        const float u = fabsf(xu[k]);
-        const float n = fmaf(-0.5f, u, 0.5f);
-        const float en = pn[k] * sn;
-        const float ss = sn + se;
-        const float ee = fmaf(pe[k], ss, pn[k] * se);
-        const float w = fmaf(en * rcp_approx(ee), 2.f, 1.f);
-        const float mag = fminf(lg2_approx(w), lim);
-        const unsigned sgn = (__float_as_uint(xu[k]) ^ pm) & 0x80000000u;
-        if (k < nreal) emit(k, __uint_as_float(__float_as_uint(mag) | sgn));
-        se = fmaf(u, ss, se * n);   // se (n + u) + sn u, reusing sn + se
-        sn = sn * n;
-    }
-}
 
 // A code's tables at the start of shared memory: edge table [nl][md] (int2), layer degrees
 // [nl], then, 16-byte aligned, one record per (grouping, group, position):
@@ -245,22 +190,9 @@ __device__ __forceinline__ void run_tile(const TileCode& C, const int2* tab, uns
                     lane_forward<LE>(t, L, lim, xu, pn, pe, cn, ce, lpar);
                 }
                 // product over the other lanes of the CN, and the total sign parity
-                float on = 1.f, oe = 0.f;
-                unsigned par = lpar;
-                if (tpc > 1) {
-                    const float xn = __shfl_xor_sync(gmask, cn, 1), xe = __shfl_xor_sync(gmask, ce, 1);
-                    par ^= __shfl_xor_sync(gmask, par, 1);
-                    if (tpc == 2) {
-                        on = xn;
-                        oe = xe;
-                    } else {
-                        const float pn2 = cn * xn, pe2 = fmaf(ce, xn + xe, cn * xe);   // this pair's total
-                        const float yn = __shfl_xor_sync(gmask, pn2, 2), ye = __shfl_xor_sync(gmask, pe2, 2);
-                        par ^= __shfl_xor_sync(gmask, par, 2);
-                        on = xn * yn;
-                        oe = fmaf(xe, yn + ye, xn * ye);
-                    }
-                }
+                float on, oe;
+                unsigned par;
+                lane_exchange(tpc, gmask, cn, ce, lpar, on, oe, par);
                 if (live) {
                     lane_backward<LE>(xu, pn, pe, L, on, oe, par & 0x80000000u, lim, [&](int k, float val) {
                         const MsgT q = from_f<MsgT>(val);

@@ -161,8 +161,11 @@ __device__ __forceinline__ void check_node_update(const float (&t)[MAXDC], int d
     }
 }
 
-// Claim the next frame for this CTA (tid 0 writes *slot); returns after a barrier.
+// Claim the next frame for this CTA (tid 0 writes *slot); returns after a barrier.  The leading
+// barrier keeps tid 0 from overwriting *slot before every thread has read the previous value
+// (a serving launch skips a listed slot that is no longer running without any other barrier).
 __device__ __forceinline__ long long next_frame(const RunArgs& r, long long* slot) {
+    __syncthreads();
     if (threadIdx.x == 0) *slot = static_cast<long long>(atomicAdd(r.counter, 1ull));
     __syncthreads();
     return *slot;

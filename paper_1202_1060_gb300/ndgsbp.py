@@ -27,6 +27,7 @@ GROUPS_CYCLIC, GROUPS_NATURAL, GROUPS_STRUCTURED = 1, 2, 4
 SCHEDULE_GROUPS, SCHEDULE_FLOOD = 0, 1
 VARIANT_AUTO, VARIANT_SMEM, VARIANT_GLOBAL, VARIANT_QC, VARIANT_QC_GLOBAL = 0, 1, 2, 3, 4
 VARIANT_TILE = 7
+VARIANT_STREAM, VARIANT_STREAM_SMEM, VARIANT_STREAM_GLOBAL, VARIANT_STREAM_BULK = 12, 13, 14, 15
 VARIANT_RAGGED_PER_CODE = 11   # ragged launches: each code on its own plan, forked streams
 TUNE_TILE_ONLY = 1
 GA_PHI_EXACT, GA_PHI_CLOSED = 0, 1
@@ -116,6 +117,7 @@ _SIGS = {
     "ndgsbp_decode_ex": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, ctypes.c_size_t,
                                 _P, _P, _P, _P, ctypes.POINTER(Extras), _P]),
     "ndgsbp_decode_static": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, _P, _P, _P, _P]),
+    "ndgsbp_workspace_status": (_I32, [_P, ctypes.POINTER(_U32), _P]),
     "ndgsbp_ragged_create": (_I32, [_P, _I32, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
     "ndgsbp_ragged_info": (_I32, [_P, ctypes.POINTER(Plan), _P]),
     "ndgsbp_ragged_launch": (_I32, [_P, _P]),
@@ -379,6 +381,13 @@ def decode_static(groups: Groups, params: Params, llr, hard_bits, iters=None, sy
     _check(_lib.ndgsbp_decode_static(groups.handle, ctypes.byref(params), _dptr(llr), dtype_code(llr),
                                      llr.shape[0], _dptr(hard_bits), _dptr(iters), _dptr(syndrome_ok),
                                      _dptr(posterior), _stream(stream)))
+
+
+def workspace_status(workspace, stream=None) -> int:
+    """ndgsbp_workspace_status: the status word of the last decode that used ``workspace``."""
+    v = ctypes.c_uint32(0)
+    _check(_lib.ndgsbp_workspace_status(_dptr(workspace), ctypes.byref(v), _stream(stream)))
+    return int(v.value)
 
 
 def _batch_array(batches):

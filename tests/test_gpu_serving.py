@@ -36,10 +36,13 @@ def _grouped(nd, name):
 
 def _alone(nd, torch, g, c, llr, params):
     """The batch decoded alone by the kernel a server with these params uses for the code: the
-    plain decode's own choice (variant AUTO), or TILE when the server runs everything on it."""
+    layered QC kernel where the plain decode (variant AUTO) uses it, else the tile kernel (and
+    the tile kernel for every code when the server is created with variant TILE)."""
     dev = torch.device("cuda")
     p = nd.params_default(**{f: getattr(params, f) for f, _ in params._fields_})
-    p.variant = nd.VARIANT_TILE if params.variant == nd.VARIANT_TILE else nd.VARIANT_AUTO
+    p.variant = nd.VARIANT_AUTO
+    if params.variant == nd.VARIANT_TILE or g.plan(p, 1024).variant not in (nd.VARIANT_QC, nd.VARIANT_QC_GLOBAL):
+        p.variant = nd.VARIANT_TILE
     F = llr.shape[0]
     d_llr = torch.from_numpy(np.ascontiguousarray(llr, np.float32)).to(dev)
     hard = torch.zeros((F, (c.N + 31) // 32), dtype=torch.int32, device=dev)
