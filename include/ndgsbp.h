@@ -341,7 +341,8 @@ ndgsbp_status ndgsbp_ragged_destroy(ndgsbp_ragged* ragged);
  * returns the fastest in result->best: params with variant, block_threads, ctas_per_sm,
  * frames_per_cta and lanes_per_cn filled in (the other fields as given).  Candidates are the
  * library's default choice, the QC kernel at 0/1/2 CTAs per SM (messages in shared memory) and
- * at 0/2/3/4 CTAs per SM (messages in global memory), and tile shapes (1, 2 or 4 lanes per CN x
+ * at 0/2/3/4 CTAs per SM (messages in global memory), the stream kernel's three storage modes at
+ * 1 and 2 lanes per CN, and tile shapes (1, 2 or 4 lanes per CN x
  * 1..16 frames per CTA x 128..512 threads, at the default residency and at 1 CTA per SM) that
  * the plan accepts.  Each
  * candidate is an ordinary decode into the tuner's own scratch buffers: one untimed call, then

@@ -168,6 +168,8 @@ ndgsbp_status ndgsbp_autotune(const ndgsbp_groups* groups, const ndgsbp_params* 
         add(NDGSBP_VARIANT_AUTO, params->block_threads, params->ctas_per_sm, 0, 0);
         for (int cps : {0, 1, 2}) add(NDGSBP_VARIANT_QC, 0, cps, 0, 0);
         for (int cps : {0, 2, 3, 4}) add(NDGSBP_VARIANT_QC_GLOBAL, 0, cps, 0, 0);
+        for (int v : {NDGSBP_VARIANT_STREAM_SMEM, NDGSBP_VARIANT_STREAM_GLOBAL, NDGSBP_VARIANT_STREAM_BULK})
+            for (int lanes : {0, 2}) add(v, 0, 0, 0, lanes);
     }
     const int maxdeg = g.qc.ok ? g.qc.max_deg : 0;
     const int threads_list[] = {128, 256, 384, 512};

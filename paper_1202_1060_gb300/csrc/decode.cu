@@ -249,28 +249,34 @@ static ndgsbp_status upload_layout(const Layout& L, DeviceLayout& D) {
     return NDGSBP_OK;
 }
 
-// Tables of the stream kernel for a layered QC grouping (decode_stream.cu): messages edge-major
-// per layer (edge k of CN c of layer l at layer_base[l] + k Z + c), which group of grouping 0
-// first uses each layer, the CSR position of each layer's first edge (negative, -(pos + 1), for a
-// layer no group holds), and -- when the groups are cyclic windows advancing one layer per group
-// (G = n_layers, one grouping, group g = ring positions g .. g + W - 1) -- the layer ring.
+// Tables of the stream kernel for a layered QC grouping (decode_stream.cu): which group of
+// grouping 0 first uses each layer, the CSR position of each layer's first edge (negative,
+// -(pos + 1), for a layer no group holds), and -- when the groups are cyclic windows advancing one
+// layer per group (G = n_layers, one grouping, group g = ring positions g .. g + W - 1) -- the
+// layer ring.  The message layout (stream_layer_elems) depends on the storage mode and message
+// type and is set per launch (stream_bases).
 struct StreamLayout {
-    std::vector<int32_t> layer_base, first_use, layer_csr, ring;
-    int msg_elems = 0, slab_elems = 0;
+    std::vector<int32_t> first_use, layer_csr, ring;
     bool ring_ok = false;
 };
+
+// Layer block offsets of a stream launch (elements), the per-frame total and the largest block.
+static void stream_bases(const QcLayout& Q, int msz, int mode, int32_t* lbase, int* msg_elems, int* slab_elems) {
+    const int zr = (Q.Z + 15) / 16 * 16;
+    int off = 0, mx = 0;
+    for (int l = 0; l < Q.n_layers; ++l) {
+        const int e = stream_layer_elems(Q.layer_deg[l], Q.Z, zr, msz, mode);
+        lbase[l] = off;
+        off += e;
+        mx = std::max(mx, e);
+    }
+    *msg_elems = off;
+    *slab_elems = mx;
+}
 
 static void stream_layout(const QcLayout& Q, StreamLayout& S) {
     const int nl = Q.n_layers, Z = Q.Z, W = Q.window;
     const int G = W ? static_cast<int>(Q.group_layers.size() / (static_cast<size_t>(W) * Q.n_groupings)) : 0;
-    S.layer_base.assign(nl, 0);
-    int off = 0;
-    for (int l = 0; l < nl; ++l) {
-        S.layer_base[l] = off;
-        off += Q.layer_deg[l] * Z;
-        S.slab_elems = std::max(S.slab_elems, Q.layer_deg[l] * Z);
-    }
-    S.msg_elems = off;
     std::vector<char> seen(nl, 0), used(nl, 0);
     S.first_use.assign(static_cast<size_t>(G) * W, 0);
     for (int g = 0; g < G; ++g)
@@ -301,7 +307,7 @@ static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     BlobBuilder b;
     const size_t o_tab = b.add(Q.edge_tab), o_deg = b.add(Q.layer_deg), o_off = b.add(Q.layer_off);
     const size_t o_gl = b.add(Q.group_layers), o_csr = b.add(Q.csr_of), o_str = b.add(Q.layer_stride);
-    const size_t o_lb = b.add(SL.layer_base), o_fu = b.add(SL.first_use), o_lc = b.add(SL.layer_csr);
+    const size_t o_fu = b.add(SL.first_use), o_lc = b.add(SL.layer_csr);
     const size_t o_ring = b.add(SL.ring);
     void* blob = nullptr;
     ndgsbp_status st = b.upload(&blob);
@@ -314,7 +320,6 @@ static ndgsbp_status upload_qc(const QcLayout& Q, DeviceQc& D) {
     D.layer_off = reinterpret_cast<const int32_t*>(p + o_off);
     D.group_layers = reinterpret_cast<const int32_t*>(p + o_gl);
     D.csr_of = reinterpret_cast<const int32_t*>(p + o_csr);
-    D.layer_base = reinterpret_cast<const int32_t*>(p + o_lb);
     D.first_use = reinterpret_cast<const int32_t*>(p + o_fu);
     D.layer_csr = reinterpret_cast<const int32_t*>(p + o_lc);
     D.ring = reinterpret_cast<const int32_t*>(p + o_ring);
@@ -397,6 +402,8 @@ struct Plan {
     bool stream = false;
     StreamKernelFn sfn = nullptr;
     int stream_mode = 0, stream_tpc = 1, stream_le = 1, stream_slabs = 0, stream_ws_stride = 0;
+    int stream_msg_elems = 0, stream_slab_elems = 0;
+    std::vector<int32_t> stream_lbase;
     int tile_tpc = 1, tile_le = 1, tile_slots = 1, tile_slot_bytes = 0, tile_p_bytes = 0, tile_m_bytes = 0;
     int tile_delta_stride = 1, tile_frames = 1, tile_table_bytes = 0, n_tiles = 0;
     bool msg_smem = false, delta_smem = false;
@@ -513,7 +520,8 @@ static ndgsbp_status make_qc_plan(const Groups& g, const ndgsbp_params* p, int64
 // Stream kernel plan: a QC grouping in whole layers whose window does not fit one CTA with one
 // thread per CN, CN degree <= 22 (one or two lanes per CN).  The message storage mode is the
 // variant's (STREAM_SMEM / _GLOBAL / _BULK) or, for AUTO and STREAM, the one that keeps the most
-// CTAs resident per SM (ties: shared memory, then bulk-staged slabs, then global).
+// CTAs resident per SM (ties: shared memory, then global, then bulk-staged slabs -- the order
+// measured on GB300 for n=16200 and n=8192).
 static ndgsbp_status make_stream_plan(const Groups& g, const ndgsbp_params* p, int64_t n_frames, bool flood,
                                       const DeviceInfo& di, Plan& plan, bool* ok, bool allow_upload = true) {
     *ok = false;
@@ -526,6 +534,7 @@ static ndgsbp_status make_stream_plan(const Groups& g, const ndgsbp_params* p, i
     const int active = Q.Z * tpc;
     const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
     if (threads < active || threads > stream_max_threads(tpc)) return NDGSBP_OK;
+    if (Q.n_layers > kStreamMaxLayers) return NDGSBP_OK;
     StreamLayout SL;
     stream_layout(Q, SL);
     const int msz = msg_size(p->msg_dtype);
@@ -540,11 +549,9 @@ static ndgsbp_status make_stream_plan(const Groups& g, const ndgsbp_params* p, i
     a.maxdeg = Q.max_deg;
     a.tpc = tpc;
     a.le = (Q.max_deg + tpc - 1) / tpc;
-    a.msg_elems = SL.msg_elems;
-    a.slab_elems = SL.slab_elems;
+    a.zr = (Q.Z + 15) / 16 * 16;
     a.n_slabs = Q.window + 2;
-    const bool bulk_ok = SL.ring_ok && Q.n_layers >= Q.window + 2 && a.n_slabs <= kStreamMaxSlabs &&
-                         (static_cast<size_t>(Q.Z) * msz) % 16 == 0;
+    const bool bulk_ok = SL.ring_ok && Q.n_layers >= Q.window + 2 && a.n_slabs <= kStreamMaxSlabs;
     int want = -1;
     if (p->variant == NDGSBP_VARIANT_STREAM_SMEM) want = kStreamSmem;
     if (p->variant == NDGSBP_VARIANT_STREAM_GLOBAL) want = kStreamGlobal;
@@ -553,9 +560,10 @@ static ndgsbp_status make_stream_plan(const Groups& g, const ndgsbp_params* p, i
     const size_t budget = static_cast<size_t>(di.smem_optin) - 64;
     int best_mode = -1, best_per_sm = 0;
     size_t best_smem = 0;
-    for (int mode : {kStreamSmem, kStreamBulk, kStreamGlobal}) {
+    for (int mode : {kStreamSmem, kStreamGlobal, kStreamBulk}) {
         if (want >= 0 && mode != want) continue;
         if (mode == kStreamBulk && !bulk_ok) continue;
+        stream_bases(Q, msz, mode, a.lbase, &a.msg_elems, &a.slab_elems);
         const size_t smem = stream_smem_bytes(a, msz, mode);
         if (smem > budget) continue;
         StreamKernelFn fn = pick_stream_kernel(p->msg_dtype, LE, tpc, mode);
@@ -579,7 +587,11 @@ static ndgsbp_status make_stream_plan(const Groups& g, const ndgsbp_params* p, i
     if (st) return st;
     st = device_qc(g, flood, plan.Q, plan.DQ, allow_upload);
     if (st) return st;
-    const int ws_stride = static_cast<int>(align256(static_cast<size_t>(SL.msg_elems) * msz) / msz);
+    stream_bases(Q, msz, best_mode, a.lbase, &a.msg_elems, &a.slab_elems);
+    const int ws_stride = static_cast<int>(align256(static_cast<size_t>(a.msg_elems) * msz) / msz);
+    plan.stream_lbase.assign(a.lbase, a.lbase + Q.n_layers);
+    plan.stream_msg_elems = a.msg_elems;
+    plan.stream_slab_elems = a.slab_elems;
     plan.stream = true;
     plan.sfn = fn;
     plan.stream_mode = best_mode;
@@ -599,7 +611,7 @@ static ndgsbp_status make_stream_plan(const Groups& g, const ndgsbp_params* p, i
     o.smem_bytes = static_cast<int64_t>(best_smem);
     o.workspace_bytes = static_cast<int64_t>(
         kHeaderBytes + (best_mode == kStreamSmem ? 0 : align256(static_cast<size_t>(grid) * ws_stride * msz)));
-    o.stored_edges = SL.msg_elems;
+    o.stored_edges = a.msg_elems;
     o.edge_updates_per_iter = flood ? g.code->E : g.edge_updates;
     *ok = true;
     return NDGSBP_OK;
@@ -853,10 +865,12 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
         a.maxdeg = Q.max_deg;
         a.tpc = plan.stream_tpc;
         a.le = (Q.max_deg + plan.stream_tpc - 1) / plan.stream_tpc;
-        a.msg_elems = static_cast<int>(plan.pub.stored_edges);
+        a.zr = (Q.Z + 15) / 16 * 16;
+        a.msg_elems = plan.stream_msg_elems;
+        a.slab_elems = plan.stream_slab_elems;
+        for (size_t l = 0; l < plan.stream_lbase.size(); ++l) a.lbase[l] = plan.stream_lbase[l];
         a.edge_tab = reinterpret_cast<const int2*>(D.edge_tab);
         a.layer_deg = D.layer_deg;
-        a.layer_base = D.layer_base;
         a.group_layers = D.group_layers;
         a.first_use = D.first_use;
         a.layer_csr = D.layer_csr;
@@ -865,9 +879,6 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
         a.ws_msgs = plan.stream_mode == kStreamSmem ? nullptr : ws + kHeaderBytes;
         a.status = reinterpret_cast<unsigned*>(ws + 8);
         a.n_slabs = plan.stream_slabs;
-        int slab = 0;
-        for (int d : Q.layer_deg) slab = std::max(slab, d * Q.Z);
-        a.slab_elems = slab;
         a.ws_stride = plan.stream_ws_stride;
         a.wait_limit = 1u << 22;
         a.test_skip_load = 0;

@@ -12,9 +12,10 @@
 //   phase B: P += changes, position by position (a barrier after each), the fixed order of the
 //     other kernels -- with tpc = 1 the results equal the QC and tile kernels bit for bit, with
 //     tpc = 2 those of the tile kernel at 2 lanes per CN (the same lane split and pair products).
-// Messages are stored edge-major per layer: edge k of CN c of layer l at layer_base[l] + k Z + c,
-// so the lanes of a warp touch consecutive CNs (coalesced in global memory, conflict-free in
-// shared memory).  MODE picks where they live:
+// Messages are stored per layer, CN-major with an odd word stride in shared memory (each thread's
+// messages at compile-time offsets, consecutive CNs in distinct banks) and edge-major in global
+// memory (edge k of CN c at k Zr + c, Zr = Z rounded up to 16 elements: the lanes of a warp
+// write whole sectors); see stream_layer_elems.  MODE picks where they live:
 //   kStreamSmem:   the frame's messages in shared memory;
 //   kStreamGlobal: in the CTA's workspace slot (mostly L2-resident), read and written in place;
 //   kStreamBulk:   in the CTA's workspace slot, each layer's slab (d_l Z messages, one contiguous
@@ -106,11 +107,11 @@ __host__ __device__ constexpr size_t sa16(size_t x) { return (x + 15) & ~static_
 
 struct StreamSmem {
     float* P;          // [N] posterior (log2 units)
-    float* dbuf;       // [W - 1][maxdeg][Z] changes of positions 0 .. W-2 (row p le + k for lane p)
+    float* dbuf;       // [W - 1][Z][maxdeg | 1] changes of positions 0 .. W-2 (entry p le + k for lane p)
     unsigned char* msg;  // SMEM: [msg_elems] messages; BULK: [n_slabs][slab_elems] slab buffers
     int2* tab;         // [nl][maxdeg] edge table
     int* ldeg;         // [nl] layer degrees
-    int4* gtab;        // [n_groupings][G][W] (l maxdeg, d_l, layer_base[l], first use in iteration 1)
+    int4* gtab;        // [n_groupings][G][W] (l maxdeg, d_l, lbase[l], first use in iteration 1)
     uint64_t* bar;     // BULK: [n_slabs] one mbarrier per slab buffer
     size_t slab_bytes;
 };
@@ -122,7 +123,7 @@ __device__ __forceinline__ StreamSmem stream_smem(unsigned char* smem, const Str
     s.P = reinterpret_cast<float*>(smem);
     off += sa16(static_cast<size_t>(a.r.N) * 4);
     s.dbuf = reinterpret_cast<float*>(smem + off);
-    off += sa16(static_cast<size_t>(a.window - 1) * a.maxdeg * a.Z * 4);
+    off += sa16(static_cast<size_t>(a.window - 1) * (a.maxdeg | 1) * a.Z * 4);
     s.msg = smem + off;
     s.slab_bytes = sa16(static_cast<size_t>(a.slab_elems) * sizeof(MsgT));
     if (MODE == kStreamSmem) off += sa16(static_cast<size_t>(a.msg_elems) * sizeof(MsgT));
@@ -138,7 +139,7 @@ __device__ __forceinline__ StreamSmem stream_smem(unsigned char* smem, const Str
 }
 
 size_t stream_smem_bytes(const StreamArgs& a, int msg_size, int mode) {
-    size_t b = sa16(static_cast<size_t>(a.r.N) * 4) + sa16(static_cast<size_t>(a.window - 1) * a.maxdeg * a.Z * 4);
+    size_t b = sa16(static_cast<size_t>(a.r.N) * 4) + sa16(static_cast<size_t>(a.window - 1) * (a.maxdeg | 1) * a.Z * 4);
     const size_t slab = sa16(static_cast<size_t>(a.slab_elems) * msg_size);
     if (mode == kStreamSmem) b += sa16(static_cast<size_t>(a.msg_elems) * msg_size);
     if (mode == kStreamBulk) b += static_cast<size_t>(a.n_slabs) * slab;
@@ -148,39 +149,111 @@ size_t stream_smem_bytes(const StreamArgs& a, int msg_size, int mode) {
     return b;
 }
 
-// Eq. (1) for one lane of CN c (its L <= LE edges at edge-table entries et[0..L-1]) with the
+// Bytes of a layer's CN-major block (a bulk copy's size).
+template <typename MsgT>
+__device__ __forceinline__ unsigned stream_slab_bytes(int d, int Z) {
+    return static_cast<unsigned>(stream_layer_elems(d, Z, 0, sizeof(MsgT), kStreamBulk) * sizeof(MsgT));
+}
+
+// Eq. (1) for one lane of CN c (its L <= NP edges at edge-table entries et[0..L-1]) with the
 // messages of that lane at m[k Z], k < L: t = P - L_old (L_old = 0 on a layer's first use in
 // the frame), new messages written back to m, changes to drow[k Z] (shared delta buffer) or
-// dreg[k] (TO_REG).  The old message is read again from m when its change is formed rather
-// than held in a register through the pass.  Lanes of a CN (tpc = 2) run it together.
-template <typename MsgT, int LE, bool TO_REG>
-__device__ __forceinline__ void stream_lane(const int2* __restrict__ et, int L, int c, int Z, int Z4,
+// dreg[k] (TO_REG).  NP positions are computed: NP = L exactly (no predicates), or NP = LE with
+// the positions past L neutral (see lane_forward).  The old message is read again from m when
+// its change is formed rather than held in a register through the pass (fewer live registers;
+// measured faster).  Lanes of a CN (tpc = 2) run it together.
+template <typename MsgT, int LE, int NP, bool TO_REG>
+__device__ __forceinline__ void stream_lane(const int2* __restrict__ et, int L, int c, int Zm, int Zd, int Z4,
                                             const float* __restrict__ P, MsgT* m, bool first, float lim, int tpc,
                                             unsigned gmask, float* __restrict__ drow, float (&dreg)[LE]) {
-    float t[LE], xu[LE], pn[LE], pe[LE];
+    static_assert(NP <= LE, "positions above the lane width");
+    if (NP < LE) L = NP;   // exact instance: L is the constant NP
+    float t[NP], xu[NP], pn[NP], pe[NP];
     float cn = 1.f, ce = 0.f;
     unsigned lpar = 0u;
 #pragma unroll
-    for (int k = 0; k < LE; ++k) {
+    for (int k = 0; k < NP; ++k) {
         if (k < L) {
-            const float old = first ? 0.f : to_f(m[k * Z]);
+            const float old = first ? 0.f : to_f(m[k * Zm]);
             t[k] = at_b(const_cast<float*>(P), tile_vb(et[k], c, Z4)) - old;
         }
     }
-    lane_forward<LE>(t, L, lim, xu, pn, pe, cn, ce, lpar);
+    lane_forward<NP>(t, L, lim, xu, pn, pe, cn, ce, lpar);
     float on, oe;
     unsigned par;
     lane_exchange(tpc, gmask, cn, ce, lpar, on, oe, par);
-    lane_backward<LE>(xu, pn, pe, L, on, oe, par & 0x80000000u, lim, [&](int k, float val) {
+    lane_backward<NP>(xu, pn, pe, L, on, oe, par & 0x80000000u, lim, [&](int k, float val) {
         const MsgT q = from_f<MsgT>(val);
-        const float old = first ? 0.f : to_f(m[k * Z]);
-        m[k * Z] = q;
+        const float old = first ? 0.f : to_f(m[k * Zm]);
+        m[k * Zm] = q;
         const float d = to_f(q) - old;
         if (TO_REG)
             dreg[k] = d;
         else
-            drow[k * Z] = d;
+            drow[k * Zd] = d;
     });
+}
+
+// Exact-degree dispatch for a CN of degree d split into L-edge lanes: a layer's CNs share their
+// degree, so the branch is uniform across a warp (for tpc = 2 only when both lanes hold LE
+// edges); other degrees take the padded width-LE path.
+template <typename MsgT, int LE, int TPC, bool TO_REG>
+__device__ __forceinline__ void stream_lane_d(int d, const int2* __restrict__ et, int L, int c, int Zm, int Zd, int Z4,
+                                              const float* __restrict__ P, MsgT* m, bool first, float lim,
+                                              unsigned gmask, float* __restrict__ drow, float (&dreg)[LE]) {
+    if (d == TPC * LE)
+        stream_lane<MsgT, LE, LE, TO_REG>(et, LE, c, Zm, Zd, Z4, P, m, first, lim, TPC, gmask, drow, dreg);
+    else if (TPC == 1 && d == LE - 1)
+        stream_lane<MsgT, LE, LE - 1, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, gmask, drow, dreg);
+    else if (TPC == 1 && d == LE - 2)
+        stream_lane<MsgT, LE, LE - 2, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, gmask, drow, dreg);
+    else
+        stream_lane<MsgT, LE, LE, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, gmask, drow, dreg);
+}
+
+// P += changes of one lane, change k = src(k) for k < L: EXACT instances take L = NP (no
+// predicates).  src is a functor so that register arrays stay in registers.
+template <int NP, bool EXACT, typename Src>
+__device__ __forceinline__ void stream_add(float* __restrict__ P, const int2* __restrict__ et, int L, int c, int Z4,
+                                           Src src) {
+    if (EXACT) L = NP;
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+        if (k < L) at_b(P, tile_vb(et[k], c, Z4)) += src(k);
+}
+
+template <int LE, int TPC, typename Src>
+__device__ __forceinline__ void stream_add_d(int d, float* __restrict__ P, const int2* __restrict__ et, int L, int c,
+                                             int Z4, Src src) {
+    if (d == TPC * LE)
+        stream_add<LE, true>(P, et, L, c, Z4, src);
+    else if (TPC == 1 && d == LE - 1)
+        stream_add<LE - 1, true>(P, et, L, c, Z4, src);
+    else if (TPC == 1 && d == LE - 2)
+        stream_add<LE - 2, true>(P, et, L, c, Z4, src);
+    else
+        stream_add<LE, false>(P, et, L, c, Z4, src);
+}
+
+// Parity of the hard decisions on one lane's L edges, with the same dispatch.
+template <int NP, bool EXACT>
+__device__ __forceinline__ unsigned stream_parity(const float* __restrict__ P, const int2* __restrict__ et, int L,
+                                                  int c, int Z4) {
+    if (EXACT) L = NP;
+    unsigned pb = 0u;
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+        if (k < L) pb ^= (at_b(const_cast<float*>(P), tile_vb(et[k], c, Z4)) < 0.f) ? 1u : 0u;
+    return pb;
+}
+
+template <int LE, int TPC>
+__device__ __forceinline__ unsigned stream_parity_d(int d, const float* __restrict__ P, const int2* __restrict__ et,
+                                                    int L, int c, int Z4) {
+    if (d == TPC * LE) return stream_parity<LE, true>(P, et, L, c, Z4);
+    if (TPC == 1 && d == LE - 1) return stream_parity<LE - 1, true>(P, et, L, c, Z4);
+    if (TPC == 1 && d == LE - 2) return stream_parity<LE - 2, true>(P, et, L, c, Z4);
+    return stream_parity<LE, false>(P, et, L, c, Z4);
 }
 
 // Launch bounds: 2 resident CTAs of up to 384 threads (tpc = 1; 85 registers) or 512 (tpc = 2;
@@ -195,6 +268,8 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
     const RunArgs& r = a.r;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int Z = a.Z, Z4 = 4 * a.Z, W = a.window, nl = a.nl, md = a.maxdeg;
+    const int Zr = a.zr;   // global edge-major row stride (Z rounded up to 16 elements)
+    const int Sd = md | 1; // delta buffer: CN-major, odd stride
     const int le = a.le;   // edges per lane (<= LE): lane p holds edges [p le, (p + 1) le) of its CN
     const StreamSmem s = stream_smem<MsgT, MODE>(smem, a);
     float* P = s.P;
@@ -203,7 +278,7 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
     const int gw1 = a.G * W, gwk = gw1 * a.n_groupings;
     for (int i = tid; i < gwk; i += nt) {
         const int l = a.group_layers[i];
-        s.gtab[i] = make_int4(l * md, a.layer_deg[l], a.layer_base[l], i < gw1 ? a.first_use[i] : 0);
+        s.gtab[i] = make_int4(l * md, a.layer_deg[l], a.lbase[l], i < gw1 ? a.first_use[i] : 0);
     }
     if (MODE == kStreamBulk && tid == 0) {
         for (int b = 0; b < a.n_slabs; ++b) mbar_init(s.bar + b, 1);
@@ -254,8 +329,8 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
                         if (kg >= 1) {   // write back the layer that left the window (sequence kg - 1)
                             const int bo = kb == 0 ? S - 1 : kb - 1;
                             const int lo = a.ring[kr == 0 ? nl - 1 : kr - 1];
-                            bulk_store(gmsg + a.layer_base[lo], s.msg + static_cast<size_t>(bo) * s.slab_bytes,
-                                       static_cast<unsigned>(s.ldeg[lo] * Z * sizeof(MsgT)));
+                            bulk_store(gmsg + a.lbase[lo], s.msg + static_cast<size_t>(bo) * s.slab_bytes,
+                                       stream_slab_bytes<MsgT>(s.ldeg[lo], Z));
                         }
                         bulk_commit();
                         // the store committed one group ago (buffer bl) has completed
@@ -264,11 +339,11 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
                             int rl = kr + W;   // ring position of the new layer, (kr + W) mod nl
                             rl -= rl >= nl ? nl : 0;
                             const int ll = a.ring[rl];
-                            const unsigned bytes = static_cast<unsigned>(s.ldeg[ll] * Z * sizeof(MsgT));
+                            const unsigned bytes = stream_slab_bytes<MsgT>(s.ldeg[ll], Z);
                             mbar_arrive_expect_tx(s.bar + bl, bytes);
                             if (!(a.test_skip_load && kl == nl))
-                                bulk_load(s.msg + static_cast<size_t>(bl) * s.slab_bytes, gmsg + a.layer_base[ll],
-                                          bytes, s.bar + bl);
+                                bulk_load(s.msg + static_cast<size_t>(bl) * s.slab_bytes, gmsg + a.lbase[ll], bytes,
+                                          s.bar + bl);
                         }
                     }
                     if (kl >= nl) pend |= 1u << bl;
@@ -282,20 +357,24 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
                         const int2* et = s.tab + ge.x + p * le;
                         const bool first = it == 1 && ge.w;
                         MsgT* m;
-                        if constexpr (MODE == kStreamSmem)
-                            m = smsg + ge.z;
-                        else if constexpr (MODE == kStreamGlobal)
-                            m = gmsg + ge.z;
-                        else {
-                            const int bj = kb + j < S ? kb + j : kb + j - S;
-                            m = reinterpret_cast<MsgT*>(s.msg + static_cast<size_t>(bj) * s.slab_bytes);
-                        }
-                        m += p * le * Z + c;
-                        if (j == W - 1) {
-                            stream_lane<MsgT, LE, true>(et, L, c, Z, Z4, P, m, first, lim, TPC, gmask, nullptr, dreg);
+                        if constexpr (MODE == kStreamSmem) {
+                            m = smsg + ge.z + c * stream_cn_stride(ge.y, sizeof(MsgT)) + p * le;
+                        } else if constexpr (MODE == kStreamGlobal) {
+                            m = gmsg + ge.z + p * le * Zr + c;
                         } else {
-                            float* drow = s.dbuf + static_cast<size_t>(j * md + p * le) * Z + c;
-                            stream_lane<MsgT, LE, false>(et, L, c, Z, Z4, P, m, first, lim, TPC, gmask, drow, dreg);
+                            const int bj = kb + j < S ? kb + j : kb + j - S;
+                            m = reinterpret_cast<MsgT*>(s.msg + static_cast<size_t>(bj) * s.slab_bytes) +
+                                c * stream_cn_stride(ge.y, sizeof(MsgT)) + p * le;
+                        }
+                        // row stride of a thread's messages: 1 (CN-major) or Zr (edge-major)
+                        const int Zm = MODE == kStreamGlobal ? Zr : 1;
+                        if (j == W - 1) {
+                            stream_lane_d<MsgT, LE, TPC, true>(ge.y, et, L, c, Zm, 1, Z4, P, m, first, lim, gmask,
+                                                               nullptr, dreg);
+                        } else {
+                            float* drow = s.dbuf + static_cast<size_t>(j * Z + c) * Sd + p * le;
+                            stream_lane_d<MsgT, LE, TPC, false>(ge.y, et, L, c, Zm, 1, Z4, P, m, first, lim, gmask,
+                                                                drow, dreg);
                         }
                     }
                     if constexpr (MODE == kStreamBulk) fence_async_shared();   // slabs written before their store
@@ -308,14 +387,10 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
                         const int L = min(max(ge.y - p * le, 0), le);
                         const int2* et = s.tab + ge.x + p * le;
                         if (jj == W - 1) {
-#pragma unroll
-                            for (int k = 0; k < LE; ++k)
-                                if (k < L) at_b(P, tile_vb(et[k], c, Z4)) += dreg[k];
+                            stream_add_d<LE, TPC>(ge.y, P, et, L, c, Z4, [&](int k) { return dreg[k]; });
                         } else {
-                            const float* drow = s.dbuf + static_cast<size_t>(jj * md + p * le) * Z + c;
-#pragma unroll
-                            for (int k = 0; k < LE; ++k)
-                                if (k < L) at_b(P, tile_vb(et[k], c, Z4)) += drow[k * Z];
+                            const float* drow = s.dbuf + static_cast<size_t>(jj * Z + c) * Sd + p * le;
+                            stream_add_d<LE, TPC>(ge.y, P, et, L, c, Z4, [&](int k) { return drow[k]; });
                         }
                     }
                     __syncthreads();
@@ -338,11 +413,9 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
                 for (int l = 0; l < nl; ++l) {
                     unsigned pb = 0u;
                     if (active) {
-                        const int L = min(max(s.ldeg[l] - p * le, 0), le);
-                        const int2* et = s.tab + l * md + p * le;
-#pragma unroll
-                        for (int k = 0; k < LE; ++k)
-                            if (k < L) pb ^= (at_b(P, tile_vb(et[k], c, Z4)) < 0.f) ? 1u : 0u;
+                        const int d = s.ldeg[l];
+                        const int L = min(max(d - p * le, 0), le);
+                        pb = stream_parity_d<LE, TPC>(d, P, s.tab + l * md + p * le, L, c, Z4);
                     }
                     if (TPC == 2) pb ^= __shfl_xor_sync(gmask, pb, 1);
                     bad |= pb;
@@ -371,8 +444,8 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
                     for (int j = 0; j < W; ++j) {
                         const int kk = kg - 1 + j;
                         const int lj = a.ring[kk % nl];
-                        bulk_store(gmsg + a.layer_base[lj], s.msg + static_cast<size_t>(kk % S) * s.slab_bytes,
-                                   static_cast<unsigned>(s.ldeg[lj] * Z * sizeof(MsgT)));
+                        bulk_store(gmsg + a.lbase[lj], s.msg + static_cast<size_t>(kk % S) * s.slab_bytes,
+                                   stream_slab_bytes<MsgT>(s.ldeg[lj], Z));
                     }
                 }
                 bulk_commit();
@@ -390,10 +463,12 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
                 const int csr = a.layer_csr[l];
                 const int cb = csr < 0 ? -csr - 1 : csr;
                 const bool zero = csr < 0 || invalid;
-                const MsgT* src = (MODE == kStreamSmem ? smsg : gmsg) + a.layer_base[l];
+                const MsgT* src = (MODE == kStreamSmem ? smsg : gmsg) + a.lbase[l];
+                const int S_l = stream_cn_stride(d, sizeof(MsgT));
                 for (int i = tid; i < d * Z; i += nt) {
                     const int rr = i / Z, cc = i - rr * Z;
-                    r.msgs_out[f * r.E + cb + cc * d + rr] = zero ? 0.f : to_f(src[i]) * kLn2;
+                    const int at = MODE == kStreamGlobal ? rr * Zr + cc : cc * S_l + rr;
+                    r.msgs_out[f * r.E + cb + cc * d + rr] = zero ? 0.f : to_f(src[at]) * kLn2;
                 }
             }
         }

@@ -14,18 +14,30 @@ constexpr int kStreamGlobal = 1;   // in the CTA's workspace slot, read and writ
 constexpr int kStreamBulk = 2;     // in the CTA's workspace slot, layer slabs staged in shared memory
                                    // by cp.async.bulk (see decode_stream.cu)
 
-// Largest number of layer slabs a bulk-staged launch keeps in shared memory.
+// Largest number of layer slabs a bulk-staged launch keeps in shared memory, and of layers.
 constexpr int kStreamMaxSlabs = 8;
+constexpr int kStreamMaxLayers = 64;
+
+// Message layout of one layer.  In shared memory (SMEM) and in the slabs of BULK launches the
+// messages are CN-major: edge k of CN c at c S + k with S = stream_cn_stride(d) (an odd number of
+// 4-byte words for FP32; d for 16-bit messages, an odd number of words whenever d/2 is odd), so
+// each thread's messages sit at compile-time offsets and 32 consecutive CNs hit distinct banks.
+// In global memory (GLOBAL) they are edge-major: edge k of CN c at k zr + c, coalesced across the
+// CNs of a warp.  A layer's block is rounded up to 16 bytes (a bulk copy's granularity).
+__host__ __device__ constexpr int stream_cn_stride(int d, int msg_size) { return msg_size == 4 ? (d | 1) : d; }
+__host__ __device__ constexpr int stream_layer_elems(int d, int Z, int zr, int msg_size, int mode) {
+    return mode == kStreamGlobal ? d * zr : (Z * stream_cn_stride(d, msg_size) * msg_size + 15) / 16 * 16 / msg_size;
+}
 
 struct StreamArgs {
     RunArgs r;
     int Z, nl, G, window, maxdeg, n_groupings;
     int tpc;                      // lanes per CN (1 or 2)
     int le;                       // edges per lane, ceil(maxdeg / tpc) (<= the instance's width)
-    int msg_elems;                // messages per frame: sum over layers of d_l Z
+    int zr;                       // global edge-major row stride: Z rounded up to a multiple of 16
+    int msg_elems;                // message elements per frame: sum of the layers' blocks
     const int2* edge_tab;         // [nl][maxdeg]: (4 (b Z + s), Z - s) of edge k of the layer
     const int32_t* layer_deg;     // [nl]
-    const int32_t* layer_base;    // [nl] first message of layer l: edge k of CN c at base + k Z + c
     const int32_t* group_layers;  // [n_groupings][G][window]
     const int32_t* first_use;     // [G][window] 1: grouping 0's group g is the first to use that
                                   // layer (iteration 1 reads no messages there: they are 0)
@@ -37,9 +49,10 @@ struct StreamArgs {
     // BULK only: group g of an iteration holds ring positions g .. g + window - 1 (mod nl)
     const int32_t* ring;          // [nl] layer at each ring position
     int n_slabs;                  // window + 2 slab buffers in shared memory
-    int slab_elems;               // elements per slab buffer (the largest d_l Z)
+    int slab_elems;               // elements per slab buffer (the largest layer block)
     unsigned wait_limit;          // polls before a bounded wait gives up
     int test_skip_load;           // test hook: 1 = arm the first load's barrier but issue no copy
+    int lbase[kStreamMaxLayers];  // first message element of each layer's block (stream_layer_elems)
 };
 
 typedef void (*StreamKernelFn)(const StreamArgs);

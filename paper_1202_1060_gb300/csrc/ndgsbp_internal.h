@@ -94,7 +94,6 @@ struct DeviceQc {
     const int32_t* group_layers = nullptr;
     const int32_t* csr_of = nullptr;
     // stream kernel tables (see StreamLayout in decode.cu)
-    const int32_t* layer_base = nullptr;
     const int32_t* first_use = nullptr;
     const int32_t* layer_csr = nullptr;
     const int32_t* ring = nullptr;
