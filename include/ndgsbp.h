@@ -467,6 +467,29 @@ ndgsbp_status ndgsbp_ga_flood_threshold(const double* lambda, int32_t dv_max, co
                                         int32_t max_iter, double mu_cap, double lo_db, double hi_db,
                                         double tol_db, double* threshold_db);
 
+/* The GA recursion for the group schedules of Sec. III: G groups (1..64) with overlap ratio r in
+ * [0, 1) (r = 0: disjoint groups, GSBP).  Per iteration and group g = 1..G the mean of a VN's
+ * other CN messages mixes class a (not updated yet in this iteration, mean mu_c of the previous
+ * iteration), class b (the overlap with group g - 1, fraction z = r / D of Eq. (12)) and class d
+ * (updated, fraction x = 1 / D for g = 1 (Eq. (10)) and y = g (1 - r) / D otherwise (Eq. (11)),
+ * with mean from Eqs. (6)-(7)), D = G - (G - 1) r; Eq. (8) with the weights of Eq. (9) is then
+ * mu0 + (i - 1)(y mu_d + z mu_b + (1 - y - z) mu_a) since it is linear in (p, q).  The group's
+ * class-c CN output follows Eqs. (15)-(16); a class-b CN (g >= 2, r > 0) uses the weights of
+ * Eq. (9) restricted to p >= 1 (at least one updated neighbour).  Eq. (17) gives the iteration's
+ * mean.  Readings of points the paper leaves open: the current group's own term in Eqs. (6)-(7)
+ * is its output of the previous iteration (what its fresh CNs hold during the sub-iteration), and
+ * for g = 1 class d is group 1's previous output.  Inputs, outputs and stop rule as
+ * ndgsbp_ga_flood.  Synchronous; allocates device memory.  Errors: INVALID, CUDA. */
+ndgsbp_status ndgsbp_ga_groups(const double* lambda, int32_t dv_max, const double* rho, int32_t dc_max, double rate,
+                               int32_t G, double r, const double* ebn0_db, int32_t n_points, int32_t phi_kind,
+                               int32_t max_iter, double mu_cap, uint8_t* converged, int32_t* iters, double* mu_c);
+/* GA threshold of the group schedule, found as by ndgsbp_ga_flood_threshold.
+ * Errors: INVALID, INFEASIBLE, CUDA. */
+ndgsbp_status ndgsbp_ga_groups_threshold(const double* lambda, int32_t dv_max, const double* rho, int32_t dc_max,
+                                         double rate, int32_t G, double r, int32_t phi_kind, int32_t max_iter,
+                                         double mu_cap, double lo_db, double hi_db, double tol_db,
+                                         double* threshold_db);
+
 /* ---- Decoding without allocating (the paper has no counterpart) ---------------------------
  * ndgsbp_decode_static is ndgsbp_decode without a workspace: it allocates no device memory.  It
  * is for callers that cannot allocate while they decode -- a real-time receive loop that may

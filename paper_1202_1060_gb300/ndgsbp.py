@@ -128,6 +128,9 @@ _SIGS = {
     "ndgsbp_ragged_autotune": (_I32, [_P, _I32, ctypes.POINTER(Params), _I64, ctypes.c_char_p,
                                       ctypes.POINTER(Params), ctypes.POINTER(_D)]),
     "ndgsbp_ga_flood": (_I32, [_P, _I32, _P, _I32, _D, _P, _I32, _I32, _I32, _D, _P, _P, _P]),
+    "ndgsbp_ga_groups": (_I32, [_P, _I32, _P, _I32, _D, _I32, _D, _P, _I32, _I32, _I32, _D, _P, _P, _P]),
+    "ndgsbp_ga_groups_threshold": (_I32, [_P, _I32, _P, _I32, _D, _I32, _D, _I32, _I32, _D, _D, _D, _D,
+                                          ctypes.POINTER(_D)]),
     "ndgsbp_ga_flood_threshold": (_I32, [_P, _I32, _P, _I32, _D, _I32, _I32, _D, _D, _D, _D,
                                          ctypes.POINTER(_D)]),
     "ndgsbp_server_create": (_I32, [_P, _I32, _P, ctypes.POINTER(Params), ctypes.c_size_t, _I32,
@@ -564,6 +567,33 @@ def ga_flood_threshold(lam: dict, rho: dict, rate: float, phi_kind: int = GA_PHI
     _check(_lib.ndgsbp_ga_flood_threshold(_hptr(la), dv, _hptr(ra), dc, float(rate), int(phi_kind), int(max_iter),
                                           float(mu_cap), float(lo_db), float(hi_db), float(tol_db),
                                           ctypes.byref(out)))
+    return out.value
+
+
+def ga_groups(lam: dict, rho: dict, rate: float, G: int, r: float, ebn0_db, phi_kind: int = GA_PHI_EXACT,
+              max_iter: int = 20000, mu_cap: float = 60.0):
+    """ndgsbp_ga_groups: (converged bool [n], iterations int [n], mu_c [n]) for each Eb/N0."""
+    la, dv = _degree_array(lam)
+    ra, dc = _degree_array(rho)
+    e = np.ascontiguousarray(np.atleast_1d(ebn0_db), np.float64)
+    n = e.size
+    cv = np.zeros(n, np.uint8)
+    it = np.zeros(n, np.int32)
+    mu = np.zeros(n, np.float64)
+    _check(_lib.ndgsbp_ga_groups(_hptr(la), dv, _hptr(ra), dc, float(rate), int(G), float(r), _hptr(e), n,
+                                 int(phi_kind), int(max_iter), float(mu_cap), _hptr(cv), _hptr(it), _hptr(mu)))
+    return cv.astype(bool), it, mu
+
+
+def ga_groups_threshold(lam: dict, rho: dict, rate: float, G: int, r: float, phi_kind: int = GA_PHI_EXACT,
+                        lo_db: float = 0.0, hi_db: float = 3.0, tol_db: float = 1e-4, max_iter: int = 20000,
+                        mu_cap: float = 60.0) -> float:
+    la, dv = _degree_array(lam)
+    ra, dc = _degree_array(rho)
+    out = ctypes.c_double()
+    _check(_lib.ndgsbp_ga_groups_threshold(_hptr(la), dv, _hptr(ra), dc, float(rate), int(G), float(r), int(phi_kind),
+                                           int(max_iter), float(mu_cap), float(lo_db), float(hi_db), float(tol_db),
+                                           ctypes.byref(out)))
     return out.value
 
 
