@@ -40,8 +40,10 @@ GROUP_SEED = 2304
 CHANNEL_SEED = 0x5EED0000
 RATE = 0.5
 MUFU_PER_EDGE_UPDATE = 3          # exp2, reciprocal, log2 per edge of Eq. (1)
-MUFU_PER_CLK_PER_SM = 32          # MUFU results per clock per SM sustained on GB300 (one warp
-                                  # instruction per clock per SM, the XU-pipe peak ncu normalises to)
+MUFU_PER_CLK_PER_SM = 32          # nominal MUFU results per clock per SM (one warp instruction per
+                                  # clock per SM, the XU-pipe peak ncu normalises to); the roofline
+                                  # uses the rate measured by ndgsbp_mufu_probe
+LATENCY_POINT = 5                 # EBN0[5] = 1.75 dB, the FER ~ 1e-3 point of the n=2304 code
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "qc_decode_kernel_n2304_sweep.md")
 
 
@@ -251,6 +253,112 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------
+# extras of the default line (outside its timed region)
+# ------------------------------------------------------------------------------------------
+def mufu_peak(nd, torch, dev, sms, sm_mhz, iters=8192):
+    """Rates of ex2 / rcp / lg2 (.approx, FP32) from ndgsbp_mufu_probe on a full grid (2 CTAs of
+    1024 threads per SM, 8 independent chains per thread), CUDA-event timed on the probe's stream,
+    and the rate of the decode kernels' 1:1:1 mix (equal counts: the harmonic mean)."""
+    blocks, threads = 2 * sms, 1024
+    sink = torch.zeros(blocks, dtype=torch.float32, device=dev)
+    st = torch.cuda.Stream(device=dev)
+    out, inv = {}, 0.0
+    for op, name in enumerate(("ex2", "rcp", "lg2")):
+        nd.mufu_probe(op, iters // 8, blocks, threads, sink, stream=st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        nd.mufu_probe(op, iters, blocks, threads, sink, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        rate = blocks * threads * iters * 8 / sec
+        inv += 1.0 / rate
+        out[name] = {"tops": rate / 1e12, "per_clk_per_sm": rate / (sms * sm_mhz * 1e6), "ms": 1e3 * sec}
+    mix = 3.0 / inv
+    out.update({"mix_tops": mix / 1e12, "mix_per_clk_per_sm": mix / (sms * sm_mhz * 1e6), "sm_mhz": sm_mhz,
+                "what": f"{blocks} x {threads} threads x {iters} rounds x 8 chains per op"})
+    return out
+
+
+def flood_equal_budget(nd, torch, dev, code, c, F, stream, rank):
+    """Flooding at I_max 50 beside NDGSBP (12 cyclic 2-layer windows) at I_max 25 on the same frames
+    (the first timed step's channel seeds): both spend 50 M CN updates per frame at most (Sec. IV,
+    equal check-update budget).  Per Eb/N0 point: FER, mean iterations, decode-only Gbit/s."""
+    import numpy as np
+    groups = nd.Groups.build(code, 12, 0.5, GROUP_SEED, unit=nd.UNIT_LAYER, flags=nd.GROUPS_CYCLIC)
+    W = (c.N + 31) // 32
+    llr = torch.empty((F, c.N), dtype=torch.float32, device=dev)
+    hard = torch.empty((F, W), dtype=torch.int32, device=dev)
+    out = {}
+    for name, sched, imax in (("ndgsbp", nd.SCHEDULE_GROUPS, IMAX_ND), ("flooding", nd.SCHEDULE_FLOOD, IMAX_FLOOD)):
+        p = nd.params_default(max_iter=imax, msg_dtype=nd.F32, schedule=sched)
+        ws = torch.zeros(max(256, groups.workspace_size(p, F)), dtype=torch.uint8, device=dev)
+        stats = torch.zeros((len(EBN0), nd.STATS_LEN), dtype=torch.int64, device=dev)
+        nd.awgn_llr(code, F, EBN0[0], RATE, channel_seed(0, 0, rank), llr, stream=stream)
+        nd.decode(groups, p, llr, ws, hard, stream=stream)   # warm-up
+        ms = 0.0
+        for i, eb in enumerate(EBN0):
+            nd.awgn_llr(code, F, eb, RATE, channel_seed(i, 0, rank), llr, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nd.decode(groups, p, llr, ws, hard, stats=stats[i], stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        st = stats.cpu().numpy()
+        fe = st[:, nd.STAT_FRAME_ERRORS]
+        out[name] = {"max_iter": imax, "fer": (fe / F).tolist(),
+                     "fer_ci95": [list(clopper_pearson(int(k), F)) for k in fe],
+                     "mean_iterations": (st[:, nd.STAT_ITERATIONS] / F).tolist(),
+                     "cn_updates_per_iter": int(c.M if sched == nd.SCHEDULE_FLOOD else groups.query()["cn_updates_per_iter"]),
+                     "gbit_s": F * len(EBN0) * (c.N - c.M) / (ms / 1e3) / 1e9,
+                     "plan": groups.plan(p, F).as_dict()["variant"]}
+    out["what"] = (f"{F} frames per point, the same channel LLRs for both schedules; equal budget: NDGSBP "
+                   f"{IMAX_ND} x {out['ndgsbp']['cn_updates_per_iter']} = flooding {IMAX_FLOOD} x {c.M} CN updates")
+    return out
+
+
+def precision_summary(nd, torch, dev, I, F):
+    """FP32 / FP16 / BF16 message storage on the n=2304 r1/2 and n=16200 r2/3 codes at each code's
+    FER ~ 1e-3 point: FER with its 95% Clopper-Pearson interval, decode-only Gbit/s (one timed
+    launch after a warm-up), and FP16 / FP32 throughput."""
+    out = {}
+    st_ = torch.cuda.Stream(device=dev)
+    for name in ("qc_n2304_r12", "qc_n16200_r23"):
+        c, code, g = _setup_code(nd, I, name)
+        eb = FER1E3_EBN0[name]
+        W = (c.N + 31) // 32
+        llr = torch.empty((F, c.N), dtype=torch.float32, device=dev)
+        nd.awgn_llr(code, F, eb, I.design_rate(c), CHANNEL_SEED + c.N, llr, stream=st_)
+        hard = torch.empty((F, W), dtype=torch.int32, device=dev)
+        rows = {}
+        for msg, dt in (("f32", nd.F32), ("f16", nd.F16), ("bf16", nd.BF16)):
+            p = nd.params_default(max_iter=IMAX_ND, msg_dtype=dt)
+            ws = torch.zeros(max(256, g.workspace_size(p, F)), dtype=torch.uint8, device=dev)
+            stats = torch.zeros(nd.STATS_LEN, dtype=torch.int64, device=dev)
+            nd.decode(g, p, llr, ws, hard, stream=st_)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st_)
+            nd.decode(g, p, llr, ws, hard, stats=stats, stream=st_)
+            e1.record(st_)
+            torch.cuda.synchronize()
+            s = stats.cpu().numpy()
+            fe = int(s[nd.STAT_FRAME_ERRORS])
+            rows[msg] = {"fer": fe / F, "fer_ci95": list(clopper_pearson(fe, F)),
+                         "mean_iterations": float(s[nd.STAT_ITERATIONS] / F),
+                         "gbit_s": F * (c.N - c.M) / (e0.elapsed_time(e1) / 1e3) / 1e9,
+                         "variant": g.plan(p, F).variant}
+            del ws
+        rows["f16_over_f32"] = rows["f16"]["gbit_s"] / rows["f32"]["gbit_s"]
+        rows["bf16_over_f32"] = rows["bf16"]["gbit_s"] / rows["f32"]["gbit_s"]
+        rows["ebn0_db"] = eb
+        out[name] = rows
+        del llr
+    out["what"] = f"{F} frames per code, the same LLRs for the three storage types, I_max {IMAX_ND}"
+    return out
+
+
+# ------------------------------------------------------------------------------------------
 # GPU leg
 # ------------------------------------------------------------------------------------------
 def run_ours(args):
@@ -298,8 +406,9 @@ def run_ours(args):
             if timing is not None:
                 timing.append(torch.cuda.Event(enable_timing=True))
                 timing[-1].record(stream)
+            stamp = latency and i == LATENCY_POINT
             nd.decode(groups, params, llr, ws, hard, iters, ok, stats=stats[i], iter_hist=hist,
-                      start_ns=start_ns if latency else None, retire_ns=retire_ns if latency else None,
+                      start_ns=start_ns if stamp else None, retire_ns=retire_ns if stamp else None,
                       stream=stream)
             if timing is not None:
                 timing.append(torch.cuda.Event(enable_timing=True))
@@ -349,14 +458,16 @@ def run_ours(args):
     service = (r_ns - s_ns) / 1e6
     batch = (r_ns - s_ns.min()) / 1e6
 
-    # roofline of the decode kernel: MUFU operations (3 per edge-update) over its launch time
+    # roofline of the decode kernel: MUFU operations (3 per edge-update) over its launch time,
+    # against the XU-pipe rate measured on this GPU for the kernel's 1:1:1 mix of ex2, rcp, lg2
     peaks, peak_kind = measured_peaks()
     dec_total_s = sum(dec_ms) / 1e3
     mufu_ops = MUFU_PER_EDGE_UPDATE * edge_updates_iter * iter_sum
     achieved = mufu_ops / dec_total_s / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = MUFU_PER_CLK_PER_SM * sms * peak_clock_mhz * 1e6 / 1e12
+    probe = mufu_peak(nd, torch, dev, sms, clk.get("sm_mhz") or peak_clock_mhz)
+    peak = probe["mix_tops"]
     kname = {nd.VARIANT_QC: "qc_decode_kernel", nd.VARIANT_QC_GLOBAL: "qc_decode_kernel",
              nd.VARIANT_TILE: "tile_decode_kernel", nd.VARIANT_STREAM_SMEM: "stream_decode_kernel",
              nd.VARIANT_STREAM_GLOBAL: "stream_decode_kernel",
@@ -366,14 +477,22 @@ def run_ours(args):
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
         "traffic": traffic,
         "what": f"MUFU ops (exp2+rcp+lg2 = {MUFU_PER_EDGE_UPDATE} per edge-update of Eq. (1)) of the decode "
-                f"kernel over its CUDA-event time; peak = {MUFU_PER_CLK_PER_SM} MUFU/clk/SM x {sms} SMs x "
-                f"{peak_clock_mhz:.0f} MHz (clock from MEASURED_PEAKS.json, {peak_kind})",
+                f"kernel over its CUDA-event time; peak = the XU-pipe rate of that 1:1:1 mix measured by "
+                f"ndgsbp_mufu_probe on this GPU (per-op rates in mufu_probe); nominal "
+                f"{MUFU_PER_CLK_PER_SM}/clk/SM x {sms} SMs x {peak_clock_mhz:.0f} MHz = "
+                f"{MUFU_PER_CLK_PER_SM * sms * peak_clock_mhz * 1e6 / 1e12:.2f} Top/s",
+        "mufu_probe": probe,
         "kernel": kname, "launches": len(dec_ms), "avg_launch_ms": sum(dec_ms) / len(dec_ms),
         "share_of_step": sum(dec_ms) / 1e3 / elapsed,
         "edge_updates_per_launch": edge_updates_iter * iter_sum / len(dec_ms),
         "hbm_bytes_per_launch_algorithmic": F * (c.N * 4 + W * 4 + 5),
         "hbm_frac_of_measured": F * (c.N * 4 + W * 4 + 5) / (sum(dec_ms) / len(dec_ms) / 1e3) / 1e9 / peaks["hbm_gbs"],
     }
+
+    # beside the timed line: flooding at the same check-update budget (Sec. IV), and the message
+    # precisions at each code's FER ~ 1e-3 point
+    flood = None if args.no_extras else flood_equal_budget(nd, torch, dev, code, c, F, stream, rank)
+    precision = None if args.no_extras else precision_summary(nd, torch, dev, I, args.extras_frames)
 
     # end-to-end through host buffers: pinned host LLRs -> device -> decode -> decisions back
     e2e = None
@@ -410,12 +529,14 @@ def run_ours(args):
                         "batch_p50_ms": float(np.percentile(batch, 50)),
                         "batch_p99_ms": float(np.percentile(batch, 99)),
                         "what": "service = frame retire - frame start; batch = frame retire - launch start "
-                                "(last timed decode launch, 65,536 frames at 2.5 dB)"},
+                                f"(the {EBN0[LATENCY_POINT]} dB decode launch of the last timed step, the FER ~ 1e-3 "
+                                f"point, {F} frames)"},
             "fer": fer, "ber": ber, "mean_iterations": iter_sum / max(frames_done, 1),
             "mean_iterations_per_point": (st[:, nd.STAT_ITERATIONS] / np.maximum(st[:, nd.STAT_FRAMES], 1)).tolist(),
             "coded_gbit_s": frames_total * c.N / elapsed_max / 1e9,
             "clocks": clk, "gpu_launches": 2 * len(EBN0) * args.steps,
             "plan": plan.as_dict(), "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "flooding_equal_budget": flood, "precision": precision,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -916,6 +1037,8 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=64, help="oracle frames per point per reference step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the flooding and precision extras")
+    ap.add_argument("--extras-frames", type=int, default=65536, help="frames per code and dtype, precision extra")
     ap.add_argument("--workload", choices=["sweep", "ragged", "serving", "precision"], default="sweep",
                     help="sweep = the default n=2304 Eb/N0 sweep line; the others are supplementary")
     ap.add_argument("--precision-frames", type=int, default=262144)

@@ -490,6 +490,14 @@ ndgsbp_status ndgsbp_ga_groups_threshold(const double* lambda, int32_t dv_max, c
                                          double mu_cap, double lo_db, double hi_db, double tol_db,
                                          double* threshold_db);
 
+/* ---- Measurement aid (the paper has no counterpart) ----------------------------------------
+ * Launch `blocks` x `threads` threads that each run iters x 8 independent FP32 MUFU operations of
+ * kind op (0: ex2.approx, 1: rcp.approx, 2: lg2.approx -- the three of each edge-update of Eq. (1))
+ * on `stream`, for timing the XU pipe's rate with events around the launch.  d_sink: a device
+ * buffer of `blocks` floats (never written in practice).  Errors: INVALID, CUDA. */
+ndgsbp_status ndgsbp_mufu_probe(int32_t op, int64_t iters, int32_t blocks, int32_t threads, float* d_sink,
+                                void* stream);
+
 /* ---- Decoding without allocating (the paper has no counterpart) ---------------------------
  * ndgsbp_decode_static is ndgsbp_decode without a workspace: it allocates no device memory.  It
  * is for callers that cannot allocate while they decode -- a real-time receive loop that may

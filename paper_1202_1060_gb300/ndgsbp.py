@@ -118,6 +118,7 @@ _SIGS = {
                                 _P, _P, _P, _P, ctypes.POINTER(Extras), _P]),
     "ndgsbp_decode_static": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, _P, _P, _P, _P]),
     "ndgsbp_workspace_status": (_I32, [_P, ctypes.POINTER(_U32), _P]),
+    "ndgsbp_mufu_probe": (_I32, [_I32, _I64, _I32, _I32, _P, _P]),
     "ndgsbp_ragged_create": (_I32, [_P, _I32, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
     "ndgsbp_ragged_info": (_I32, [_P, ctypes.POINTER(Plan), _P]),
     "ndgsbp_ragged_launch": (_I32, [_P, _P]),
@@ -391,6 +392,11 @@ def workspace_status(workspace, stream=None) -> int:
     v = ctypes.c_uint32(0)
     _check(_lib.ndgsbp_workspace_status(_dptr(workspace), ctypes.byref(v), _stream(stream)))
     return int(v.value)
+
+
+def mufu_probe(op: int, iters: int, blocks: int, threads: int, sink, stream=None):
+    """ndgsbp_mufu_probe: blocks x threads x iters x 8 MUFU operations of kind op (0 ex2, 1 rcp, 2 lg2)."""
+    _check(_lib.ndgsbp_mufu_probe(int(op), int(iters), int(blocks), int(threads), _dptr(sink), _stream(stream)))
 
 
 def _batch_array(batches):
