@@ -651,14 +651,16 @@ def _setup_code(nd, I, name, seed=2304):
     return c, code, g
 
 
-def _mufu_roofline(peaks, peak_kind, sms, mufu_ops, kernel_s, kernel, launches, extra=None):
-    peak_clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = MUFU_PER_CLK_PER_SM * sms * peak_clock_mhz * 1e6 / 1e12
+def _mufu_roofline(probe, mufu_ops, kernel_s, kernel, launches, extra=None):
+    """MUFU roofline of a decode workload: mufu_ops (3 per edge-update, counted over the timed
+    launches) over their CUDA-event time, against the measured rate of the 1:1:1 MUFU mix."""
+    peak = probe["mix_tops"]
     achieved = mufu_ops / kernel_s / 1e12
     r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
          "traffic": None, "kernel": kernel, "launches": launches, "avg_launch_ms": 1e3 * kernel_s / launches,
-         "what": f"MUFU ops (3 per edge-update of Eq. (1)) over the kernel's CUDA-event time; peak = "
-                 f"{MUFU_PER_CLK_PER_SM} MUFU/clk/SM x {sms} SMs x {peak_clock_mhz:.0f} MHz ({peak_kind})"}
+         "mufu_probe": probe,
+         "what": "MUFU ops (3 per edge-update of Eq. (1)) over the kernels' CUDA-event time; peak = the measured "
+                 "rate of the ex2/rcp/lg2 mix (ndgsbp_mufu_probe)"}
     if extra:
         r.update(extra)
     return r
@@ -797,9 +799,10 @@ def run_ragged(args):
                                         "plan": plan,
                                         "other_mode_ms": other_ms},
         "clocks": clk, "gpu_launches": (8 if per_code_mode else 5) * args.steps,
-        "roofline": _mufu_roofline(peaks, kind, sms, mufu * args.steps, dec_s,
-                                   "per-code launches (qc_decode_kernel for n=576/1152/2304, tile_decode_kernel for "
-                                   "n=8192) on forked streams" if per_code_mode else "tile_decode_kernel",
+        # (mufu counts the timed launches: the replayed graph carries the statistics pointers)
+        "roofline": _mufu_roofline(mufu_peak(nd, torch, dev, sms, clk.get("sm_mhz") or 2070.0), mufu, dec_s,
+                                   "per-code launches (qc_decode_kernel for n=576/1152/2304, stream_decode_kernel "
+                                   "for n=8192) on forked streams" if per_code_mode else "tile_decode_kernel",
                                    args.steps),
         "e2e": None, "cpu_baseline": None,
     }
@@ -958,20 +961,26 @@ def run_serving(args):
 
 def run_precision(args):
     """Reduced-precision messages: the n=2304 r1/2 and n=16200 r2/3 QC codes at their FER ~ 1e-3
-    points, 262,144 frames, FP32 / FP16 / BF16 message storage with FP32 arithmetic."""
+    points, 262,144 frames, FP32 / FP16 / BF16 message storage with FP32 arithmetic.  The FP64
+    oracle decodes the first --precision-oracle-frames (n=2304) and a quarter of that (n=16200) of
+    the same LLRs: every storage type's FER on those frames must lie inside the oracle's 95%
+    Clopper-Pearson interval, and so must its FER over all frames."""
     import numpy as np
     import torch
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     import __graft_entry__
     __graft_entry__.build_library()
+    from oracle import oracle as O
     from paper_1202_1060_gb300 import inputs as I
     from paper_1202_1060_gb300 import ndgsbp as nd
+    O.build()
     stream = torch.cuda.Stream(device=dev)
     F = args.precision_frames
-    rows = []
+    rows, oracle_rows = [], []
     clocks = ClockSampler(0)
     clocks.start()
+    mufu_total = {}
     for name in ("qc_n2304_r12", "qc_n16200_r23"):
         c, code, g = _setup_code(nd, I, name)
         eb = FER1E3_EBN0[name]
@@ -983,6 +992,20 @@ def run_precision(args):
         ok = torch.empty(F, dtype=torch.uint8, device=dev)
         stats = torch.zeros(nd.STATS_LEN, dtype=torch.int64, device=dev)
         q = g.query()
+        n_or = args.precision_oracle_frames if c.N <= 2304 else args.precision_oracle_frames // 4
+        n_or = min(n_or, F)
+        # the oracle on the first n_or frames of the same LLRs (FP64 of the FP32 values)
+        torch.cuda.synchronize()
+        host = llr[:n_or].cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        ref = O.ndgsbp_decode(c, q["grp_ptr"], q["cn_idx"], host, IMAX_ND, want_total=False)
+        t_or = time.perf_counter() - t0
+        del host
+        fe_or = int(ref.hard.any(axis=1).sum())
+        lo, hi = clopper_pearson(fe_or, n_or)
+        oracle_rows.append({"code": name, "frames": n_or, "fer": fe_or / n_or, "fer_ci95": [lo, hi],
+                            "seconds": t_or, "frames_per_s": n_or / t_or, "gbit_s": n_or * (c.N - c.M) / t_or / 1e9,
+                            "cores": host_cores()})
         for msg, dt in (("f32", nd.F32), ("f16", nd.F16), ("bf16", nd.BF16)):
             p = nd.params_default(max_iter=IMAX_ND, msg_dtype=dt)
             ws = torch.zeros(max(256, g.workspace_size(p, F)), dtype=torch.uint8, device=dev)
@@ -998,18 +1021,31 @@ def run_precision(args):
             sec = e0.elapsed_time(e1) / 1e3
             st = stats.cpu().numpy()
             plan = g.plan(p, F)
+            # FER of this storage type on the oracle's frames (the last decode's outputs)
+            bits = nd.unpack_bits(hard[:n_or], c.N)
+            fe_pair = int(bits.any(axis=1).sum())
+            fer_all = float(st[nd.STAT_FRAME_ERRORS] / st[nd.STAT_FRAMES])
+            mufu = MUFU_PER_EDGE_UPDATE * q["edge_updates_per_iter"] * float(st[nd.STAT_ITERATIONS])
+            mufu_total[(name, msg)] = (mufu, sec)
             rows.append({"code": name, "msg_dtype": msg, "ebn0_db": eb, "frames": F,
                          "gbit_s": F * args.steps * (c.N - c.M) / sec / 1e9,
-                         "fer": float(st[nd.STAT_FRAME_ERRORS] / st[nd.STAT_FRAMES]),
+                         "fer": fer_all, "fer_ci95": list(clopper_pearson(int(st[nd.STAT_FRAME_ERRORS] / args.steps), F)),
+                         "fer_on_oracle_frames": fe_pair / n_or,
+                         "inside_oracle_ci": bool(lo <= fe_pair / n_or <= hi and lo <= fer_all <= hi),
                          "ber": float(st[nd.STAT_BIT_ERRORS] / (st[nd.STAT_FRAMES] * c.N)),
                          "mean_iterations": float(st[nd.STAT_ITERATIONS] / st[nd.STAT_FRAMES]),
                          "variant": plan.variant, "ms_per_decode": 1e3 * sec / args.steps,
-                         "mufu_tops": MUFU_PER_EDGE_UPDATE * q["edge_updates_per_iter"] * float(st[nd.STAT_ITERATIONS])
-                                      / sec / 1e12})
+                         "mufu_tops": mufu / sec / 1e12})
             del ws
         del llr
     clk = clocks.stop()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    probe = mufu_peak(nd, torch, dev, sms, clk.get("sm_mhz") or 2070.0)
     f16 = [r for r in rows if r["msg_dtype"] == "f16"]
+    big = mufu_total[("qc_n16200_r23", "f16")]
+    for r in rows:
+        r["mufu_frac"] = r["mufu_tops"] / probe["mix_tops"]
+    t_or = sum(o["seconds"] for o in oracle_rows)
     line = {
         "metric": METRIC, "value": sum(r["gbit_s"] for r in f16) / len(f16), "unit": "Gbit/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
@@ -1017,8 +1053,104 @@ def run_precision(args):
         "config": {"workload": f"precision: n=2304 r1/2 and n=16200 r2/3 QC codes at FER~1e-3, {F} frames, "
                                "cyclic 2-layer NDGSBP, I_max 25, FP32/FP16/BF16 message storage",
                    "l2": "inputs larger than L2"},
-        "rows": rows, "clocks": clk, "gpu_launches": 6 * args.steps, "roofline": None, "e2e": None,
-        "cpu_baseline": None,
+        "rows": rows, "oracle": oracle_rows,
+        "f16_over_f32": {n: next(r["gbit_s"] for r in rows if r["code"] == n and r["msg_dtype"] == "f16") /
+                         next(r["gbit_s"] for r in rows if r["code"] == n and r["msg_dtype"] == "f32")
+                         for n in ("qc_n2304_r12", "qc_n16200_r23")},
+        "all_inside_oracle_ci": all(r["inside_oracle_ci"] for r in rows),
+        "clocks": clk, "gpu_launches": 6 * (args.steps + args.warmup),
+        "roofline": _mufu_roofline(probe, big[0], big[1], "stream_decode_kernel (n=16200, FP16)", args.steps),
+        "e2e": None,
+        "cpu_baseline": {"value": sum(o["frames"] * 1.0 for o in oracle_rows) / t_or, "unit": "frames/s",
+                         "cores": host_cores(), "kind": "oracle",
+                         "sample": "; ".join(f"{o['frames']} frames of {o['code']}" for o in oracle_rows)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_c1(args):
+    """The Gallager (3,6) n=1008 workload: 500 frames at Eb/N0 1.5 dB, FP64 channel LLRs, flooding,
+    disjoint GSBP (4 groups) and NDGSBP (4 groups, r = 0.4) at I_max 50, and NDGSBP at the equal
+    check-update budget I_ND = floor(50 M / U) = 35 (Sec. IV).  GPU and FP64 oracle decode the same
+    LLRs; per schedule: FER and BER with the oracle's 95% interval, mean iterations, and GPU
+    throughput (the 500 frames, and 65,536 frames of the same kind)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from oracle import oracle as O
+    from paper_1202_1060_gb300 import inputs as I
+    from paper_1202_1060_gb300 import ndgsbp as nd
+    O.build()
+    c = I.code_by_name("gallager36_n1008")
+    code = nd.Code.from_inputs(c)
+    F, eb = 500, 1.5
+    host = I.channel_llr(c.N, F, eb, 0.5, seed=1008)
+    big_F = 65536
+    big = torch.empty((big_F, c.N), dtype=torch.float32, device=dev)
+    nd.awgn_llr(code, big_F, eb, 0.5, CHANNEL_SEED + 1008, big)
+    d_llr = torch.from_numpy(host).to(dev)
+    W = (c.N + 31) // 32
+    schedules = [("flooding", 1, 0.0, nd.SCHEDULE_FLOOD, 50), ("gsbp", 4, 0.0, nd.SCHEDULE_GROUPS, 50),
+                 ("ndgsbp", 4, 0.4, nd.SCHEDULE_GROUPS, 50), ("ndgsbp_equal_budget", 4, 0.4, nd.SCHEDULE_GROUPS, None)]
+    rows = []
+    for name, G, r, sched, imax in schedules:
+        g = nd.Groups.build(code, G, r, 7)
+        qq = g.query()
+        if imax is None:
+            imax = int(50 * c.M // qq["cn_updates_per_iter"])
+        p = nd.params_default(max_iter=imax, schedule=sched)
+        out = {}
+        for tag, llr, n in (("c1", d_llr, F), ("large", big, big_F)):
+            ws = torch.zeros(max(256, g.workspace_size(p, n)), dtype=torch.uint8, device=dev)
+            hard = torch.empty((n, W), dtype=torch.int32, device=dev)
+            stats = torch.zeros(nd.STATS_LEN, dtype=torch.int64, device=dev)
+            for _ in range(args.warmup):
+                nd.decode(g, p, llr, ws, hard)
+            stats.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                nd.decode(g, p, llr, ws, hard, stats=stats)
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            st = stats.cpu().numpy() / args.steps
+            out[tag] = {"frames": n, "gbit_s": n * args.steps * (c.N - c.M) / sec / 1e9, "fer": float(st[nd.STAT_FRAME_ERRORS] / n),
+                        "ber": float(st[nd.STAT_BIT_ERRORS] / (n * c.N)), "mean_iterations": float(st[nd.STAT_ITERATIONS] / n),
+                        "variant": g.plan(p, n).variant}
+        # the oracle on the same 500 frames
+        t0 = time.perf_counter()
+        if sched == nd.SCHEDULE_FLOOD:
+            ref = O.flood_decode(c, host, imax, want_total=False)
+        else:
+            ref = O.ndgsbp_decode(c, qq["grp_ptr"], qq["cn_idx"], host, imax, want_total=False)
+        t_or = time.perf_counter() - t0
+        fe, be = int(ref.hard.any(axis=1).sum()), int(ref.hard.sum())
+        lo, hi = clopper_pearson(fe, F)
+        blo, bhi = clopper_pearson(be, F * c.N)
+        gpu = out["c1"]
+        rows.append({"schedule": name, "groups": G, "r": r, "max_iter": imax,
+                     "cn_updates_per_iter": int(c.M if sched == nd.SCHEDULE_FLOOD else qq["cn_updates_per_iter"]),
+                     "gpu": gpu, "gpu_65536_frames": out["large"],
+                     "oracle": {"fer": fe / F, "fer_ci95": [lo, hi], "ber": be / (F * c.N), "ber_ci95": [blo, bhi],
+                                "mean_iterations": float(ref.iters.mean()), "seconds": t_or},
+                     "gpu_inside_oracle_ci": bool(lo <= gpu["fer"] <= hi and blo <= gpu["ber"] <= bhi)})
+    t_or = sum(rw["oracle"]["seconds"] for rw in rows)
+    line = {
+        "metric": METRIC, "value": next(rw["gpu_65536_frames"]["gbit_s"] for rw in rows if rw["schedule"] == "ndgsbp"),
+        "unit": "Gbit/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Gallager (3,6) n=1008 (seeded, 4-cycle-free), Eb/N0 1.5 dB, 500 frames, FP64 channel "
+                               "LLRs; flooding, GSBP (4 groups), NDGSBP (4 groups, r = 0.4) at I_max 50 and NDGSBP "
+                               "at the equal check-update budget; value = NDGSBP on 65,536 such frames"},
+        "rows": rows, "all_inside_oracle_ci": all(rw["gpu_inside_oracle_ci"] for rw in rows),
+        "roofline": None, "e2e": None,
+        "cpu_baseline": {"value": 4 * F * (c.N - c.M) / t_or / 1e9, "unit": "Gbit/s", "cores": host_cores(),
+                         "kind": "oracle", "sample": f"the same {F} frames under the 4 schedules, {t_or:.2f} s"},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -1039,12 +1171,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the flooding and precision extras")
     ap.add_argument("--extras-frames", type=int, default=65536, help="frames per code and dtype, precision extra")
-    ap.add_argument("--workload", choices=["sweep", "ragged", "serving", "precision"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "ragged", "serving", "precision", "c1"], default="sweep",
                     help="sweep = the default n=2304 Eb/N0 sweep line; the others are supplementary")
     ap.add_argument("--precision-frames", type=int, default=262144)
+    ap.add_argument("--precision-oracle-frames", type=int, default=65536,
+                    help="oracle frames for n=2304 (a quarter of that for n=16200)")
     ap.add_argument("--serve-budget-mb", type=int, default=2048)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
-    ap.add_argument("--serve-backlog", type=int, default=400)
+    ap.add_argument("--serve-backlog", type=int, default=6500,
+                    help="requests of the saturated capacity window (about 3 s of work)")
     ap.add_argument("--epoch-iters", type=int, default=8)
     ap.add_argument("--arrival-seed", type=int, default=20260)
     args = ap.parse_args()
@@ -1054,7 +1189,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "sweep":
-        return {"ragged": run_ragged, "serving": run_serving, "precision": run_precision}[args.workload](args)
+        return {"ragged": run_ragged, "serving": run_serving, "precision": run_precision,
+                "c1": run_c1}[args.workload](args)
     return run_ours(args)
 
 
