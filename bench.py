@@ -1069,6 +1069,50 @@ def run_precision(args):
     return 0
 
 
+def run_decode(args):
+    """One code alone (the profiling command of the committed kernel summaries): --code at --ebn0,
+    --frames frames of GPU-generated LLRs, cyclic 2-layer NDGSBP, I_max 25, --msg storage,
+    --variant; --warmup untimed then --steps timed decodes (CUDA events)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1202_1060_gb300 import inputs as I
+    from paper_1202_1060_gb300 import ndgsbp as nd
+    c, code, g = _setup_code(nd, I, args.code)
+    F = args.frames
+    eb = args.ebn0 if args.ebn0 is not None else FER1E3_EBN0.get(args.code, 2.0)
+    st_ = torch.cuda.Stream(device=dev)
+    llr = torch.empty((F, c.N), dtype=torch.float32, device=dev)
+    nd.awgn_llr(code, F, eb, I.design_rate(c), CHANNEL_SEED + c.N, llr, stream=st_)
+    W = (c.N + 31) // 32
+    hard = torch.empty((F, W), dtype=torch.int32, device=dev)
+    stats = torch.zeros(nd.STATS_LEN, dtype=torch.int64, device=dev)
+    dt = {"f32": nd.F32, "f16": nd.F16, "bf16": nd.BF16}[args.msg]
+    p = nd.params_default(max_iter=IMAX_ND, msg_dtype=dt, variant=args.variant)
+    ws = torch.zeros(max(256, g.workspace_size(p, F)), dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        nd.decode(g, p, llr, ws, hard, stream=st_)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st_)
+    for _ in range(args.steps):
+        nd.decode(g, p, llr, ws, hard, stats=stats, stream=st_)
+    e1.record(st_)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    s = stats.cpu().numpy()
+    line = {"metric": METRIC, "value": F * args.steps * (c.N - c.M) / sec / 1e9, "unit": "Gbit/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.msg, "data": "synthetic",
+            "config": {"workload": f"decode: {args.code} at {eb} dB, {F} frames, cyclic 2-layer NDGSBP, I_max {IMAX_ND}"},
+            "fer": float(s[nd.STAT_FRAME_ERRORS] / max(s[nd.STAT_FRAMES], 1)),
+            "mean_iterations": float(s[nd.STAT_ITERATIONS] / max(s[nd.STAT_FRAMES], 1)),
+            "plan": g.plan(p, F).as_dict(), "roofline": None, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_c1(args):
     """The Gallager (3,6) n=1008 workload: 500 frames at Eb/N0 1.5 dB, FP64 channel LLRs, flooding,
     disjoint GSBP (4 groups) and NDGSBP (4 groups, r = 0.4) at I_max 50, and NDGSBP at the equal
@@ -1171,9 +1215,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the flooding and precision extras")
     ap.add_argument("--extras-frames", type=int, default=65536, help="frames per code and dtype, precision extra")
-    ap.add_argument("--workload", choices=["sweep", "ragged", "serving", "precision", "c1"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "ragged", "serving", "precision", "c1", "decode"],
+                    default="sweep",
                     help="sweep = the default n=2304 Eb/N0 sweep line; the others are supplementary")
     ap.add_argument("--precision-frames", type=int, default=262144)
+    ap.add_argument("--code", default="qc_n16200_r23", help="decode workload: the code")
+    ap.add_argument("--ebn0", type=float, default=None, help="decode workload: Eb/N0 (default: the FER~1e-3 point)")
+    ap.add_argument("--msg", choices=["f32", "f16", "bf16"], default="f16", help="decode workload: message storage")
     ap.add_argument("--precision-oracle-frames", type=int, default=65536,
                     help="oracle frames for n=2304 (a quarter of that for n=16200)")
     ap.add_argument("--serve-budget-mb", type=int, default=2048)
@@ -1190,7 +1238,7 @@ def main():
         return run_reference(args)
     if args.workload != "sweep":
         return {"ragged": run_ragged, "serving": run_serving, "precision": run_precision,
-                "c1": run_c1}[args.workload](args)
+                "c1": run_c1, "decode": run_decode}[args.workload](args)
     return run_ours(args)
 
 

@@ -206,6 +206,7 @@ typedef struct {
     double *total;
     double *c2v_out;
     int max_deg_row, max_deg_col;
+    int *edge_row;  /* [E] CN of each edge (vertical schedule only; NULL otherwise) */
     long next_frame;
     pthread_mutex_t lock;
     void (*frame_fn)(const void *ctx, long f, struct Work *w);
@@ -556,6 +557,7 @@ static int setup(Ctx *c, int M, int N, const int *row_ptr, const int *col_idx, c
 static void teardown(Ctx *c) {
     free(c->col_ptr);
     free(c->col_edge);
+    free(c->edge_row);
 }
 
 /* NDGSBP decoder.  grp_ptr has n_groupings * (G + 1) entries (grouping k's pointers at
@@ -628,6 +630,90 @@ int oracle_layered_decode(int M, int N, const int *row_ptr, const int *col_idx, 
                    iters, synd_ok, total, c2v_out);
     if (rc) { teardown(&c); return rc; }
     c.frame_fn = layered_frame;
+    rc = run_frames(&c, n_threads);
+    teardown(&c);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Vertical group shuffled BP, the VN-partitioned serial schedule of Sec. I: the VNs are split
+ * into G groups that are processed one after another within an iteration.  In sub-iteration g
+ * every VN n of group g receives from each of its CNs m the message of Eq. (1), computed from the
+ * VN->CN messages of m's other VNs as they stand at the start of the sub-iteration (VNs of
+ * earlier groups already updated in this iteration, the others not yet); only then do the VNs
+ * of the group send their new messages, L_{n->m} = L_n + sum over the other CNs m' of n of
+ * L_{m'->n} (Eq. (2)).  With one group this is flooding.  After the last group: Eq. (3), the
+ * decision and the syndrome of Step 4.
+ * ---------------------------------------------------------------------------------------- */
+static void vertical_frame(const void *vctx, long f, Work *w) {
+    const Ctx *c = (const Ctx *)vctx;
+    const int E = c->E, N = c->N;
+    const double *L = c->llr + (size_t)f * N;
+    double *v2c = w->a, *c2v = w->b, *tot = w->tot, *th = w->th;
+    uint8_t *d = w->d;
+    for (int e = 0; e < E; ++e) { v2c[e] = L[c->col_idx[e]]; c2v[e] = 0.0; }
+    int l, ok = 0;
+    for (l = 1;; ++l) {
+        for (int g = 0; g < c->G; ++g) {
+            /* CN->VN messages into the group's VNs (Eq. (1)), from the current VN->CN messages */
+            for (int i = c->grp_ptr[g]; i < c->grp_ptr[g + 1]; ++i) {
+                const int n = c->grp_cn[i];
+                for (int a = c->col_ptr[n]; a < c->col_ptr[n + 1]; ++a) {
+                    const int e = c->col_edge[a], m = c->edge_row[e];
+                    const int b = c->row_ptr[m], dd = c->row_ptr[m + 1] - b;
+                    double prod = 1.0;
+                    for (int j = 0; j < dd; ++j) {
+                        th[j] = tanh(0.5 * clip(v2c[b + j], c->llr_max));
+                        if (b + j != e) prod *= th[j];
+                    }
+                    const double lim = 1.0 - 1e-15;
+                    if (prod > lim) prod = lim;
+                    if (prod < -lim) prod = -lim;
+                    c2v[e] = clip(2.0 * atanh(prod), c->llr_max);
+                }
+            }
+            /* then the group's VN->CN messages (Eq. (2), a direct sum over the other CNs) */
+            for (int i = c->grp_ptr[g]; i < c->grp_ptr[g + 1]; ++i) {
+                const int n = c->grp_cn[i];
+                for (int a = c->col_ptr[n]; a < c->col_ptr[n + 1]; ++a) {
+                    double s = L[n];
+                    for (int a2 = c->col_ptr[n]; a2 < c->col_ptr[n + 1]; ++a2)
+                        if (a2 != a) s += c2v[c->col_edge[a2]];
+                    v2c[c->col_edge[a]] = s;
+                }
+            }
+        }
+        ok = total_and_syndrome(c, L, c2v, tot, d);
+        if ((ok && c->early_stop) || l >= c->max_iter) break;
+    }
+    write_outputs(c, f, l, ok, tot, d, c2v);
+}
+
+/* Vertical group shuffled decoder: grp_ptr[G + 1] into grp_vn, a partition of the N VNs (each
+ * exactly once).  Outputs as oracle_ndgsbp_decode. */
+int oracle_vertical_decode(int M, int N, const int *row_ptr, const int *col_idx, int G, const int *grp_ptr,
+                           const int *grp_vn, const double *llr, long n_frames, int max_iter, double llr_max,
+                           int early_stop, uint8_t *hard, int *iters, uint8_t *synd_ok, double *total,
+                           double *c2v_out, int n_threads) {
+    Ctx c;
+    int rc = setup(&c, M, N, row_ptr, col_idx, llr, n_frames, max_iter, llr_max, early_stop, hard,
+                   iters, synd_ok, total, c2v_out);
+    if (rc) { teardown(&c); return rc; }
+    if (G < 1 || grp_ptr[0] != 0 || grp_ptr[G] != N) { teardown(&c); return ORACLE_EINVAL; }
+    uint8_t *seen = (uint8_t *)calloc((size_t)N, 1);
+    c.edge_row = (int *)malloc(sizeof(int) * (size_t)(c.E > 0 ? c.E : 1));
+    if (!seen || !c.edge_row) { free(seen); teardown(&c); return ORACLE_ENOMEM; }
+    for (int i = 0; i < N; ++i) {
+        if (grp_vn[i] < 0 || grp_vn[i] >= N || seen[grp_vn[i]]) { free(seen); teardown(&c); return ORACLE_EINVAL; }
+        seen[grp_vn[i]] = 1;
+    }
+    free(seen);
+    for (int g = 0; g < G; ++g)
+        if (grp_ptr[g + 1] < grp_ptr[g]) { teardown(&c); return ORACLE_EINVAL; }
+    for (int m = 0; m < M; ++m)
+        for (int e = row_ptr[m]; e < row_ptr[m + 1]; ++e) c.edge_row[e] = m;
+    c.G = G; c.grp_ptr = grp_ptr; c.grp_cn = grp_vn;
+    c.frame_fn = vertical_frame;
     rc = run_frames(&c, n_threads);
     teardown(&c);
     return rc;

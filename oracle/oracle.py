@@ -60,6 +60,7 @@ def _load():
                                                           P, P, P, P, P, I]
             lib.oracle_flood_decode.argtypes = [I, I, P, P, P, L, I, D, I, P, P, P, P, P, I]
             lib.oracle_layered_decode.argtypes = [I, I, P, P, P, L, I, D, I, P, P, P, P, P, I]
+            lib.oracle_vertical_decode.argtypes = [I, I, P, P, I, P, P, P, L, I, D, I, P, P, P, P, P, I]
             lib.oracle_philox4x32_10.argtypes = [P, P, P]
             lib.oracle_awgn_llr.argtypes = [I, L, D, D, U64, P, P]
             _lib = lib
@@ -80,8 +81,8 @@ class swapped_library:
         lib = ctypes.CDLL(self.path)
         for name in ("oracle_group_sizes", "oracle_groups", "oracle_budget_iters",
                      "oracle_ndgsbp_decode", "oracle_group_posterior_decode",
-                     "oracle_flood_decode", "oracle_layered_decode", "oracle_philox4x32_10",
-                     "oracle_awgn_llr"):
+                     "oracle_flood_decode", "oracle_layered_decode", "oracle_vertical_decode",
+                     "oracle_philox4x32_10", "oracle_awgn_llr"):
             getattr(lib, name).argtypes = getattr(self._saved, name).argtypes
         with _lock:
             _lib = lib
@@ -299,6 +300,24 @@ def layered_decode(code, llr, max_iter: int, llr_max: float = 20.0, early_stop: 
     _check(lib.oracle_layered_decode(code.M, code.N, _ptr(rp), _ptr(ci), _ptr(llr), F, max_iter,
                                      float(llr_max), int(early_stop), _ptr(hard), _ptr(iters),
                                      _ptr(ok), _ptr(tot), _ptr(c2v), _threads(n_threads)), "layered")
+    return Result(hard, iters, ok, tot, c2v)
+
+
+def vertical_decode(code, grp_ptr, grp_vn, llr, max_iter: int, llr_max: float = 20.0, early_stop: bool = True,
+                    want_total: bool = True, want_c2v: bool = False, n_threads=None) -> Result:
+    """Vertical group shuffled BP (VN groups, Sec. I): grp_ptr [G+1] into grp_vn, a partition of
+    the VNs processed in that order every iteration."""
+    lib = _load()
+    llr = np.ascontiguousarray(llr, np.float64)
+    F = llr.shape[0]
+    gp = np.ascontiguousarray(grp_ptr, np.int32)
+    gv = np.ascontiguousarray(grp_vn, np.int32)
+    rp = np.ascontiguousarray(code.row_ptr, np.int32)
+    ci = np.ascontiguousarray(code.col_idx, np.int32)
+    hard, iters, ok, tot, c2v = _alloc(code, F, want_total, want_c2v)
+    _check(lib.oracle_vertical_decode(code.M, code.N, _ptr(rp), _ptr(ci), len(gp) - 1, _ptr(gp), _ptr(gv),
+                                      _ptr(llr), F, max_iter, float(llr_max), int(early_stop), _ptr(hard),
+                                      _ptr(iters), _ptr(ok), _ptr(tot), _ptr(c2v), _threads(n_threads)), "vertical")
     return Result(hard, iters, ok, tot, c2v)
 
 

@@ -223,6 +223,97 @@ def test_tree_posteriors_equal_map(oracle_mod, seed):
 
 
 # ----------------------------------------------------------------------------------------
+# Vertical (VN-group) shuffled BP, the other serial schedule of Sec. I
+# ----------------------------------------------------------------------------------------
+
+def test_vertical_one_group_is_flooding(oracle_mod):
+    """All VNs in one group: every CN message of the iteration comes from the previous
+    iteration's VN messages, i.e. the textbook flooding decoder."""
+    code = I.code_by_name("gallager36_n1008")
+    llr = _llr(code, 16, 1.5, seed=41)
+    a = oracle_mod.vertical_decode(code, [0, code.N], np.arange(code.N), llr, 25, want_c2v=True)
+    b = oracle_mod.flood_decode(code, llr, 25, want_c2v=True)
+    assert (a.iters == b.iters).all() and (a.hard == b.hard).all()
+    assert np.abs(a.total - b.total).max() < 1e-8 and np.abs(a.c2v - b.c2v).max() < 1e-8
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_vertical_tree_posteriors_equal_map(oracle_mod, seed):
+    """On cycle-free graphs every VN-group schedule converges to the bitwise-MAP LLRs."""
+    code = I.tree_code(14, seed=seed)
+    rng = np.random.default_rng(100 + seed)
+    llr = rng.normal(0.8, 1.2, size=(6, code.N))
+    ref = oracle_mod.brute_force_map(code, llr)
+    for G in (1, 2, 5, code.N):
+        gp, gv = oracle_mod.groups(code.N, G, 0.0, seed=seed)
+        r = oracle_mod.vertical_decode(code, gp, gv, llr, 60, llr_max=0.0, early_stop=False)
+        assert np.abs(r.total - ref).max() < 1e-9, G
+
+
+def _vertical_expected_deps(code, groups):
+    """Channel values each CN->VN message of iteration 1 depends on, from the schedule's
+    definition alone: the message into VN n from CN m, formed in n's sub-iteration, reads the
+    other VNs n' of m; n' contributes {n'} if its group comes at or after n's (not yet updated),
+    else {n'} plus everything its other CNs sent it in its own sub-iteration."""
+    gof = {}
+    for g, vs in enumerate(groups):
+        for v in vs:
+            gof[v] = g
+    rows = [list(code.col_idx[code.row_ptr[m]:code.row_ptr[m + 1]]) for m in range(code.M)]
+    cols = [[m for m in range(code.M) if n in rows[m]] for n in range(code.N)]
+    deps = {}
+    for g, vs in enumerate(groups):
+        for n in vs:
+            for m in cols[n]:
+                d = set()
+                for n2 in rows[m]:
+                    if n2 == n:
+                        continue
+                    d.add(n2)
+                    if gof[n2] < g:
+                        for m2 in cols[n2]:
+                            if m2 != m:
+                                d |= deps[(m2, n2)]
+                deps[(m, n)] = d
+    return deps
+
+
+@pytest.mark.parametrize("seed", [3, 8])
+def test_vertical_influence_sets(oracle_mod, seed):
+    """The order of the VN groups, pinned by which channel values reach each CN->VN message in
+    the first iteration: perturbing L_j moves message (m, n) exactly when the schedule's
+    definition says it reads L_j (a VN of an earlier group carries what it received; a VN of the
+    same or a later group only its channel value)."""
+    rng = np.random.default_rng(seed)
+    N, M = 12, 6
+    # a random sparse code: every VN on 1-2 CNs, every CN on >= 2 VNs
+    H = np.zeros((M, N), np.uint8)
+    for n in range(N):
+        for m in rng.choice(M, size=int(rng.integers(1, 3)), replace=False):
+            H[m, n] = 1
+    for m in range(M):
+        while H[m].sum() < 2:
+            H[m, int(rng.integers(0, N))] = 1
+    code = I.code_from_rows([list(np.nonzero(H[m])[0]) for m in range(M)], N, name=f"vsbp_s{seed}")
+    perm = rng.permutation(N)
+    groups = [[int(v) for v in perm[i::3]] for i in range(3)]
+    gp = np.cumsum([0] + [len(g) for g in groups])
+    gv = np.concatenate([np.array(g) for g in groups])
+    llr = rng.normal(1.0, 1.0, size=(1, N))
+    kw = dict(llr_max=0.0, early_stop=False, want_c2v=True)
+    base = oracle_mod.vertical_decode(code, gp, gv, llr, 1, **kw).c2v[0]
+    deps = _vertical_expected_deps(code, groups)
+    for j in range(N):
+        pert = llr.copy()
+        pert[0, j] += 1e-3
+        moved = np.abs(oracle_mod.vertical_decode(code, gp, gv, pert, 1, **kw).c2v[0] - base) > 1e-12
+        for m in range(code.M):
+            for e in range(code.row_ptr[m], code.row_ptr[m + 1]):
+                n = int(code.col_idx[e])
+                assert moved[e] == (j in deps[(m, n)]), (j, m, n)
+
+
+# ----------------------------------------------------------------------------------------
 # Fig. 1 message sets (Sec. II-A)
 # ----------------------------------------------------------------------------------------
 
@@ -384,6 +475,9 @@ MUTANTS = {
     # channel generator: a wrong Weyl increment, and counter words 1 and 3 swapped in a round
     "philox_weyl": ("W1 = 0xBB67AE85u;", "W1 = 0xBB67AE86u;"),
     "philox_word_swap": ("uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;", "uint32_t n0 = (uint32_t)(p1 >> 32) ^ c3 ^ k0;"),
+    # vertical schedule: a VN's own edge included in its outgoing sum (Eq. (2))
+    "vertical_own_edge": ("                        if (a2 != a) s += c2v[c->col_edge[a2]];",
+                          "                        s += c2v[c->col_edge[a2]];"),
 }
 
 
@@ -396,6 +490,8 @@ def _pins_pass(oracle_mod):
         test_step1_structure(oracle_mod, 60, 4, 0.4)
         test_one_group_is_flooding(oracle_mod)
         test_philox_matches_curand_host_generator(oracle_mod)
+        test_vertical_one_group_is_flooding(oracle_mod)
+        test_vertical_influence_sets(oracle_mod, 3)
     except AssertionError:
         return False
     return True
