@@ -1091,13 +1091,24 @@ def run_decode(args):
     stats = torch.zeros(nd.STATS_LEN, dtype=torch.int64, device=dev)
     dt = {"f32": nd.F32, "f16": nd.F16, "bf16": nd.BF16}[args.msg]
     p = nd.params_default(max_iter=IMAX_ND, msg_dtype=dt, variant=args.variant)
-    ws = torch.zeros(max(256, g.workspace_size(p, F)), dtype=torch.uint8, device=dev)
+    if args.vertical > 0:
+        # the vertical (VN-group) schedule with --vertical random VN groups
+        vg = nd.VGroups.build(code, args.vertical, GROUP_SEED)
+        sched = f"vertical shuffled BP, {args.vertical} VN groups"
+        ws = torch.zeros(max(256, vg.workspace_size(p, F)), dtype=torch.uint8, device=dev)
+        run = lambda **kw: nd.decode_vertical(vg, p, llr, ws, hard, stream=st_, **kw)
+        plan = {"schedule": "vertical", "G": args.vertical, "workspace_bytes": vg.workspace_size(p, F)}
+    else:
+        sched = "cyclic 2-layer NDGSBP"
+        ws = torch.zeros(max(256, g.workspace_size(p, F)), dtype=torch.uint8, device=dev)
+        run = lambda **kw: nd.decode(g, p, llr, ws, hard, stream=st_, **kw)
+        plan = g.plan(p, F).as_dict()
     for _ in range(args.warmup):
-        nd.decode(g, p, llr, ws, hard, stream=st_)
+        run()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st_)
     for _ in range(args.steps):
-        nd.decode(g, p, llr, ws, hard, stats=stats, stream=st_)
+        run(stats=stats)
     e1.record(st_)
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) / 1e3
@@ -1105,10 +1116,10 @@ def run_decode(args):
     line = {"metric": METRIC, "value": F * args.steps * (c.N - c.M) / sec / 1e9, "unit": "Gbit/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.msg, "data": "synthetic",
-            "config": {"workload": f"decode: {args.code} at {eb} dB, {F} frames, cyclic 2-layer NDGSBP, I_max {IMAX_ND}"},
+            "config": {"workload": f"decode: {args.code} at {eb} dB, {F} frames, {sched}, I_max {IMAX_ND}"},
             "fer": float(s[nd.STAT_FRAME_ERRORS] / max(s[nd.STAT_FRAMES], 1)),
             "mean_iterations": float(s[nd.STAT_ITERATIONS] / max(s[nd.STAT_FRAMES], 1)),
-            "plan": g.plan(p, F).as_dict(), "roofline": None, "e2e": None, "cpu_baseline": None}
+            "plan": plan, "roofline": None, "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1222,6 +1233,8 @@ def main():
     ap.add_argument("--code", default="qc_n16200_r23", help="decode workload: the code")
     ap.add_argument("--ebn0", type=float, default=None, help="decode workload: Eb/N0 (default: the FER~1e-3 point)")
     ap.add_argument("--msg", choices=["f32", "f16", "bf16"], default="f16", help="decode workload: message storage")
+    ap.add_argument("--vertical", type=int, default=0,
+                    help="decode workload: decode with the vertical schedule over this many VN groups (0 = NDGSBP)")
     ap.add_argument("--precision-oracle-frames", type=int, default=65536,
                     help="oracle frames for n=2304 (a quarter of that for n=16200)")
     ap.add_argument("--serve-budget-mb", type=int, default=2048)

@@ -99,6 +99,7 @@ typedef int32_t ndgsbp_status;
 
 typedef struct ndgsbp_code ndgsbp_code;
 typedef struct ndgsbp_groups ndgsbp_groups;
+typedef struct ndgsbp_vgroups ndgsbp_vgroups;
 
 /* Decoder parameters (Sec. II-C).  Use ndgsbp_params_default and change what you need. */
 typedef struct ndgsbp_params {
@@ -283,6 +284,53 @@ ndgsbp_status ndgsbp_decode_ex(const ndgsbp_groups* groups, const ndgsbp_params*
                                void* d_workspace, size_t workspace_bytes, uint32_t* d_hard_bits,
                                int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
                                const ndgsbp_extras* extras, void* stream);
+
+/* ---- Vertical (VN-group) shuffled BP (Sec. I, the shuffled schedule over VNs it cites) ------
+ * The N VNs are split into G disjoint groups, kept for every iteration.  ndgsbp_vgroups_build
+ * draws them as Step 1 does for CN units with r = 0 (SplitMix64(seed) Fisher-Yates over the VNs,
+ * or index order with NDGSBP_GROUPS_NATURAL, the only flag taken): G_1 takes the first
+ * ceil(N / G) drawn VNs and the other groups share the rest as evenly as possible, larger
+ * shares first.  ndgsbp_vgroups_from_lists takes them explicitly: grp_ptr[G+1] (grp_ptr[0] = 0,
+ * grp_ptr[G] = N, no empty group) into grp_vn[N], which lists every VN exactly once.  Host-only;
+ * *out is freed by ndgsbp_vgroups_destroy and keeps its own reference to the code.
+ * Errors: INVALID (bad lists, unknown flag, G < 1 or G > N), INFEASIBLE (as ndgsbp_group_sizes),
+ * NOMEM. */
+ndgsbp_status ndgsbp_vgroups_build(const ndgsbp_code* code, int32_t G, uint64_t seed, int32_t flags,
+                                   ndgsbp_vgroups** out);
+ndgsbp_status ndgsbp_vgroups_from_lists(const ndgsbp_code* code, const int32_t* grp_ptr, const int32_t* grp_vn,
+                                        int32_t G, ndgsbp_vgroups** out);
+/* Read the groups back (any output may be NULL): G, grp_ptr[G+1], grp_vn[N], and the largest
+ * number of edges of one group's VNs. */
+ndgsbp_status ndgsbp_vgroups_query(const ndgsbp_vgroups* vgroups, int32_t* G, int32_t* grp_ptr, int32_t* grp_vn,
+                                   int32_t* max_group_edges);
+ndgsbp_status ndgsbp_vgroups_destroy(ndgsbp_vgroups* vgroups);
+
+/* Workspace bytes of ndgsbp_decode_vertical for n_frames frames on the current device (the
+ * CN->VN messages of a frame stay in shared memory when 8 N bytes plus the messages fit in
+ * one CTA's, else they use a workspace slot per CTA; variant SMEM requires the former, GLOBAL
+ * takes the latter, AUTO chooses).  Of params only max_iter, msg_dtype, llr_max, early_stop,
+ * variant (AUTO, SMEM or GLOBAL), block_threads (0 or a multiple of 32 up to 512) and
+ * ctas_per_sm are used.  Errors: INVALID, UNSUPPORTED (8 N bytes above a CTA's shared memory,
+ * or SMEM when the messages do not fit), CUDA. */
+ndgsbp_status ndgsbp_vertical_workspace_size(const ndgsbp_vgroups* vgroups, const ndgsbp_params* params,
+                                             int64_t n_frames, size_t* bytes);
+
+/* Decode with the vertical schedule.  Per frame and iteration l = 1..max_iter, for each VN group
+ * in order: every edge (m, n) with n in the group gets L_{m->n} by Eq. (1) from the VN->CN
+ * messages L_{n'->m} of the CN's other edges as they stand when the group starts (inputs and
+ * output clipped to llr_max); then every edge of the group's VNs gets L_{n->m} = L_n + the sum
+ * of L_{m'->n} over the VN's other CNs (Eq. (2); the kernel holds it as P_n - L_{m->n} with
+ * P_n = L_n + the sum over all of the VN's CNs).  After the last group, Step 4 of Sec. II-C:
+ * d_n = 1 iff P_n < 0, stop when D H^T = 0 (early_stop) or l = max_iter.  Messages start at 0,
+ * VN->CN messages at L_n.  G = 1 is flooding.  Inputs, outputs, extras (statistics, histogram,
+ * timestamps, final CN->VN messages in CSR order), NaN/infinity handling, frame independence
+ * and workspace rules as ndgsbp_decode_ex.  Uploads the groups' tables on first use on a device
+ * (allocates).  Errors: INVALID, WORKSPACE, UNSUPPORTED, CUDA. */
+ndgsbp_status ndgsbp_decode_vertical(const ndgsbp_vgroups* vgroups, const ndgsbp_params* params,
+                                     const void* d_llr, int32_t llr_dtype, int64_t n_frames,
+                                     void* d_workspace, size_t workspace_bytes, uint32_t* d_hard_bits,
+                                     int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
+                                     const ndgsbp_extras* extras, void* stream);
 
 /* ---- Ragged batches: several codes in one persistent launch --------------------------------
  * One code's part of a ragged batch: its grouping (a QC code grouped in whole layers), its

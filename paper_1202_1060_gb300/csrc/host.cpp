@@ -172,6 +172,11 @@ static ndgsbp_status draw_unit_groups(int Mu, int G, double r, uint64_t seed, in
     return NDGSBP_OK;
 }
 
+ndgsbp_status draw_groups(int n_units, int G, double r, uint64_t seed, int flags,
+                          std::vector<std::vector<int>>& groups) {
+    return draw_unit_groups(n_units, G, r, seed, flags & ~NDGSBP_GROUPS_STRUCTURED, groups);
+}
+
 // ------------------------------------------------------------------------------------------
 // Layout compiler
 // ------------------------------------------------------------------------------------------

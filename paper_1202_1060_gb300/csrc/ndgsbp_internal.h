@@ -127,6 +127,12 @@ const Layout& flood_layout(const Groups& g);
 const QcLayout& flood_qc_layout(const Groups& g);
 void release_device_layouts(Groups& g);   // frees device copies (defined in the CUDA file)
 
+// Step 1 over n_units units (the draw of ndgsbp_groups_build, without the structured option):
+// groups[g] lists group g's units.  Used for CN groups and for the VN groups of the vertical
+// schedule.
+ndgsbp_status draw_groups(int n_units, int G, double r, uint64_t seed, int flags,
+                          std::vector<std::vector<int>>& groups);
+
 // The clip limit llr_max (natural LLR units) in the kernels' log2 units (LLR times log2 e).
 inline float kernel_llr_limit(float llr_max) { return llr_max * 1.4426950408889634f; }
 

@@ -108,6 +108,13 @@ _SIGS = {
     "ndgsbp_groups_query_grouping": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "ndgsbp_groups_query": (_I32, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "ndgsbp_groups_destroy": (_I32, [_P]),
+    "ndgsbp_vgroups_build": (_I32, [_P, _I32, _U64, _I32, ctypes.POINTER(_P)]),
+    "ndgsbp_vgroups_from_lists": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_P)]),
+    "ndgsbp_vgroups_query": (_I32, [_P, _P, _P, _P, _P]),
+    "ndgsbp_vgroups_destroy": (_I32, [_P]),
+    "ndgsbp_vertical_workspace_size": (_I32, [_P, ctypes.POINTER(Params), _I64, ctypes.POINTER(ctypes.c_size_t)]),
+    "ndgsbp_decode_vertical": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, ctypes.c_size_t,
+                                      _P, _P, _P, _P, ctypes.POINTER(Extras), _P]),
     "ndgsbp_awgn_llr": (_I32, [_P, _I64, _D, _D, _U64, _P, _I32, _P, _I32, _P]),
     "ndgsbp_philox4x32_10": (_I32, [_P, _U32, _U32, _I64, _P, _P]),
     "ndgsbp_decode_plan": (_I32, [_P, ctypes.POINTER(Params), _I64, ctypes.POINTER(Plan)]),
@@ -329,6 +336,51 @@ class Groups:
             self._h = None
 
 
+class VGroups:
+    """Owned ndgsbp_vgroups handle: VN groups of the vertical shuffled schedule."""
+
+    def __init__(self, handle, code: Code):
+        self._h = handle
+        self.code = code
+
+    @classmethod
+    def build(cls, code: Code, G: int, seed: int, flags: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib.ndgsbp_vgroups_build(code.handle, G, seed & (2**64 - 1), flags, ctypes.byref(h)))
+        return cls(h, code)
+
+    @classmethod
+    def from_lists(cls, code: Code, grp_ptr, grp_vn):
+        gp = np.ascontiguousarray(grp_ptr, np.int32)
+        gv = np.ascontiguousarray(grp_vn, np.int32)
+        h = ctypes.c_void_p()
+        _check(_lib.ndgsbp_vgroups_from_lists(code.handle, _hptr(gp), _hptr(gv), len(gp) - 1, ctypes.byref(h)))
+        return cls(h, code)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def query(self):
+        G, me = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.ndgsbp_vgroups_query(self._h, ctypes.byref(G), None, None, None))
+        gp = np.zeros(G.value + 1, np.int32)
+        gv = np.zeros(self.code.N, np.int32)
+        _check(_lib.ndgsbp_vgroups_query(self._h, None, _hptr(gp), _hptr(gv), ctypes.byref(me)))
+        return dict(G=G.value, grp_ptr=gp, grp_vn=gv, max_group_edges=me.value)
+
+    def workspace_size(self, params: Params, n_frames: int) -> int:
+        b = ctypes.c_size_t()
+        _check(_lib.ndgsbp_vertical_workspace_size(self._h, ctypes.byref(params), n_frames, ctypes.byref(b)))
+        return b.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.ndgsbp_vgroups_destroy(h)
+            self._h = None
+
+
 _DT = {}
 
 
@@ -367,6 +419,19 @@ def decode(groups: Groups, params: Params, llr, workspace, hard_bits, iters=None
                                  _dptr(workspace), workspace.numel() * workspace.element_size(),
                                  _dptr(hard_bits), _dptr(iters), _dptr(syndrome_ok), _dptr(posterior),
                                  ctypes.byref(ex), _stream(stream)))
+
+
+def decode_vertical(vgroups: VGroups, params: Params, llr, workspace, hard_bits, iters=None, syndrome_ok=None,
+                    posterior=None, ref_bits=None, ref_per_frame: bool = False, stats=None, iter_hist=None,
+                    start_ns=None, retire_ns=None, messages=None, stream=None):
+    """ndgsbp_decode_vertical on CUDA tensors; llr is [n_frames, N]."""
+    ex = Extras(d_ref_bits=_addr(ref_bits), ref_per_frame=int(ref_per_frame), d_stats=_addr(stats),
+                d_iter_hist=_addr(iter_hist), d_start_ns=_addr(start_ns), d_retire_ns=_addr(retire_ns),
+                d_messages=_addr(messages))
+    _check(_lib.ndgsbp_decode_vertical(vgroups.handle, ctypes.byref(params), _dptr(llr), dtype_code(llr),
+                                       llr.shape[0], _dptr(workspace), workspace.numel() * workspace.element_size(),
+                                       _dptr(hard_bits), _dptr(iters), _dptr(syndrome_ok), _dptr(posterior),
+                                       ctypes.byref(ex), _stream(stream)))
 
 
 def decode_plain(groups: Groups, params: Params, llr, workspace, hard_bits, iters=None, syndrome_ok=None,

@@ -127,3 +127,39 @@ def test_bit_packing_roundtrip(nd):
     rng = np.random.default_rng(0)
     bits = rng.integers(0, 2, size=(5, 77)).astype(np.uint8)
     assert (nd.unpack_bits(nd.pack_bits(bits), 77) == bits).all()
+
+
+@pytest.mark.parametrize("name,G", [("gallager36_n1008", 1), ("gallager36_n1008", 7), ("qc_n2304_r12", 5),
+                                    ("qc_n576_r12", 576)])
+def test_vgroups_build_matches_oracle(nd, oracle_mod, name, G):
+    """VN groups of the vertical schedule: Step 1's draw over the N VNs with r = 0 (the oracle's
+    own grouping over N units), a partition of the VNs."""
+    c = I.code_by_name(name)
+    code = nd.Code.from_inputs(c)
+    for seed, natural in ((0, False), (99, False), (2**63 + 7, False), (5, True)):
+        v = nd.VGroups.build(code, G, seed, flags=nd.GROUPS_NATURAL if natural else 0)
+        q = v.query()
+        gp, gv = oracle_mod.groups(c.N, G, 0.0, seed, unit=1, natural=natural)
+        assert q["G"] == G and (q["grp_ptr"] == gp).all() and (q["grp_vn"] == gv).all()
+        assert sorted(q["grp_vn"].tolist()) == list(range(c.N))
+        col = c.col_degrees()
+        assert q["max_group_edges"] == max(int(col[gv[gp[g]:gp[g + 1]]].sum()) for g in range(G))
+
+
+def test_vgroups_validation(nd):
+    c = I.fig1_code(5)
+    code = nd.Code.from_inputs(c)
+    N = c.N
+    v = nd.VGroups.from_lists(code, [0, 2, N], list(range(N))[::-1])
+    assert v.query()["G"] == 2
+    for gp, gv in (([0, N], [0] * N),                        # repeated VN
+                   ([0, 0, N], list(range(N))),               # empty group
+                   ([0, N - 1], list(range(N - 1))),          # VN missing
+                   ([0, N], [N] + list(range(1, N)))):        # out of range
+        with pytest.raises(nd.NdgsbpError) as e:
+            nd.VGroups.from_lists(code, gp, gv + [0] * (N - len(gv)))
+        assert e.value.status == nd.ERR_INVALID
+    with pytest.raises(nd.NdgsbpError):
+        nd.VGroups.build(code, N + 1, 0)
+    with pytest.raises(nd.NdgsbpError):
+        nd.VGroups.build(code, 2, 0, flags=nd.GROUPS_CYCLIC)
