@@ -941,9 +941,9 @@ def run_serving(args):
         "config": {"workload": "serving: Poisson arrivals at 0.5/0.75/1.0/1.2x saturated capacity, request sizes "
                                "log-uniform in [1, 4096] frames, codes by the 40/30/20/10 mix of n=576/1152/2304/8192, "
                                "Eb/N0 ~ U[1,3] dB (nearest 0.25 dB pool), FP16 messages, I_max 30, continuous "
-                               "batching with device-resident frame state; per epoch a serving launch of the "
-                               "layered QC kernel per pool whose plain decode uses it (n=576/1152/2304) and one "
-                               "tile-kernel launch for the rest (n=8192), forked",
+                               "batching with device-resident frame state; per epoch one serving launch per pool of the "
+                               "kernel its plain decode uses (the layered QC kernel for n=576/1152/2304, the "
+                               "stream kernel for n=8192), forked",
                    "hbm_budget_mb": args.serve_budget_mb, "epoch_iters": args.epoch_iters,
                    "arrival_seed": args.arrival_seed, "slots": stats["slots_total"],
                    "l2": "pool state larger than L2"},
@@ -1239,9 +1239,9 @@ def main():
                     help="oracle frames for n=2304 (a quarter of that for n=16200)")
     ap.add_argument("--serve-budget-mb", type=int, default=2048)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
-    ap.add_argument("--serve-backlog", type=int, default=6500,
+    ap.add_argument("--serve-backlog", type=int, default=9000,
                     help="requests of the saturated capacity window (about 3 s of work)")
-    ap.add_argument("--epoch-iters", type=int, default=8)
+    ap.add_argument("--epoch-iters", type=int, default=12)
     ap.add_argument("--arrival-seed", type=int, default=20260)
     args = ap.parse_args()
     os.makedirs(OUT_DIR, exist_ok=True)

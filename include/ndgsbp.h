@@ -436,17 +436,19 @@ ndgsbp_status ndgsbp_ragged_autotune(ndgsbp_batch* batches, int32_t n_batches,
  * A server owns, per code, a pool of frame slots (posterior and messages of running frames in
  * device memory; LLR staging and outputs in pinned host memory that the kernel reads and writes
  * directly) sized so that all pools fit hbm_budget_bytes (split in proportion to weights; NULL =
- * equal shares).  A staging thread of the library places the frames of queued
+ * equal shares).  Staging threads of the library place the frames of queued
  * requests into free slots in arrival order (copying their LLRs while epochs run); a worker
  * thread runs epochs in which every running frame advances by at most epoch_iters iterations
  * (its state stays in device memory between epochs), and retires frames whose syndrome is zero
- * (Step 4 b) or that reached params->max_iter, freeing their slots for the next frames at once.
- * A request completes when all its frames have retired.  An epoch is one serving launch of the
- * layered QC kernel per pool whose plain decode would use that kernel (forked onto the pool's
- * own stream) and one serving launch of the tile kernel over the other pools; with
- * params->variant = NDGSBP_VARIANT_TILE every pool runs on the tile kernel.  Every frame is
- * decoded exactly as by ndgsbp_decode with the kernel of its pool (variant QC for a pool on the
- * layered QC kernel, TILE for the others), whatever else is in flight.
+ * (Step 4 b) or that reached params->max_iter; the worker copies an epoch's retired frames out
+ * and frees their slots while the next epoch runs on the GPU.
+ * A request completes when all its frames have retired.  An epoch is one serving launch per
+ * pool whose plain decode (variant AUTO) would use the layered QC kernel or the stream kernel,
+ * of that kernel (forked onto the pool's own stream; a stream pool keeps its messages in shared
+ * or global memory, never bulk-staged), and one serving launch of the tile kernel over the
+ * other pools; with params->variant = NDGSBP_VARIANT_TILE every pool runs on the tile kernel.
+ * Every frame is decoded exactly as by ndgsbp_decode with the kernel of its pool (variant AUTO
+ * for a pool on the QC or stream kernel, TILE for the others), whatever else is in flight.
  * Errors: INVALID, BUDGET (a pool would get no slot), UNSUPPORTED (a code that is not QC in
  * whole layers, or that the tile kernel does not take), CUDA, NOMEM. */
 typedef struct ndgsbp_server ndgsbp_server;
@@ -458,10 +460,10 @@ typedef struct ndgsbp_server_stats {
     int64_t iterations;          /* frame-iterations run */
     double busy_seconds;         /* host time with at least one frame on the device */
     int64_t slots_total, slots_in_use;
-    double admit_seconds;        /* staging-thread time copying admitted frames' LLRs (overlaps epochs) */
-    double device_seconds;       /* host time from an epoch's first enqueue to its stream sync */
-    double harvest_seconds;      /* host time copying retired frames' outputs to their requests */
-    int64_t launches;            /* kernels launched by the epochs (admit, QC and tile launches) */
+    double admit_seconds;        /* staging threads' time copying admitted frames' LLRs, summed (overlaps epochs) */
+    double device_seconds;       /* worker time waiting for epochs to finish (after the overlapped harvest) */
+    double harvest_seconds;      /* worker time copying retired frames' outputs (overlaps the next epoch) */
+    int64_t launches;            /* kernels launched by the epochs (admit, QC, stream and tile launches) */
 } ndgsbp_server_stats;
 
 ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_codes,

@@ -846,6 +846,35 @@ static ndgsbp_status static_scratch_address(void** out) {
 }
 
 // Launch a plan with `ws` as its scratch (its counter already cleared on the stream).
+// The table and shape arguments of a stream-kernel launch (everything but the run arguments,
+// the message slots and the status word).
+static void fill_stream_args(StreamArgs& a, const Plan& plan) {
+    const QcLayout& Q = *plan.Q;
+    const DeviceQc& D = *plan.DQ;
+    a.Z = Q.Z;
+    a.nl = Q.n_layers;
+    a.window = Q.window;
+    a.n_groupings = Q.n_groupings;
+    a.G = static_cast<int>(Q.group_layers.size() / (static_cast<size_t>(Q.window) * Q.n_groupings));
+    a.maxdeg = Q.max_deg;
+    a.tpc = plan.stream_tpc;
+    a.le = (Q.max_deg + plan.stream_tpc - 1) / plan.stream_tpc;
+    a.zr = (Q.Z + 15) / 16 * 16;
+    a.msg_elems = plan.stream_msg_elems;
+    a.slab_elems = plan.stream_slab_elems;
+    for (size_t l = 0; l < plan.stream_lbase.size(); ++l) a.lbase[l] = plan.stream_lbase[l];
+    a.edge_tab = reinterpret_cast<const int2*>(D.edge_tab);
+    a.layer_deg = D.layer_deg;
+    a.group_layers = D.group_layers;
+    a.first_use = D.first_use;
+    a.layer_csr = D.layer_csr;
+    a.ring = D.ring;
+    a.n_slabs = plan.stream_slabs;
+    a.ws_stride = plan.stream_ws_stride;
+    a.wait_limit = 1u << 22;
+    a.test_skip_load = 0;
+}
+
 static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp_params* params, const void* d_llr,
                                  int32_t llr_dtype, int64_t n_frames, unsigned char* ws, uint32_t* d_hard_bits,
                                  int32_t* d_iters, uint8_t* d_syndrome_ok, float* d_posterior,
@@ -855,33 +884,10 @@ static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp
         std::memset(&a, 0, sizeof(a));
         fill_run(a.r, g, params, d_llr, llr_dtype, n_frames, ws, d_hard_bits, d_iters, d_syndrome_ok, d_posterior,
                  extras);
-        const QcLayout& Q = *plan.Q;
-        const DeviceQc& D = *plan.DQ;
-        a.Z = Q.Z;
-        a.nl = Q.n_layers;
-        a.window = Q.window;
-        a.n_groupings = Q.n_groupings;
-        a.G = static_cast<int>(Q.group_layers.size() / (static_cast<size_t>(Q.window) * Q.n_groupings));
-        a.maxdeg = Q.max_deg;
-        a.tpc = plan.stream_tpc;
-        a.le = (Q.max_deg + plan.stream_tpc - 1) / plan.stream_tpc;
-        a.zr = (Q.Z + 15) / 16 * 16;
-        a.msg_elems = plan.stream_msg_elems;
-        a.slab_elems = plan.stream_slab_elems;
-        for (size_t l = 0; l < plan.stream_lbase.size(); ++l) a.lbase[l] = plan.stream_lbase[l];
-        a.edge_tab = reinterpret_cast<const int2*>(D.edge_tab);
-        a.layer_deg = D.layer_deg;
-        a.group_layers = D.group_layers;
-        a.first_use = D.first_use;
-        a.layer_csr = D.layer_csr;
-        a.ring = D.ring;
+        fill_stream_args(a, plan);
         // per-CTA message slots are ws_stride elements apart (256-byte multiples)
         a.ws_msgs = plan.stream_mode == kStreamSmem ? nullptr : ws + kHeaderBytes;
         a.status = reinterpret_cast<unsigned*>(ws + 8);
-        a.n_slabs = plan.stream_slabs;
-        a.ws_stride = plan.stream_ws_stride;
-        a.wait_limit = 1u << 22;
-        a.test_skip_load = 0;
         plan.sfn<<<plan.pub.grid, plan.pub.block_threads, plan.pub.smem_bytes, s>>>(a);
     } else if (plan.tile) {
         TileArgs a;
@@ -990,6 +996,50 @@ ndgsbp_status qc_serve_plan(const Groups& g, const ndgsbp_params* p, QcServePlan
     out->msg_slots = plan.Q->msg_slots;
     std::memset(&out->args, 0, sizeof(out->args));
     fill_qc_args(out->args, *plan.Q, *plan.DQ, nullptr);
+    *ok = true;
+    return NDGSBP_OK;
+}
+
+ndgsbp_status stream_serve_plan(const Groups& g, const ndgsbp_params* p, StreamServePlan* out, bool* ok) {
+    *ok = false;
+    ndgsbp_status st = validate_params(p);
+    if (st) return st;
+    ndgsbp_params q = *p;
+    q.variant = NDGSBP_VARIANT_AUTO;
+    q.block_threads = 0;
+    q.ctas_per_sm = 0;
+    q.frames_per_cta = 0;
+    q.lanes_per_cn = 0;
+    DeviceInfo di;
+    st = device_info(di);
+    if (st) return st;
+    // the plain decode's choice: the QC kernel first (then the pool is a QC pool), else the stream kernel
+    {
+        Plan qp;
+        bool qok = false;
+        st = make_qc_plan(g, &q, int64_t{1} << 30, /*flood=*/false, di, qp, &qok);
+        if (st || qok) return st;
+    }
+    Plan plan;
+    bool sok = false;
+    st = make_stream_plan(g, &q, int64_t{1} << 30, /*flood=*/false, di, plan, &sok);
+    if (st || !sok) return st;
+    if (plan.stream_mode == kStreamBulk) {   // served in global mode: the same arithmetic
+        q.variant = NDGSBP_VARIANT_STREAM_GLOBAL;
+        plan = Plan();
+        st = make_stream_plan(g, &q, int64_t{1} << 30, /*flood=*/false, di, plan, &sok);
+        if (st || !sok) return st;
+    }
+    StreamKernelFn fn = pick_stream_serve_kernel(q.msg_dtype, plan.stream_le, plan.stream_tpc, plan.stream_mode);
+    if (!fn) return NDGSBP_OK;
+    out->fn = fn;
+    out->threads = plan.pub.block_threads;
+    out->per_sm = plan.pub.ctas_per_sm;
+    out->mode = plan.stream_mode;
+    out->smem = static_cast<size_t>(plan.pub.smem_bytes);
+    out->msg_elems_per_slot = plan.stream_ws_stride;
+    std::memset(&out->args, 0, sizeof(out->args));
+    fill_stream_args(out->args, plan);
     *ok = true;
     return NDGSBP_OK;
 }

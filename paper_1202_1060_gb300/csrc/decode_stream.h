@@ -3,6 +3,7 @@
 // n=8192 (Z = 256, degree 22).
 #pragma once
 
+#include "decode_tile.h"
 #include "device_common.cuh"
 #include "ndgsbp_internal.h"
 
@@ -53,6 +54,16 @@ struct StreamArgs {
     unsigned wait_limit;          // polls before a bounded wait gives up
     int test_skip_load;           // test hook: 1 = arm the first load's barrier but issue no copy
     int lbase[kStreamMaxLayers];  // first message element of each layer's block (stream_layer_elems)
+    // serving instances: frame i of the launch (r.n_frames of them) is pool slot serve_list[i],
+    // whose decoding state persists in the pool between launches (as for the QC kernel)
+    const int* serve_list;
+    int* state_flag;              // [pool] kSlotNew / kSlotRunning / kSlotDone ...
+    int* state_iter;              // [pool] iterations done so far
+    float* state_P;               // [pool][N] posteriors of running frames
+    void* state_msgs;             // [pool][ws_stride] messages of running frames (the launch's layout)
+    int epoch_iters;              // iterations a frame may run in one launch before it is parked
+    int* done_list;               // [pool] slots whose frame retired in this launch
+    int* done_count;              // entries in done_list (zeroed before the launch)
 };
 
 typedef void (*StreamKernelFn)(const StreamArgs);
@@ -66,5 +77,21 @@ int stream_lane_width(int le, int tpc);
 int stream_max_threads(int tpc);
 // Dynamic shared memory of a launch (a filled in; msg_size 2 or 4 bytes).
 size_t stream_smem_bytes(const StreamArgs& a, int msg_size, int mode);
+// Serving instance (decode_stream_serve.cu; shared-memory and global modes only).
+StreamKernelFn pick_stream_serve_kernel(int msg_dtype, int le, int tpc, int mode);
+
+// The serving form of a grouping's stream plan (server pools): the kernel, block, shared bytes,
+// message elements per slot (ws_stride) and table arguments that ndgsbp_decode would use for the
+// grouping with variant AUTO when that picks the stream kernel, restricted to the shared-memory
+// and global modes (a bulk-staged plan is served in global mode: the same arithmetic).  *ok =
+// false when the plain decode would not use the stream kernel.
+struct StreamServePlan {
+    StreamKernelFn fn = nullptr;
+    int threads = 0, per_sm = 0, mode = 0;
+    size_t smem = 0;
+    int msg_elems_per_slot = 0;   // ws_stride
+    StreamArgs args{};
+};
+ndgsbp_status stream_serve_plan(const Groups& g, const ndgsbp_params* p, StreamServePlan* out, bool* ok);
 
 }  // namespace ndgsbp

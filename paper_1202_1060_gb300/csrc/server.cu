@@ -5,18 +5,19 @@
 // pinned host memory that the kernel reads when the frame starts, and its outputs go straight
 // to pinned host memory that the kernel writes when the frame retires.  A worker thread repeats
 // one epoch:
-//   1. admit: frames that a staging thread has already placed (queued requests' frames, in
+//   1. admit: frames that the staging threads have already placed (queued requests' frames, in
 //      arrival order, take free slots of their code's pool and have their LLRs copied to the
 //      slots' staging, concurrently with the epochs) are listed for a small admit kernel that
 //      marks their slots new;
-//   2. run: per pool whose code the layered QC kernel decodes (the plain decode's choice), one
-//      serving launch of that kernel over the pool's running slots, on the pool's own stream;
-//      for the other pools, one launch of the tile kernel in serving mode over the tiles of
-//      their occupied slots; all launches of the epoch run concurrently and join before the
+//   2. run: per pool whose code the layered QC kernel or the stream kernel decodes (the plain
+//      decode's choice), one serving launch of that kernel over the pool's running slots, on the
+//      pool's own stream; for the other pools, one launch of the tile kernel in serving mode over
+//      the tiles of their occupied slots; all launches of the epoch run concurrently and join before the
 //      harvest.  Each running frame advances by at most epoch_iters iterations, then retires
 //      (zero syndrome or max_iter: outputs written, slot listed as done) or is parked with its
 //      state in device memory;
-//   3. harvest: the done lists come back (a count per pool); retired frames free their slots
+//   3. harvest (on the host while the next epoch runs on the GPU; epochs alternate between two
+//      done lists): the done lists come back (a count per pool); retired frames free their slots
 //      and their outputs are copied into their requests' buffers; a request completes when all
 //      its frames have retired.
 // Frames of different requests and codes share every launch, and new requests join as soon as
@@ -36,6 +37,7 @@
 #include <vector>
 
 #include "decode_qc.h"
+#include "decode_stream.h"
 #include "decode_tile.h"
 #include "ndgsbp_internal.h"
 
@@ -94,23 +96,33 @@ struct Pool {
     uint32_t* h_hard = nullptr;
     int32_t* h_iters = nullptr;
     uint8_t* h_ok = nullptr;
-    int* h_done = nullptr;
-    std::vector<int> free_slots;   // kept in descending order: the lowest free slot is taken first
+    int* h_done[2] = {nullptr, nullptr};   // two done lists: epochs alternate between them
+    int* d_done[2] = {nullptr, nullptr};   // their device views
+    std::vector<int> free_slots;   // tile pools: kept in descending order (the lowest free slot is taken first)
     std::vector<std::pair<Request*, int64_t>> owner;   // frame held by each slot (staged or running)
     std::vector<uint8_t> running;   // the slot's frame has been launched
     std::vector<int> ready;         // staged slots waiting for the next epoch
     // QC pools: advanced by the serving instance of the layered QC kernel (one launch per epoch
-    // over the listed running slots, on the pool's own stream); the others by the tile launch
+    // over the listed running slots, on the pool's own stream); stream pools likewise by the
+    // serving instance of the stream kernel; the others by the tile launch
     bool qc = false;
     QcServePlan qp;
     QcArgs qargs{};
+    bool stream = false;
+    StreamServePlan sp;
+    StreamArgs sargs{};
     int qc_grid = 1, n_list = 0;
+    bool listed() const { return qc || stream; }   // runs its own launch over a slot list
     int* h_list = nullptr;          // pinned, mapped: this epoch's running slots
     cudaStream_t qstream = nullptr;
     cudaEvent_t qdone = nullptr;    // the pool's launch of this epoch has completed (join)
 };
 
-constexpr int kStageBatch = 512;   // frames the staging thread places per lock hold
+constexpr int kStageBatch = 512;   // frames a staging thread places per lock hold
+// Staging threads: each takes the next batch of queued frames (slots are assigned in arrival
+// order under the lock) and copies their LLRs concurrently with the others; one thread's copy
+// rate (about 10 GB/s) would otherwise bound the saturated serving rate.
+constexpr int kStagers = 3;
 
 template <typename T>
 T* device_view(T* host) {
@@ -149,13 +161,15 @@ struct ndgsbp_server {
     bool stop = false;
     ndgsbp_status failed = NDGSBP_OK;
     std::string failure;
-    std::thread worker, stager;
+    std::thread worker;
+    std::vector<std::thread> stagers;
     ndgsbp_server_stats stats{};
 
     ~ndgsbp_server();
     void run();
     void stage();
-    bool epoch();
+    bool enqueue(int par, bool* launched);
+    void harvest(int par);
     bool can_stage() const {
         for (const Request* r : queue)
             if (!pools[r->code].free_slots.empty()) return true;
@@ -170,7 +184,8 @@ ndgsbp_server::~ndgsbp_server() {
     }
     cv_work.notify_all();
     cv_stage.notify_all();
-    if (stager.joinable()) stager.join();
+    for (std::thread& t : stagers)
+        if (t.joinable()) t.join();
     if (worker.joinable()) worker.join();
     int cur = 0;
     if (cudaGetDevice(&cur) == cudaSuccess && cudaSetDevice(device) == cudaSuccess) {
@@ -187,7 +202,8 @@ ndgsbp_server::~ndgsbp_server() {
             cudaFreeHost(p.h_hard);
             cudaFreeHost(p.h_iters);
             cudaFreeHost(p.h_ok);
-            cudaFreeHost(p.h_done);
+            cudaFreeHost(p.h_done[0]);
+            cudaFreeHost(p.h_done[1]);
         }
         cudaFree(d_tiles);
         cudaFreeHost(h_tiles);
@@ -214,9 +230,11 @@ ndgsbp_server::~ndgsbp_server() {
         }                                                                                     \
     } while (0)
 
-// One epoch; false on a CUDA error (recorded, the worker stops).
-bool ndgsbp_server::epoch() {
-    const auto t0 = Clock::now();
+// Enqueue one epoch on `stream` with done-list buffer `par` (the previous epoch has been
+// synchronised): admission, slot lists and tiles, launches.  *launched = false when no frame is
+// running or staged.  False on a CUDA error (recorded, the worker stops).
+bool ndgsbp_server::enqueue(int par, bool* launched) {
+    *launched = false;
     int n_admit = 0, n_tiles = 0;
     {
         std::lock_guard<std::mutex> lock(mu);
@@ -231,11 +249,13 @@ bool ndgsbp_server::epoch() {
             p.ready.clear();
         }
         n_ready = 0;
-        // QC pools: the list of running slots; tile pools: tiles over the running slots, ranges
-        // holding up to tile_frames running slots (other slots inside a range are skipped)
+        // listed pools: their running slots (slots whose frame retired in the epoch not yet
+        // harvested are still listed: the kernel skips them, their flag says done); tile pools:
+        // tiles over the running slots, ranges holding up to tile_frames running slots (other
+        // slots inside a range are skipped)
         for (int i = 0; i < static_cast<int>(pools.size()); ++i) {
             Pool& p = pools[i];
-            if (p.qc) {
+            if (p.listed()) {
                 p.n_list = 0;
                 for (int slot = 0; slot < p.slots; ++slot)
                     if (p.running[slot]) p.h_list[p.n_list++] = slot;
@@ -255,11 +275,11 @@ bool ndgsbp_server::epoch() {
             if (first >= 0) h_tiles[n_tiles++] = make_int4(i, first, last - first + 1, 0);
         }
     }
-    const auto t1 = Clock::now();
-    int n_qc = 0, n_launches = 0;
-    for (const Pool& p : pools) n_qc += p.qc ? p.n_list : 0;
-    if (n_tiles == 0 && n_qc == 0) return true;
-    // 2. admit, then one serving launch over the occupied tiles
+    int n_listed = 0, n_launches = 0;
+    for (const Pool& p : pools) n_listed += p.listed() ? p.n_list : 0;
+    if (n_tiles == 0 && n_listed == 0) return true;
+    int* d_count = d_done_count + par * kTileMaxCodes;
+    // 2. admit, then the launches
     if (n_admit) {
         SRV_CUDA(cudaMemcpyAsync(d_admit, h_admit, sizeof(int) * n_admit, cudaMemcpyHostToDevice, stream));
         AdmitArgs aa{};
@@ -270,16 +290,27 @@ bool ndgsbp_server::epoch() {
         SRV_CUDA(cudaGetLastError());
         ++n_launches;
     }
-    SRV_CUDA(cudaMemsetAsync(d_done_count, 0, sizeof(int) * pools.size(), stream));
+    SRV_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int) * pools.size(), stream));
     SRV_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long) * (1 + pools.size()), stream));
-    // fork: each QC pool's launch on its own stream, concurrent with the tile launch
+    // fork: each listed pool's launch on its own stream, concurrent with the tile launch
     SRV_CUDA(cudaEventRecord(fork, stream));
-    for (Pool& p : pools) {
-        if (!p.qc || p.n_list == 0) continue;
+    for (size_t i = 0; i < pools.size(); ++i) {
+        Pool& p = pools[i];
+        if (!p.listed() || p.n_list == 0) continue;
         SRV_CUDA(cudaStreamWaitEvent(p.qstream, fork, 0));
-        QcArgs qa = p.qargs;
-        qa.r.n_frames = p.n_list;
-        p.qp.fn<<<std::min(p.qc_grid, p.n_list), p.qp.threads, p.qp.smem, p.qstream>>>(qa);
+        if (p.qc) {
+            QcArgs qa = p.qargs;
+            qa.r.n_frames = p.n_list;
+            qa.done_list = p.d_done[par];
+            qa.done_count = d_count + i;
+            p.qp.fn<<<std::min(p.qc_grid, p.n_list), p.qp.threads, p.qp.smem, p.qstream>>>(qa);
+        } else {
+            StreamArgs sa = p.sargs;
+            sa.r.n_frames = p.n_list;
+            sa.done_list = p.d_done[par];
+            sa.done_count = d_count + i;
+            p.sp.fn<<<std::min(p.qc_grid, p.n_list), p.sp.threads, p.sp.smem, p.qstream>>>(sa);
+        }
         SRV_CUDA(cudaGetLastError());
         ++n_launches;
         SRV_CUDA(cudaEventRecord(p.qdone, p.qstream));
@@ -288,24 +319,38 @@ bool ndgsbp_server::epoch() {
         SRV_CUDA(cudaMemcpyAsync(d_tiles, h_tiles, sizeof(int4) * n_tiles, cudaMemcpyHostToDevice, stream));
         TileArgs a = args;
         a.n_tiles = n_tiles;
+        for (size_t i = 0; i < pools.size(); ++i) {
+            a.codes[i].done_list = pools[i].d_done[par];
+            a.codes[i].done_count = d_count + i;
+        }
         fn<<<std::min(max_grid, n_tiles), threads, smem, stream>>>(a);
         SRV_CUDA(cudaGetLastError());
         ++n_launches;
     }
     for (Pool& p : pools)
-        if (p.qc && p.n_list > 0) SRV_CUDA(cudaStreamWaitEvent(stream, p.qdone, 0));
-    SRV_CUDA(cudaMemcpyAsync(h_done_count, d_done_count, sizeof(int) * pools.size(), cudaMemcpyDeviceToHost, stream));
-    SRV_CUDA(cudaStreamSynchronize(stream));
-    const auto t2 = Clock::now();
-    // 3. harvest the retired frames
+        if (p.listed() && p.n_list > 0) SRV_CUDA(cudaStreamWaitEvent(stream, p.qdone, 0));
+    SRV_CUDA(cudaMemcpyAsync(h_done_count + par * kTileMaxCodes, d_count, sizeof(int) * pools.size(),
+                             cudaMemcpyDeviceToHost, stream));
+    *launched = true;
+    std::lock_guard<std::mutex> lock(mu);
+    stats.epochs += 1;
+    stats.launches += n_launches;
+    return true;
+}
+
+// 3. Harvest the frames that retired in the (synchronised) epoch with done-list buffer par:
+// free their slots, copy their outputs into their requests, complete finished requests.
+void ndgsbp_server::harvest(int par) {
+    const auto t0 = Clock::now();
     std::vector<Request*> finished;
     {
         std::lock_guard<std::mutex> lock(mu);
         for (size_t i = 0; i < pools.size(); ++i) {
             Pool& p = pools[i];
-            const int n_done = h_done_count[i];
+            const int n_done = h_done_count[par * kTileMaxCodes + i];
+            const int* done = p.h_done[par];
             for (int k = 0; k < n_done; ++k) {
-                const int slot = p.h_done[k];
+                const int slot = done[k];
                 Request* r = p.owner[slot].first;
                 if (!r) continue;
                 const int64_t f = p.owner[slot].second;
@@ -323,41 +368,61 @@ bool ndgsbp_server::epoch() {
                 --n_running;
                 if (++r->retired == r->n_frames) finished.push_back(r);
             }
-            if (n_done) std::sort(p.free_slots.begin(), p.free_slots.end(), std::greater<int>());
+            // tile pools take the lowest free slots first (their tiles cover ranges of running
+            // slots, so compact occupancy means fewer tiles); listed pools take any free slot
+            if (n_done && !p.listed()) std::sort(p.free_slots.begin(), p.free_slots.end(), std::greater<int>());
         }
-        const auto t3 = Clock::now();
+        const auto t1 = Clock::now();
         for (Request* r : finished) {
             r->done = true;
-            r->t_done = t3;
+            r->t_done = t1;
             stats.requests_completed += 1;
         }
-        stats.epochs += 1;
-        stats.launches += n_launches;
-        stats.device_seconds += std::chrono::duration<double>(t2 - t1).count();
-        stats.harvest_seconds += std::chrono::duration<double>(t3 - t2).count();
-        stats.busy_seconds += std::chrono::duration<double>(t3 - t0).count();
+        stats.harvest_seconds += std::chrono::duration<double>(t1 - t0).count();
     }
     if (!finished.empty()) cv_done.notify_all();
-    cv_stage.notify_one();
-    return true;
+    cv_stage.notify_all();
 }
 
+// The worker: enqueue epoch k, harvest epoch k - 1 on the host while epoch k runs, synchronise,
+// repeat.  A frame that retires in epoch k frees its slot when epoch k is harvested (during
+// epoch k + 1), so the next frame can take it from epoch k + 2 on.
 void ndgsbp_server::run() {
     cudaSetDevice(device);
+    int par = 0;
+    bool have_prev = false;   // an epoch has been synchronised and not yet harvested
     for (;;) {
         {
             std::unique_lock<std::mutex> lock(mu);
-            cv_work.wait(lock, [&] { return stop || n_ready > 0 || n_running > 0; });
+            cv_work.wait(lock, [&] { return stop || have_prev || n_ready > 0 || n_running > 0; });
             if (stop) return;
         }
-        if (!epoch()) {
-            cv_done.notify_all();
-            return;
+        const auto t0 = Clock::now();
+        bool launched = false;
+        if (!enqueue(par, &launched)) break;
+        if (have_prev) harvest(par ^ 1);
+        have_prev = false;
+        const auto t1 = Clock::now();
+        if (launched) {
+            const cudaError_t e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) {
+                std::lock_guard<std::mutex> lock(mu);
+                failed = NDGSBP_ERR_CUDA;
+                failure = std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e);
+                break;
+            }
+            have_prev = true;
+            par ^= 1;
         }
+        const auto t2 = Clock::now();
+        std::lock_guard<std::mutex> lock(mu);
+        stats.device_seconds += std::chrono::duration<double>(t2 - t1).count();
+        stats.busy_seconds += std::chrono::duration<double>(t2 - t0).count();
     }
+    cv_done.notify_all();
 }
 
-// Staging thread: places queued frames, in arrival order, into free slots and copies their LLRs
+// Staging threads: place queued frames, in arrival order, into free slots and copy their LLRs
 // to the slots' staging while epochs run; the next epoch admits them.
 void ndgsbp_server::stage() {
     struct Job {
@@ -451,6 +516,11 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
             st = qc_serve_plan(*p.g, params, &p.qp, &ok);
             if (st) return st;
             p.qc = ok;
+            if (!ok) {   // the stream kernel where the plain decode uses it
+                st = stream_serve_plan(*p.g, params, &p.sp, &ok);
+                if (st) return st;
+                p.stream = ok;
+            }
         }
         p.tpc = tile_lanes_per_cn(p.Q->max_deg);
         if (!p.tpc) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: code %d has row degree above 32", i);
@@ -466,6 +536,10 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         p.d_bytes = a16(static_cast<size_t>(shp.delta_floats) * 4);
         if (p.qc) {
             p.msg_slots = p.qp.msg_slots;
+            continue;
+        }
+        if (p.stream) {
+            p.msg_slots = p.sp.msg_elems_per_slot;
             continue;
         }
         ++n_tile_pools;
@@ -484,7 +558,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     };
     auto fits = [&](size_t cap) {
         for (const Pool& p : h->pools)
-            if (!p.qc && table_max + p.p_bytes + p.d_bytes > cap) return false;
+            if (!p.listed() && table_max + p.p_bytes + p.d_bytes > cap) return false;
         return true;
     };
     const int target = params->ctas_per_sm > 0 ? params->ctas_per_sm : (fits(cap_for(2)) ? 2 : 1);
@@ -492,7 +566,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     size_t smem = table_max;
     for (int i = 0; i < n_codes; ++i) {
         Pool& p = h->pools[i];
-        if (!p.qc) {
+        if (!p.listed()) {
             if (table_max + p.p_bytes + p.m_bytes + p.d_bytes > budget) p.m_bytes = 0;
             p.slot_bytes = p.p_bytes + p.m_bytes + p.d_bytes;
             if (table_max + p.slot_bytes > budget)
@@ -516,7 +590,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     bool regb = true;
     for (int i = 0; i < n_codes; ++i) {
         const Pool& p = h->pools[i];
-        if (p.qc) continue;
+        if (p.listed()) continue;
         lane_width = std::max(lane_width, tile_lane_width(p.le));
         regb = regb && p.cta_slots * p.Q->window * p.Q->Z * p.tpc <= threads;
     }
@@ -545,8 +619,9 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         hmalloc(reinterpret_cast<void**>(&p.h_hard), sizeof(uint32_t) * p.W * static_cast<size_t>(p.slots));
         hmalloc(reinterpret_cast<void**>(&p.h_iters), sizeof(int32_t) * p.slots);
         hmalloc(reinterpret_cast<void**>(&p.h_ok), p.slots);
-        hmalloc(reinterpret_cast<void**>(&p.h_done), sizeof(int) * p.slots);
-        if (p.qc) {
+        hmalloc(reinterpret_cast<void**>(&p.h_done[0]), sizeof(int) * p.slots);
+        hmalloc(reinterpret_cast<void**>(&p.h_done[1]), sizeof(int) * p.slots);
+        if (p.listed()) {
             hmalloc(reinterpret_cast<void**>(&p.h_list), sizeof(int) * p.slots);
             if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p.qstream, cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.qdone, cudaEventDisableTiming);
@@ -555,15 +630,15 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         p.owner.assign(p.slots, {nullptr, 0});
         p.running.assign(p.slots, 0);
         for (int s = p.slots - 1; s >= 0; --s) p.free_slots.push_back(s);
-        if (!p.qc) max_tiles += (p.slots + p.tile_frames - 1) / p.tile_frames;
+        if (!p.listed()) max_tiles += (p.slots + p.tile_frames - 1) / p.tile_frames;
         h->stats.slots_total += p.slots;
     }
     dmalloc(reinterpret_cast<void**>(&h->d_tiles), sizeof(int4) * max_tiles);
     hmalloc(reinterpret_cast<void**>(&h->h_tiles), sizeof(int4) * max_tiles);
     dmalloc(reinterpret_cast<void**>(&h->d_admit), sizeof(int) * h->stats.slots_total);
     hmalloc(reinterpret_cast<void**>(&h->h_admit), sizeof(int) * h->stats.slots_total);
-    dmalloc(reinterpret_cast<void**>(&h->d_done_count), sizeof(int) * kTileMaxCodes);
-    hmalloc(reinterpret_cast<void**>(&h->h_done_count), sizeof(int) * kTileMaxCodes);
+    dmalloc(reinterpret_cast<void**>(&h->d_done_count), sizeof(int) * 2 * kTileMaxCodes);
+    hmalloc(reinterpret_cast<void**>(&h->h_done_count), sizeof(int) * 2 * kTileMaxCodes);
     dmalloc(reinterpret_cast<void**>(&h->d_counter), 256);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
@@ -579,16 +654,17 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         per_sm = std::min(per_sm, target);
     }
     for (Pool& p : h->pools) {
-        if (!p.qc) continue;
+        if (!p.listed()) continue;
+        const void* lfn = p.qc ? reinterpret_cast<const void*>(p.qp.fn) : reinterpret_cast<const void*>(p.sp.fn);
+        const int lthreads = p.qc ? p.qp.threads : p.sp.threads;
+        const size_t lsmem = p.qc ? p.qp.smem : p.sp.smem;
         int q_sm = 0;
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(reinterpret_cast<const void*>(p.qp.fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(p.qp.smem));
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_sm, reinterpret_cast<const void*>(p.qp.fn),
-                                                              p.qp.threads, p.qp.smem);
+            e = cudaFuncSetAttribute(lfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(lsmem));
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q_sm, lfn, lthreads, lsmem);
         if (e != cudaSuccess) return fail(NDGSBP_ERR_CUDA, "server_create: %s", cudaGetErrorString(e));
-        if (q_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: a QC launch does not fit on an SM");
+        if (q_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "server_create: a pool's launch does not fit on an SM");
+        if (p.stream) q_sm = std::min(q_sm, std::max(1, p.sp.per_sm));
         p.qc_grid = q_sm * sms;
     }
     for (int i = 0; i < n_codes; ++i) {
@@ -621,7 +697,9 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         C.state_P = p.st_P;
         C.state_msgs = p.st_msgs;
         C.epoch_iters = epoch_iters;
-        C.done_list = device_view(p.h_done);
+        p.d_done[0] = device_view(p.h_done[0]);
+        p.d_done[1] = device_view(p.h_done[1]);
+        C.done_list = p.d_done[0];
         C.done_count = h->d_done_count + i;
         RunArgs& r = C.r;
         r.N = p.N;
@@ -636,7 +714,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
         r.hard_bits = device_view(p.h_hard);
         r.iters = device_view(p.h_iters);
         r.synd_ok = device_view(p.h_ok);
-        if (!C.done_list || !r.llr || !r.hard_bits || !r.iters || !r.synd_ok)
+        if (!p.d_done[0] || !p.d_done[1] || !r.llr || !r.hard_bits || !r.iters || !r.synd_ok)
             return fail(NDGSBP_ERR_CUDA, "server_create: cannot map host buffers into the device");
         if (p.qc) {
             QcArgs& q = p.qargs;
@@ -653,6 +731,23 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
             q.done_count = C.done_count;
             if (!q.serve_list) return fail(NDGSBP_ERR_CUDA, "server_create: cannot map host buffers into the device");
         }
+        if (p.stream) {
+            StreamArgs& a = p.sargs;
+            a = p.sp.args;
+            a.r = r;
+            a.r.counter = h->d_counter + 1 + i;
+            a.ws_msgs = nullptr;
+            a.status = nullptr;
+            a.serve_list = device_view(p.h_list);
+            a.state_flag = p.flag;
+            a.state_iter = p.st_iter;
+            a.state_P = p.st_P;
+            a.state_msgs = p.st_msgs;
+            a.epoch_iters = epoch_iters;
+            a.done_list = C.done_list;
+            a.done_count = C.done_count;
+            if (!a.serve_list) return fail(NDGSBP_ERR_CUDA, "server_create: cannot map host buffers into the device");
+        }
     }
     h->args.n_codes = n_codes;
     h->args.tiles = h->d_tiles;
@@ -665,7 +760,7 @@ ndgsbp_status ndgsbp_server_create(const ndgsbp_groups* const* codes, int32_t n_
     h->max_grid = std::max(1, per_sm * sms);
     ndgsbp_server* raw = h.release();
     raw->worker = std::thread([raw] { raw->run(); });
-    raw->stager = std::thread([raw] { raw->stage(); });
+    for (int k = 0; k < kStagers; ++k) raw->stagers.emplace_back([raw] { raw->stage(); });
     *out = raw;
     return NDGSBP_OK;
 }

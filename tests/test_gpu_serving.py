@@ -1,8 +1,9 @@
 """Serving (continuous batching) through the C ABI server (needs a GB300).
 
 Every frame a server decodes must come out exactly as when its batch is decoded alone by the
-kernel its pool runs on: the layered QC kernel for codes whose plain decode uses it (the
-default), the TILE kernel for the others or when the server is created with variant TILE.  Same
+kernel its pool runs on: the layered QC kernel or the stream kernel for codes whose plain decode
+uses it (the default), the TILE kernel for the others or when the server is created with variant
+TILE.  Same
 hard decisions, iteration counts and syndrome flags, bit for bit, whatever else is in flight,
 however many slots the budget gives, and however the decoding is cut into epochs (its state
 stays in device memory between launches).
@@ -36,12 +37,15 @@ def _grouped(nd, name):
 
 def _alone(nd, torch, g, c, llr, params):
     """The batch decoded alone by the kernel a server with these params uses for the code: the
-    layered QC kernel where the plain decode (variant AUTO) uses it, else the tile kernel (and
-    the tile kernel for every code when the server is created with variant TILE)."""
+    layered QC kernel or the stream kernel where the plain decode (variant AUTO) uses it, else
+    the tile kernel (and the tile kernel for every code when the server is created with variant
+    TILE)."""
     dev = torch.device("cuda")
     p = nd.params_default(**{f: getattr(params, f) for f, _ in params._fields_})
     p.variant = nd.VARIANT_AUTO
-    if params.variant == nd.VARIANT_TILE or g.plan(p, 1024).variant not in (nd.VARIANT_QC, nd.VARIANT_QC_GLOBAL):
+    listed = (nd.VARIANT_QC, nd.VARIANT_QC_GLOBAL, nd.VARIANT_STREAM_SMEM, nd.VARIANT_STREAM_GLOBAL,
+              nd.VARIANT_STREAM_BULK)
+    if params.variant == nd.VARIANT_TILE or g.plan(p, 1024).variant not in listed:
         p.variant = nd.VARIANT_TILE
     F = llr.shape[0]
     d_llr = torch.from_numpy(np.ascontiguousarray(llr, np.float32)).to(dev)
@@ -101,19 +105,55 @@ def test_served_equals_alone(env, msg, epoch_iters, budget_mb, kernel):
 
 
 @pytest.mark.parametrize("msg", ["f32", "f16"])
-def test_served_mixed_kernels(env, msg):
-    """A server whose pools run on different kernels (n=576 on the QC kernel, n=8192 on the tile
-    kernel: its 2-layer window does not fit one CTA of the QC kernel), with their launches
-    forked within each epoch: every frame equals its batch decoded alone."""
+@pytest.mark.parametrize("kernel", ["auto", "tile"])
+def test_served_mixed_kernels(env, msg, kernel):
+    """A server whose pools run on different kernels (n=576 on the QC kernel, n=8192 on the
+    stream kernel -- its 2-layer window does not fit one CTA of the QC kernel -- with FP16
+    messages in shared memory and FP32 messages in global memory, as the plain decode plans them;
+    or both on the tile kernel), with their launches forked within each epoch: every frame equals
+    its batch decoded alone."""
     nd, torch = env
     names = ["qc_n576_r12", "qc_n8192_r2732"]
     built = [_grouped(nd, n) for n in names]
     codes = [b[0] for b in built]
     groups = [b[2] for b in built]
-    params = nd.params_default(max_iter=20, msg_dtype={"f32": nd.F32, "f16": nd.F16}[msg])
+    params = nd.params_default(max_iter=20, msg_dtype={"f32": nd.F32, "f16": nd.F16}[msg],
+                               variant=nd.VARIANT_TILE if kernel == "tile" else nd.VARIANT_AUTO)
+    if kernel == "auto":
+        want = nd.VARIANT_STREAM_SMEM if msg == "f16" else nd.VARIANT_STREAM_GLOBAL
+        assert groups[1].plan(nd.params_default(msg_dtype=params.msg_dtype), 1024).variant == want
     srv = nd.Server(groups, params, 48 << 20, epoch_iters=3)
     try:
         reqs = _requests(codes, [300, 40, 7, 120, 64, 33], [2.25, 3.25], seed=7300)
+        handles = [srv.submit(k, llr) for k, llr in reqs]
+        for h in handles:
+            h.wait(120000)
+        st = srv.stats()
+    finally:
+        srv.close()
+    for (k, llr), h in zip(reqs, handles):
+        hard, iters, ok = _alone(nd, torch, groups[k], codes[k], llr, params)
+        np.testing.assert_array_equal(h.hard_words, hard)
+        np.testing.assert_array_equal(h.iters, iters)
+        np.testing.assert_array_equal(h.syndrome_ok, ok)
+    assert st["frames_completed"] == sum(llr.shape[0] for _, llr in reqs)
+    assert st["slots_in_use"] == 0
+
+
+@pytest.mark.parametrize("msg", ["f32", "bf16"])
+def test_served_large_code_on_stream_kernel(env, msg):
+    """n=16200 (the stream kernel, messages in the slots' global state) beside n=2304 (the QC
+    kernel), frames parked every 2 iterations: equal to the batches decoded alone."""
+    nd, torch = env
+    names = ["qc_n2304_r12", "qc_n16200_r23"]
+    built = [_grouped(nd, n) for n in names]
+    codes = [b[0] for b in built]
+    groups = [b[2] for b in built]
+    params = nd.params_default(max_iter=25, msg_dtype={"f32": nd.F32, "bf16": nd.BF16}[msg])
+    assert groups[1].plan(nd.params_default(msg_dtype=params.msg_dtype), 1024).variant == nd.VARIANT_STREAM_GLOBAL
+    srv = nd.Server(groups, params, 64 << 20, epoch_iters=2)
+    try:
+        reqs = _requests(codes, [50, 9, 120, 31, 1, 40], [1.75, 1.85], seed=7600)
         handles = [srv.submit(k, llr) for k, llr in reqs]
         for h in handles:
             h.wait(120000)
