@@ -534,6 +534,8 @@ static ndgsbp_status make_stream_plan(const Groups& g, const ndgsbp_params* p, i
     const int active = Q.Z * tpc;
     const int threads = p->block_threads ? p->block_threads : (active + 31) / 32 * 32;
     if (threads < active || threads > stream_max_threads(tpc)) return NDGSBP_OK;
+    // two lanes per CN: each lane in its own warps (Z a multiple of 32, a block of exactly 2 Z)
+    if (tpc == 2 && (Q.Z % 32 != 0 || threads != active)) return NDGSBP_OK;
     if (Q.n_layers > kStreamMaxLayers) return NDGSBP_OK;
     StreamLayout SL;
     stream_layout(Q, SL);

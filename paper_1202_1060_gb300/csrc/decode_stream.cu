@@ -6,12 +6,15 @@
 namespace ndgsbp {
 
 size_t stream_smem_bytes(const StreamArgs& a, int msg_size, int mode) {
-    size_t b = sa16(static_cast<size_t>(a.r.N) * 4) + sa16(static_cast<size_t>(a.window - 1) * (a.maxdeg | 1) * a.Z * 4);
+    size_t b = sa16(static_cast<size_t>(a.r.N) * 4) +
+               sa16(static_cast<size_t>(a.window - 1) * (a.maxdeg | 1) * a.Z *
+                    (msg_size == 2 && mode != kStreamGlobal ? 2 : 4));   // Old16 (decode_stream_kernel.cuh)
     const size_t slab = sa16(static_cast<size_t>(a.slab_elems) * msg_size);
     if (mode == kStreamSmem) b += sa16(static_cast<size_t>(a.msg_elems) * msg_size);
     if (mode == kStreamBulk) b += static_cast<size_t>(a.n_slabs) * slab;
     b += sa16(static_cast<size_t>(a.nl) * a.maxdeg * 8) + sa16(static_cast<size_t>(a.nl) * 4) +
          static_cast<size_t>(a.n_groupings) * a.G * a.window * 16;
+    if (a.tpc == 2) b += static_cast<size_t>(4) * a.Z * 8;   // pair-exchange slots
     if (mode == kStreamBulk) b += static_cast<size_t>(a.n_slabs) * 8;
     return b;
 }

@@ -2,9 +2,10 @@
 // per CN of the window (n=16200: 2 layers of Z = 360 CNs; n=8192: degree 22).
 //
 // A CTA decodes one frame at a time (persistent CTAs, frames from an atomic counter, so a frame
-// that stops early frees its CTA at once).  Thread t owns lane p = t mod tpc of CN c = t / tpc of
-// a layer (tpc = 1, or 2 for degrees above 11: lane p holds edges [p le, (p+1) le), le =
-// ceil(maxdeg / tpc), as in the tile kernel) and steps
+// that stops early frees its CTA at once).  Thread t = p Z + c owns lane p of CN c of a layer
+// (tpc = 1, or 2 for degrees above 11: lane p holds edges [p le, (p+1) le), le =
+// ceil(maxdeg / tpc), as in the tile kernel; the two lanes of a CN are in different warps and
+// exchange their pair totals through shared memory, see pair_exchange) and steps
 // through the W layers of each group in window order:
 //   phase A, position j = 0..W-1: Eq. (1) for CN c of layer L_g[j] from t = P - L_old (P as it
 //     stood at the start of the sub-iteration: phase A writes no posterior), new messages stored,
@@ -30,6 +31,8 @@
 //                  the CTA drains its copies and returns.
 // Posteriors and messages are in log2 units (see load_llr).
 #pragma once
+
+#include <type_traits>
 
 #include "decode_stream.h"
 #include "lane_cnu.cuh"
@@ -102,17 +105,31 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// OLD16: 16-bit messages whose new values phase B reads back from shared memory (shared-memory
+// and bulk-staged modes) keep the old message (2 bytes) instead of the change (4 bytes): half the
+// buffer, which lets n=8192 keep 2 CTAs per SM beside the pair-exchange slots.  In global mode
+// the read-back would be a global load, so the change is kept.
+template <typename MsgT, int MODE>
+struct Old16 {
+    static constexpr bool value = sizeof(MsgT) == 2 && MODE != kStreamGlobal;
+};
+template <typename MsgT, int MODE>
+using DeltaT = typename std::conditional<Old16<MsgT, MODE>::value, MsgT, float>::type;
+
 // ---- shared-memory layout (stream_smem_bytes on the host computes the same sizes) ------------
 __host__ __device__ constexpr size_t sa16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
 struct StreamSmem {
     float* P;          // [N] posterior (log2 units)
-    float* dbuf;       // [W - 1][Z][maxdeg | 1] changes of positions 0 .. W-2 (entry p le + k for lane p)
+    void* dbuf;        // [W - 1][Z][maxdeg | 1] per position 0 .. W-2 (entry p le + k for lane p): the
+                       // message changes, or the old messages where Old16 holds (phase B forms the
+                       // change from the new message, the same FP32 value)
     unsigned char* msg;  // SMEM: [msg_elems] messages; BULK: [n_slabs][slab_elems] slab buffers
     int2* tab;         // [nl][maxdeg] edge table
     int* ldeg;         // [nl] layer degrees
     int4* gtab;        // [n_groupings][G][W] (l maxdeg, d_l, lbase[l], first use in iteration 1)
     uint64_t* bar;     // BULK: [n_slabs] one mbarrier per slab buffer
+    float2* xbuf;      // tpc = 2: [2 slots][2 lanes][Z] pair totals exchanged between the lanes of a CN
     size_t slab_bytes;
 };
 
@@ -122,8 +139,8 @@ __device__ __forceinline__ StreamSmem stream_smem(unsigned char* smem, const Str
     size_t off = 0;
     s.P = reinterpret_cast<float*>(smem);
     off += sa16(static_cast<size_t>(a.r.N) * 4);
-    s.dbuf = reinterpret_cast<float*>(smem + off);
-    off += sa16(static_cast<size_t>(a.window - 1) * (a.maxdeg | 1) * a.Z * 4);
+    s.dbuf = smem + off;
+    off += sa16(static_cast<size_t>(a.window - 1) * (a.maxdeg | 1) * a.Z * (Old16<MsgT, MODE>::value ? 2 : 4));
     s.msg = smem + off;
     s.slab_bytes = sa16(static_cast<size_t>(a.slab_elems) * sizeof(MsgT));
     if (MODE == kStreamSmem) off += sa16(static_cast<size_t>(a.msg_elems) * sizeof(MsgT));
@@ -134,6 +151,8 @@ __device__ __forceinline__ StreamSmem stream_smem(unsigned char* smem, const Str
     off += sa16(static_cast<size_t>(a.nl) * 4);
     s.gtab = reinterpret_cast<int4*>(smem + off);
     off += static_cast<size_t>(a.n_groupings) * a.G * a.window * 16;
+    s.xbuf = reinterpret_cast<float2*>(smem + off);
+    if (a.tpc == 2) off += static_cast<size_t>(4) * a.Z * sizeof(float2);
     s.bar = reinterpret_cast<uint64_t*>(smem + off);
     return s;
 }
@@ -144,17 +163,43 @@ __device__ __forceinline__ unsigned stream_slab_bytes(int d, int Z) {
     return static_cast<unsigned>(stream_layer_elems(d, Z, 0, sizeof(MsgT), kStreamBulk) * sizeof(MsgT));
 }
 
+// The two lanes of a CN (tpc = 2) sit in different warps: lane p of CN c is thread p Z + c, so
+// the 32 threads of a warp read one block column of P at 32 consecutive VNs -- distinct banks
+// (with both lanes of a CN in one warp, two block columns at unrelated circulant shifts shared
+// the banks: 41.6 % of the shared-memory wavefronts were conflicts for n=8192).  The lanes swap
+// their pair totals through shared memory (xw: this lane's entry, xr: the other lane's) and
+// meet at a named barrier of their two warps (id xid); two slots alternate, so an entry is
+// rewritten only after the other lane has passed the next barrier, i.e. after it has read it.
+// cn >= 0, so its sign bit carries the lane's sign parity.  The values are those lane_exchange
+// gives for two lanes: the other lane's (cn, ce), and the parity of all the CN's input signs.
+struct PairX {
+    uint32_t xw, xr;   // shared-memory addresses of this lane's and the other lane's entry
+    int xid;
+};
+
+__device__ __forceinline__ void pair_exchange(const PairX& x, float cn, float ce, unsigned lpar, float& on, float& oe,
+                                              unsigned& par) {
+    const float sc = __uint_as_float(__float_as_uint(cn) | (lpar & 0x80000000u));
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(x.xw), "f"(sc), "f"(ce) : "memory");
+    asm volatile("bar.sync %0, 64;" ::"r"(x.xid) : "memory");
+    float o0, o1;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(o0), "=f"(o1) : "r"(x.xr) : "memory");
+    on = __uint_as_float(__float_as_uint(o0) & 0x7fffffffu);
+    oe = o1;
+    par = lpar ^ (__float_as_uint(o0) & 0x80000000u);
+}
+
 // Eq. (1) for one lane of CN c (its L <= NP edges at edge-table entries et[0..L-1]) with the
 // messages of that lane at m[k Z], k < L: t = P - L_old (L_old = 0 on a layer's first use in
-// the frame), new messages written back to m, changes to drow[k Z] (shared delta buffer) or
-// dreg[k] (TO_REG).  NP positions are computed: NP = L exactly (no predicates), or NP = LE with
+// the frame), new messages written back to m, changes to drow[k Z] (shared delta buffer; for
+// 16-bit messages the old message instead) or dreg[k] (TO_REG).  NP positions are computed: NP = L exactly (no predicates), or NP = LE with
 // the positions past L neutral (see lane_forward).  The old message is read again from m when
 // its change is formed rather than held in a register through the pass (fewer live registers;
-// measured faster).  Lanes of a CN (tpc = 2) run it together.
-template <typename MsgT, int LE, int NP, bool TO_REG>
+// measured faster).  Lanes of a CN (tpc = 2) run it together and exchange through x.
+template <typename MsgT, int MODE, int LE, int NP, bool TO_REG>
 __device__ __forceinline__ void stream_lane(const int2* __restrict__ et, int L, int c, int Zm, int Zd, int Z4,
                                             const float* __restrict__ P, MsgT* m, bool first, float lim, int tpc,
-                                            unsigned gmask, float* __restrict__ drow, float (&dreg)[LE]) {
+                                            const PairX& x, DeltaT<MsgT, MODE>* __restrict__ drow, float (&dreg)[LE]) {
     static_assert(NP <= LE, "positions above the lane width");
     if (NP < LE) L = NP;   // exact instance: L is the constant NP
     float t[NP], xu[NP], pn[NP], pe[NP];
@@ -168,16 +213,18 @@ __device__ __forceinline__ void stream_lane(const int2* __restrict__ et, int L, 
         }
     }
     lane_forward<NP>(t, L, lim, xu, pn, pe, cn, ce, lpar);
-    float on, oe;
-    unsigned par;
-    lane_exchange(tpc, gmask, cn, ce, lpar, on, oe, par);
+    float on = 1.f, oe = 0.f;
+    unsigned par = lpar;
+    if (tpc == 2) pair_exchange(x, cn, ce, lpar, on, oe, par);
     lane_backward<NP>(xu, pn, pe, L, on, oe, par & 0x80000000u, lim, [&](int k, float val) {
         const MsgT q = from_f<MsgT>(val);
-        const float old = first ? 0.f : to_f(m[k * Zm]);
+        const MsgT om = first ? from_f<MsgT>(0.f) : m[k * Zm];
         m[k * Zm] = q;
-        const float d = to_f(q) - old;
-        if (TO_REG)
+        const float d = to_f(q) - to_f(om);
+        if constexpr (TO_REG)
             dreg[k] = d;
+        else if constexpr (Old16<MsgT, MODE>::value)
+            drow[k * Zd] = om;   // phase B forms to_f(new) - to_f(old): the same value d
         else
             drow[k * Zd] = d;
     });
@@ -186,18 +233,18 @@ __device__ __forceinline__ void stream_lane(const int2* __restrict__ et, int L, 
 // Exact-degree dispatch for a CN of degree d split into L-edge lanes: a layer's CNs share their
 // degree, so the branch is uniform across a warp (for tpc = 2 only when both lanes hold LE
 // edges); other degrees take the padded width-LE path.
-template <typename MsgT, int LE, int TPC, bool TO_REG>
+template <typename MsgT, int MODE, int LE, int TPC, bool TO_REG>
 __device__ __forceinline__ void stream_lane_d(int d, const int2* __restrict__ et, int L, int c, int Zm, int Zd, int Z4,
                                               const float* __restrict__ P, MsgT* m, bool first, float lim,
-                                              unsigned gmask, float* __restrict__ drow, float (&dreg)[LE]) {
+                                              const PairX& x, DeltaT<MsgT, MODE>* __restrict__ drow, float (&dreg)[LE]) {
     if (d == TPC * LE)
-        stream_lane<MsgT, LE, LE, TO_REG>(et, LE, c, Zm, Zd, Z4, P, m, first, lim, TPC, gmask, drow, dreg);
+        stream_lane<MsgT, MODE, LE, LE, TO_REG>(et, LE, c, Zm, Zd, Z4, P, m, first, lim, TPC, x, drow, dreg);
     else if (TPC == 1 && d == LE - 1)
-        stream_lane<MsgT, LE, LE - 1, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, gmask, drow, dreg);
+        stream_lane<MsgT, MODE, LE, LE - 1, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, x, drow, dreg);
     else if (TPC == 1 && d == LE - 2)
-        stream_lane<MsgT, LE, LE - 2, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, gmask, drow, dreg);
+        stream_lane<MsgT, MODE, LE, LE - 2, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, x, drow, dreg);
     else
-        stream_lane<MsgT, LE, LE, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, gmask, drow, dreg);
+        stream_lane<MsgT, MODE, LE, LE, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, x, drow, dreg);
 }
 
 // P += changes of one lane, change k = src(k) for k < L: EXACT instances take L = NP (no
@@ -282,9 +329,13 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
     }
     if (tid == 0) s_err = 0u;
     // (the leading barrier of next_frame orders the tables and barrier set-up before any use)
-    const int c = tid / TPC, p = tid - c * TPC;
-    const bool active = c < Z;
-    const unsigned gmask = TPC == 1 ? 0u : (3u << ((tid & 31) & ~1));
+    // lane p of CN c: thread p Z + c (for tpc = 2 the plan makes Z a multiple of 32 and the block
+    // 2 Z threads, so a warp holds one lane of 32 consecutive CNs)
+    const int p = TPC == 1 ? 0 : tid / Z;
+    const int c = tid - p * Z;
+    const bool active = c < Z && p < TPC;
+    int xs = 0;   // exchange slot (tpc = 2)
+    const uint32_t xb0 = smem_addr(s.xbuf);
     const float lim = r.llr_max;
     MsgT* gmsg = MODE != kStreamSmem ? static_cast<MsgT*>(a.ws_msgs) + static_cast<size_t>(blockIdx.x) * a.ws_stride
                                      : nullptr;
@@ -371,30 +422,37 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
                 }
                 // ---- phase A: Eq. (1) on CN c of every layer of the window, in window order ----
                 float dreg[LE];
+                // this lane's messages of window position j (layer record ge)
+                auto msg_at = [&](int j, const int4& ge) -> MsgT* {
+                    if constexpr (MODE == kStreamSmem) {
+                        return smsg + ge.z + c * stream_cn_stride(ge.y, sizeof(MsgT)) + p * le;
+                    } else if constexpr (MODE == kStreamGlobal) {
+                        return gmsg + ge.z + p * le * Zr + c;
+                    } else {
+                        const int bj = kb + j < S ? kb + j : kb + j - S;
+                        return reinterpret_cast<MsgT*>(s.msg + static_cast<size_t>(bj) * s.slab_bytes) +
+                               c * stream_cn_stride(ge.y, sizeof(MsgT)) + p * le;
+                    }
+                };
+                DeltaT<MsgT, MODE>* dbuf = static_cast<DeltaT<MsgT, MODE>*>(s.dbuf);
                 if (active) {
                     for (int j = 0; j < W; ++j) {
                         const int4 ge = gt[g * W + j];
                         const int L = min(max(ge.y - p * le, 0), le);
                         const int2* et = s.tab + ge.x + p * le;
                         const bool first = it == 1 && ge.w;
-                        MsgT* m;
-                        if constexpr (MODE == kStreamSmem) {
-                            m = smsg + ge.z + c * stream_cn_stride(ge.y, sizeof(MsgT)) + p * le;
-                        } else if constexpr (MODE == kStreamGlobal) {
-                            m = gmsg + ge.z + p * le * Zr + c;
-                        } else {
-                            const int bj = kb + j < S ? kb + j : kb + j - S;
-                            m = reinterpret_cast<MsgT*>(s.msg + static_cast<size_t>(bj) * s.slab_bytes) +
-                                c * stream_cn_stride(ge.y, sizeof(MsgT)) + p * le;
-                        }
+                        MsgT* m = msg_at(j, ge);
                         // row stride of a thread's messages: 1 (CN-major) or Zr (edge-major)
                         const int Zm = MODE == kStreamGlobal ? Zr : 1;
+                        const PairX x{xb0 + static_cast<uint32_t>((2 * xs + p) * Z + c) * 8u,
+                                      xb0 + static_cast<uint32_t>((2 * xs + 1 - p) * Z + c) * 8u, 1 + (c >> 5)};
+                        xs ^= 1;
                         if (j == W - 1) {
-                            stream_lane_d<MsgT, LE, TPC, true>(ge.y, et, L, c, Zm, 1, Z4, P, m, first, lim, gmask,
+                            stream_lane_d<MsgT, MODE, LE, TPC, true>(ge.y, et, L, c, Zm, 1, Z4, P, m, first, lim, x,
                                                                nullptr, dreg);
                         } else {
-                            float* drow = s.dbuf + static_cast<size_t>(j * Z + c) * Sd + p * le;
-                            stream_lane_d<MsgT, LE, TPC, false>(ge.y, et, L, c, Zm, 1, Z4, P, m, first, lim, gmask,
+                            DeltaT<MsgT, MODE>* drow = dbuf + static_cast<size_t>(j * Z + c) * Sd + p * le;
+                            stream_lane_d<MsgT, MODE, LE, TPC, false>(ge.y, et, L, c, Zm, 1, Z4, P, m, first, lim, x,
                                                                 drow, dreg);
                         }
                     }
@@ -410,8 +468,15 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
                         if (jj == W - 1) {
                             stream_add_d<LE, TPC>(ge.y, P, et, L, c, Z4, [&](int k) { return dreg[k]; });
                         } else {
-                            const float* drow = s.dbuf + static_cast<size_t>(jj * Z + c) * Sd + p * le;
-                            stream_add_d<LE, TPC>(ge.y, P, et, L, c, Z4, [&](int k) { return drow[k]; });
+                            const DeltaT<MsgT, MODE>* drow = dbuf + static_cast<size_t>(jj * Z + c) * Sd + p * le;
+                            if constexpr (Old16<MsgT, MODE>::value) {
+                                const MsgT* mj = msg_at(jj, ge);
+                                const int Zm = MODE == kStreamGlobal ? Zr : 1;
+                                stream_add_d<LE, TPC>(ge.y, P, et, L, c, Z4,
+                                                      [&](int k) { return to_f(mj[k * Zm]) - to_f(drow[k]); });
+                            } else {
+                                stream_add_d<LE, TPC>(ge.y, P, et, L, c, Z4, [&](int k) { return drow[k]; });
+                            }
                         }
                     }
                     __syncthreads();
@@ -431,14 +496,16 @@ __global__ void __launch_bounds__(stream_block_bound(TPC), 2) stream_decode_kern
             const bool last = it >= r.max_iter;
             if (r.early_stop || last) {
                 unsigned bad = 0u;
-                for (int l = 0; l < nl; ++l) {
+                // one thread per CN and layer: with tpc = 2 lane p checks whole CNs of the layers
+                // l = p, p + 2, ... (both halves of the edge list), uniform across its warp
+                for (int l = p; l < nl; l += TPC) {
                     unsigned pb = 0u;
                     if (active) {
                         const int d = s.ldeg[l];
-                        const int L = min(max(d - p * le, 0), le);
-                        pb = stream_parity_d<LE, TPC>(d, P, s.tab + l * md + p * le, L, c, Z4);
+                        const int2* et = s.tab + l * md;
+                        pb = stream_parity_d<LE, TPC>(d, P, et, min(d, le), c, Z4);
+                        if (TPC == 2) pb ^= stream_parity_d<LE, TPC>(d, P, et + le, max(d - le, 0), c, Z4);
                     }
-                    if (TPC == 2) pb ^= __shfl_xor_sync(gmask, pb, 1);
                     bad |= pb;
                     // once a lane has found an unsatisfied check the frame's syndrome is decided
                     if (__any_sync(0xffffffffu, bad)) break;
