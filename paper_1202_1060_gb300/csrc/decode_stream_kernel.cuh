@@ -172,6 +172,24 @@ __device__ __forceinline__ unsigned stream_slab_bytes(int d, int Z) {
 // rewritten only after the other lane has passed the next barrier, i.e. after it has read it.
 // cn >= 0, so its sign bit carries the lane's sign parity.  The values are those lane_exchange
 // gives for two lanes: the other lane's (cn, ce), and the parity of all the CN's input signs.
+// Raw bits of a 16-bit message and back (HOLD in stream_lane).
+template <typename MsgT>
+__device__ __forceinline__ unsigned short msg_bits(MsgT v);
+template <>
+__device__ __forceinline__ unsigned short msg_bits<__half>(__half v) { return __half_as_ushort(v); }
+template <>
+__device__ __forceinline__ unsigned short msg_bits<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+template <>
+__device__ __forceinline__ unsigned short msg_bits<float>(float) { return 0; }
+template <typename MsgT>
+__device__ __forceinline__ MsgT msg_from_bits(unsigned short b);
+template <>
+__device__ __forceinline__ __half msg_from_bits<__half>(unsigned short b) { return __ushort_as_half(b); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 msg_from_bits<__nv_bfloat16>(unsigned short b) { return __ushort_as_bfloat16(b); }
+template <>
+__device__ __forceinline__ float msg_from_bits<float>(unsigned short) { return 0.f; }
+
 struct PairX {
     uint32_t xw, xr;   // shared-memory addresses of this lane's and the other lane's entry
     int xid;
@@ -196,29 +214,41 @@ __device__ __forceinline__ void pair_exchange(const PairX& x, float cn, float ce
 // the positions past L neutral (see lane_forward).  The old message is read again from m when
 // its change is formed rather than held in a register through the pass (fewer live registers;
 // measured faster).  Lanes of a CN (tpc = 2) run it together and exchange through x.
-template <typename MsgT, int MODE, int LE, int NP, bool TO_REG>
+template <typename MsgT, int MODE, int TPC, int LE, int NP, bool TO_REG>
 __device__ __forceinline__ void stream_lane(const int2* __restrict__ et, int L, int c, int Zm, int Zd, int Z4,
-                                            const float* __restrict__ P, MsgT* m, bool first, float lim, int tpc,
+                                            const float* __restrict__ P, MsgT* m, bool first, float lim,
                                             const PairX& x, DeltaT<MsgT, MODE>* __restrict__ drow, float (&dreg)[LE]) {
     static_assert(NP <= LE, "positions above the lane width");
     if (NP < LE) L = NP;   // exact instance: L is the constant NP
     float t[NP], xu[NP], pn[NP], pe[NP];
     float cn = 1.f, ce = 0.f;
     unsigned lpar = 0u;
+    // 16-bit messages in global memory at one lane per CN: the old messages stay in registers, two
+    // per word, for the backward pass (a re-read would be a global load); otherwise (and at two
+    // lanes per CN, whose 64-register budget they would push into spills) they are read again
+    constexpr bool HOLD = sizeof(MsgT) == 2 && MODE == kStreamGlobal && TPC == 1;
+    uint32_t ob[HOLD ? (NP + 1) / 2 : 1];
+#pragma unroll
+    for (int i = 0; i < (HOLD ? (NP + 1) / 2 : 1); ++i) ob[i] = 0u;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         if (k < L) {
-            const float old = first ? 0.f : to_f(m[k * Zm]);
-            t[k] = at_b(const_cast<float*>(P), tile_vb(et[k], c, Z4)) - old;
+            const MsgT om = first ? from_f<MsgT>(0.f) : m[k * Zm];
+            if constexpr (HOLD) ob[k / 2] |= static_cast<uint32_t>(msg_bits(om)) << (16 * (k & 1));
+            t[k] = at_b(const_cast<float*>(P), tile_vb(et[k], c, Z4)) - to_f(om);
         }
     }
     lane_forward<NP>(t, L, lim, xu, pn, pe, cn, ce, lpar);
     float on = 1.f, oe = 0.f;
     unsigned par = lpar;
-    if (tpc == 2) pair_exchange(x, cn, ce, lpar, on, oe, par);
+    if (TPC == 2) pair_exchange(x, cn, ce, lpar, on, oe, par);
     lane_backward<NP>(xu, pn, pe, L, on, oe, par & 0x80000000u, lim, [&](int k, float val) {
         const MsgT q = from_f<MsgT>(val);
-        const MsgT om = first ? from_f<MsgT>(0.f) : m[k * Zm];
+        MsgT om;
+        if constexpr (HOLD)
+            om = msg_from_bits<MsgT>(static_cast<unsigned short>(ob[k / 2] >> (16 * (k & 1))));
+        else
+            om = first ? from_f<MsgT>(0.f) : m[k * Zm];
         m[k * Zm] = q;
         const float d = to_f(q) - to_f(om);
         if constexpr (TO_REG)
@@ -238,13 +268,13 @@ __device__ __forceinline__ void stream_lane_d(int d, const int2* __restrict__ et
                                               const float* __restrict__ P, MsgT* m, bool first, float lim,
                                               const PairX& x, DeltaT<MsgT, MODE>* __restrict__ drow, float (&dreg)[LE]) {
     if (d == TPC * LE)
-        stream_lane<MsgT, MODE, LE, LE, TO_REG>(et, LE, c, Zm, Zd, Z4, P, m, first, lim, TPC, x, drow, dreg);
+        stream_lane<MsgT, MODE, TPC, LE, LE, TO_REG>(et, LE, c, Zm, Zd, Z4, P, m, first, lim, x, drow, dreg);
     else if (TPC == 1 && d == LE - 1)
-        stream_lane<MsgT, MODE, LE, LE - 1, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, x, drow, dreg);
+        stream_lane<MsgT, MODE, TPC, LE, LE - 1, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, x, drow, dreg);
     else if (TPC == 1 && d == LE - 2)
-        stream_lane<MsgT, MODE, LE, LE - 2, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, x, drow, dreg);
+        stream_lane<MsgT, MODE, TPC, LE, LE - 2, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, x, drow, dreg);
     else
-        stream_lane<MsgT, MODE, LE, LE, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, TPC, x, drow, dreg);
+        stream_lane<MsgT, MODE, TPC, LE, LE, TO_REG>(et, L, c, Zm, Zd, Z4, P, m, first, lim, x, drow, dreg);
 }
 
 // P += changes of one lane, change k = src(k) for k < L: EXACT instances take L = NP (no
