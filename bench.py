@@ -1090,7 +1090,7 @@ def run_decode(args):
     hard = torch.empty((F, W), dtype=torch.int32, device=dev)
     stats = torch.zeros(nd.STATS_LEN, dtype=torch.int64, device=dev)
     dt = {"f32": nd.F32, "f16": nd.F16, "bf16": nd.BF16}[args.msg]
-    p = nd.params_default(max_iter=IMAX_ND, msg_dtype=dt, variant=args.variant)
+    p = nd.params_default(max_iter=IMAX_ND, msg_dtype=dt, variant=args.variant, ctas_per_sm=args.ctas_per_sm)
     if args.vertical > 0:
         # the vertical (VN-group) schedule with --vertical random VN groups
         vg = nd.VGroups.build(code, args.vertical, GROUP_SEED)
@@ -1233,6 +1233,7 @@ def main():
     ap.add_argument("--code", default="qc_n16200_r23", help="decode workload: the code")
     ap.add_argument("--ebn0", type=float, default=None, help="decode workload: Eb/N0 (default: the FER~1e-3 point)")
     ap.add_argument("--msg", choices=["f32", "f16", "bf16"], default="f16", help="decode workload: message storage")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="decode workload: residency cap (0 = library choice)")
     ap.add_argument("--vertical", type=int, default=0,
                     help="decode workload: decode with the vertical schedule over this many VN groups (0 = NDGSBP)")
     ap.add_argument("--precision-oracle-frames", type=int, default=65536,
