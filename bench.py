@@ -243,9 +243,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(per_point),
+        "data": "synthetic", "config": workload_config(args.frames),
         "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{per_point} frames per Eb/N0 point x {len(EBN0)} points per step"},
+                         "sample": f"a bounded sample of the workload: {per_point} frames per Eb/N0 point x "
+                                   f"{len(EBN0)} points per step (the workload has {args.frames} per point)"},
         "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
