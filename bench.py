@@ -960,12 +960,39 @@ def run_serving(args):
     return 0
 
 
+EDGE_ERR_FRAMES = 64
+EDGE_ERR_ITERS = (1, 5)
+
+
+def edge_error(nd, torch, g, msg_dtype, llr, ref_k, stream):
+    """Largest per-edge CN->VN message error of the GPU against the oracle's (ref_k[k], natural
+    LLR units) after k iterations without early stop, on the frames of llr: absolute and relative
+    to max(|L_oracle|, 1)."""
+    import numpy as np
+    dev = llr.device
+    F, E = llr.shape[0], int(ref_k[EDGE_ERR_ITERS[0]].shape[1])
+    W = (llr.shape[1] + 31) // 32
+    hard = torch.empty((F, W), dtype=torch.int32, device=dev)
+    msgs = torch.zeros((F, E), dtype=torch.float32, device=dev)
+    out = {"frames": F}
+    for k in EDGE_ERR_ITERS:
+        p = nd.params_default(max_iter=k, msg_dtype=msg_dtype, early_stop=0)
+        ws = torch.zeros(max(256, g.workspace_size(p, F)), dtype=torch.uint8, device=dev)
+        nd.decode(g, p, llr, ws, hard, messages=msgs, stream=stream)
+        torch.cuda.synchronize()
+        m, r = msgs.cpu().numpy(), ref_k[k]
+        d = np.abs(m - r)
+        out[f"k{k}"] = {"max_abs": float(d.max()), "max_rel": float((d / np.maximum(np.abs(r), 1.0)).max())}
+    return out
+
+
 def run_precision(args):
     """Reduced-precision messages: the n=2304 r1/2 and n=16200 r2/3 QC codes at their FER ~ 1e-3
     points, 262,144 frames, FP32 / FP16 / BF16 message storage with FP32 arithmetic.  The FP64
     oracle decodes the first --precision-oracle-frames (n=2304) and a quarter of that (n=16200) of
     the same LLRs: every storage type's FER on those frames must lie inside the oracle's 95%
-    Clopper-Pearson interval, and so must its FER over all frames."""
+    Clopper-Pearson interval, and so must its FER over all frames.  Each row also states the
+    largest per-edge message error against the oracle after 1 and 5 iterations on 64 frames."""
     import numpy as np
     import torch
     torch.cuda.set_device(0)
@@ -1007,6 +1034,13 @@ def run_precision(args):
         oracle_rows.append({"code": name, "frames": n_or, "fer": fe_or / n_or, "fer_ci95": [lo, hi],
                             "seconds": t_or, "frames_per_s": n_or / t_or, "gbit_s": n_or * (c.N - c.M) / t_or / 1e9,
                             "cores": host_cores()})
+        # per-edge message error: the oracle's CN->VN messages after k iterations (no early stop)
+        # of the first EDGE_ERR_FRAMES frames
+        n_e = min(EDGE_ERR_FRAMES, F)
+        host_e = llr[:n_e].cpu().numpy().astype(np.float64)
+        ref_k = {k: O.ndgsbp_decode(c, q["grp_ptr"], q["cn_idx"], host_e, k, early_stop=False, want_total=False,
+                                    want_c2v=True).c2v for k in EDGE_ERR_ITERS}
+        del host_e
         for msg, dt in (("f32", nd.F32), ("f16", nd.F16), ("bf16", nd.BF16)):
             p = nd.params_default(max_iter=IMAX_ND, msg_dtype=dt)
             ws = torch.zeros(max(256, g.workspace_size(p, F)), dtype=torch.uint8, device=dev)
@@ -1036,7 +1070,8 @@ def run_precision(args):
                          "ber": float(st[nd.STAT_BIT_ERRORS] / (st[nd.STAT_FRAMES] * c.N)),
                          "mean_iterations": float(st[nd.STAT_ITERATIONS] / st[nd.STAT_FRAMES]),
                          "variant": plan.variant, "ms_per_decode": 1e3 * sec / args.steps,
-                         "mufu_tops": mufu / sec / 1e12})
+                         "mufu_tops": mufu / sec / 1e12,
+                         "max_edge_error": edge_error(nd, torch, g, dt, llr[:n_e], ref_k, stream)})
             del ws
         del llr
     clk = clocks.stop()
@@ -1243,7 +1278,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-backlog", type=int, default=9000,
                     help="requests of the saturated capacity window (about 3 s of work)")
-    ap.add_argument("--epoch-iters", type=int, default=12)
+    ap.add_argument("--epoch-iters", type=int, default=30)
     ap.add_argument("--arrival-seed", type=int, default=20260)
     args = ap.parse_args()
     os.makedirs(OUT_DIR, exist_ok=True)
