@@ -1276,7 +1276,7 @@ def main():
                     help="oracle frames for n=2304 (a quarter of that for n=16200)")
     ap.add_argument("--serve-budget-mb", type=int, default=2048)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
-    ap.add_argument("--serve-backlog", type=int, default=9000,
+    ap.add_argument("--serve-backlog", type=int, default=10500,
                     help="requests of the saturated capacity window (about 3 s of work)")
     ap.add_argument("--epoch-iters", type=int, default=30)
     ap.add_argument("--arrival-seed", type=int, default=20260)
