@@ -276,6 +276,15 @@ ndgsbp_status ndgsbp_decode(const ndgsbp_groups* groups, const ndgsbp_params* pa
  * clears the word when it starts.  Errors: INVALID, CUDA. */
 ndgsbp_status ndgsbp_workspace_status(const void* d_workspace, uint32_t* status, void* stream);
 
+/* Test hooks for the failure path of the bounded waits (process-wide, read when a decode is
+ * launched; not for production use).  skip_first_bulk_load = 1: every CTA of a STREAM_BULK
+ * launch arms the mbarrier of its first bulk message load but issues no copy, so that wait can
+ * only give up -- the CTA then sets bit 0 of the workspace status word and stops, leaving its
+ * frame's outputs unwritten, and no copy is left in flight.  wait_polls: polls before a bounded
+ * wait gives up (0 = the default, about 0.3 s).  ndgsbp_test_hooks(0, 0) restores normal
+ * decoding.  Errors: INVALID. */
+ndgsbp_status ndgsbp_test_hooks(int32_t skip_first_bulk_load, uint32_t wait_polls);
+
 /* ndgsbp_decode plus the fused statistics epilogue and debug outputs of ndgsbp_extras
  * (FER/BER counters against the transmitted word, iteration histogram, retire timestamps,
  * final CN->VN messages).  extras may be NULL. */

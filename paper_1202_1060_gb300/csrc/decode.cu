@@ -18,6 +18,7 @@
 // The layered QC kernel (decode_qc.cu) runs the same two phases with circulant index
 // arithmetic instead of tables.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 
@@ -848,6 +849,12 @@ static ndgsbp_status static_scratch_address(void** out) {
 }
 
 // Launch a plan with `ws` as its scratch (its counter already cleared on the stream).
+// Test hooks of the bulk-staged stream kernel (ndgsbp_test_hooks): leave the first bulk load of
+// each CTA unissued, and the polls a bounded wait makes before it gives up (0 = the default).
+static std::atomic<int> g_hook_skip_load{0};
+static std::atomic<unsigned> g_hook_wait_polls{0};
+constexpr unsigned kDefaultWaitPolls = 1u << 22;   // about 0.3 s of polling
+
 // The table and shape arguments of a stream-kernel launch (everything but the run arguments,
 // the message slots and the status word).
 static void fill_stream_args(StreamArgs& a, const Plan& plan) {
@@ -873,8 +880,9 @@ static void fill_stream_args(StreamArgs& a, const Plan& plan) {
     a.ring = D.ring;
     a.n_slabs = plan.stream_slabs;
     a.ws_stride = plan.stream_ws_stride;
-    a.wait_limit = 1u << 22;
-    a.test_skip_load = 0;
+    const unsigned polls = g_hook_wait_polls.load();
+    a.wait_limit = polls ? polls : kDefaultWaitPolls;
+    a.test_skip_load = g_hook_skip_load.load();
 }
 
 static ndgsbp_status launch_plan(const Groups& g, const Plan& plan, const ndgsbp_params* params, const void* d_llr,
@@ -1149,6 +1157,15 @@ ndgsbp_status ndgsbp_decode(const ndgsbp_groups* groups, const ndgsbp_params* pa
                             void* stream) {
     return ndgsbp_decode_ex(groups, params, d_llr, llr_dtype, n_frames, d_workspace, workspace_bytes,
                             d_hard_bits, d_iters, d_syndrome_ok, d_posterior, nullptr, stream);
+}
+
+ndgsbp_status ndgsbp_test_hooks(int32_t skip_first_bulk_load, uint32_t wait_polls) {
+    clear_error();
+    if (skip_first_bulk_load != 0 && skip_first_bulk_load != 1)
+        return fail(NDGSBP_ERR_INVALID, "test_hooks: skip_first_bulk_load must be 0 or 1");
+    g_hook_skip_load.store(skip_first_bulk_load);
+    g_hook_wait_polls.store(wait_polls);
+    return NDGSBP_OK;
 }
 
 ndgsbp_status ndgsbp_workspace_status(const void* d_workspace, uint32_t* status, void* stream) {

@@ -125,6 +125,7 @@ _SIGS = {
                                 _P, _P, _P, _P, ctypes.POINTER(Extras), _P]),
     "ndgsbp_decode_static": (_I32, [_P, ctypes.POINTER(Params), _P, _I32, _I64, _P, _P, _P, _P, _P]),
     "ndgsbp_workspace_status": (_I32, [_P, ctypes.POINTER(_U32), _P]),
+    "ndgsbp_test_hooks": (_I32, [_I32, _U32]),
     "ndgsbp_mufu_probe": (_I32, [_I32, _I64, _I32, _I32, _P, _P]),
     "ndgsbp_ragged_create": (_I32, [_P, _I32, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
     "ndgsbp_ragged_info": (_I32, [_P, ctypes.POINTER(Plan), _P]),
@@ -457,6 +458,11 @@ def workspace_status(workspace, stream=None) -> int:
     v = ctypes.c_uint32(0)
     _check(_lib.ndgsbp_workspace_status(_dptr(workspace), ctypes.byref(v), _stream(stream)))
     return int(v.value)
+
+
+def test_hooks(skip_first_bulk_load: int = 0, wait_polls: int = 0):
+    """ndgsbp_test_hooks: drive the bulk-staged stream kernel's bounded waits to give up (tests)."""
+    _check(_lib.ndgsbp_test_hooks(int(skip_first_bulk_load), int(wait_polls)))
 
 
 def mufu_probe(op: int, iters: int, blocks: int, threads: int, sink, stream=None):

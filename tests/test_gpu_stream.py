@@ -198,3 +198,31 @@ def test_auto_plan_and_modes_agree(env, name):
     assert all(r["status"] == 0 for r in runs.values())
     it = runs["bulk"]["iters"]
     assert it.min() >= 1 and it.max() <= 25
+
+
+def test_bulk_wait_gives_up_and_reports(env):
+    """The failure path of the bounded mbarrier waits (no GPU fault involved): with the test hook
+    every CTA of a STREAM_BULK launch leaves its first bulk load unissued, so that wait can only
+    give up.  The launch must end by itself, set bit 0 of the workspace status word and leave the
+    outputs of the frames it could not finish unwritten; the next decode on the same context and
+    workspace must clear the word and equal the shared-memory mode bit for bit."""
+    nd, torch = env
+    c = I.code_by_name("qc_n8192_r2732")
+    g = _groups(nd, c, "cyclic")
+    F = 48
+    llr = I.channel_llr(c.N, F, 3.3, I.design_rate(c), seed=4711, dtype=np.float32)
+    kw = dict(max_iter=20, msg_dtype=nd.F16)
+    try:
+        nd.test_hooks(1, 1 << 12)
+        bad = _run(nd, torch, g, c, llr, variant=nd.VARIANT_STREAM_BULK, **kw)
+    finally:
+        nd.test_hooks(0, 0)
+    assert bad["status"] & 1
+    assert (bad["iters"] == -1).all()          # no frame finished: every CTA stopped on its first
+    assert (bad["ok"] == 7).all()
+    good = _run(nd, torch, g, c, llr, variant=nd.VARIANT_STREAM_BULK, **kw)
+    ref = _run(nd, torch, g, c, llr, variant=nd.VARIANT_STREAM_SMEM, **kw)
+    assert good["status"] == 0
+    _same(good, ref, "bulk after a given-up wait")
+    with pytest.raises(nd.NdgsbpError):
+        nd.test_hooks(2, 0)
