@@ -189,10 +189,10 @@ def profiled_traffic(kernel_name):
 # ------------------------------------------------------------------------------------------
 # CPU oracle leg
 # ------------------------------------------------------------------------------------------
-def oracle_sweep(frames_per_point, threads=None, seed_base=CHANNEL_SEED):
+def oracle_sweep(frames_per_point, threads=None, seed_base=CHANNEL_SEED, keep=None):
     """Decode frames_per_point frames at every Eb/N0 point with the FP64 oracle (its own channel
     generator, same definition and seeds as the GPU generator).  Returns (seconds, frames, errors
-    per point)."""
+    per point); with keep a list, appends each point's oracle Result to it."""
     from oracle import oracle as O
     from paper_1202_1060_gb300 import inputs as I
     code = I.code_by_name(CODE_NAME)
@@ -203,8 +203,36 @@ def oracle_sweep(frames_per_point, threads=None, seed_base=CHANNEL_SEED):
     for llr in llrs:
         r = O.ndgsbp_decode(code, gp, gc, llr, IMAX_ND, want_total=False, n_threads=threads)
         fe.append(int(r.hard.any(axis=1).sum()))
+        if keep is not None:
+            keep.append(r)
     dt = time.perf_counter() - t0
     return dt, frames_per_point * len(EBN0), fe
+
+
+def paired_check(nd, torch, code, c, groups, params, oracle_results, n, dev, stream):
+    """The GPU decodes the same n frames per Eb/N0 point as the oracle (step 0's first n frames,
+    same seeds) outside the timed region; counts, per point, the frames whose frame-error status,
+    hard decisions or iteration counts differ from the oracle's (FP32 against FP64: differences
+    are expected only on frames the oracle does not decode, whose trajectories are chaotic)."""
+    import numpy as np
+    W = (c.N + 31) // 32
+    llr = torch.empty((n, c.N), dtype=torch.float32, device=dev)
+    hard = torch.empty((n, W), dtype=torch.int32, device=dev)
+    iters = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = torch.zeros(max(256, groups.workspace_size(params, n)), dtype=torch.uint8, device=dev)
+    out = {"frames_per_point": n, "frame_error_status_differs": [], "bits_differ_frames": [],
+           "iterations_differ": [], "oracle_failing": []}
+    for i, (eb, ref) in enumerate(zip(EBN0, oracle_results)):
+        nd.awgn_llr(code, n, eb, RATE, channel_seed(i, 0, 0), llr, stream=stream)
+        nd.decode(groups, params, llr, ws, hard, iters, stream=stream)
+        torch.cuda.synchronize()
+        bits = nd.unpack_bits(hard, c.N)
+        it = iters.cpu().numpy()
+        out["frame_error_status_differs"].append(int((bits.any(axis=1) != ref.hard.any(axis=1)).sum()))
+        out["bits_differ_frames"].append(int((bits != ref.hard).any(axis=1).sum()))
+        out["iterations_differ"].append(int((it != ref.iters).sum()))
+        out["oracle_failing"].append(int((ref.synd_ok == 0).sum()))
+    return out
 
 
 def clopper_pearson(k, n, alpha=0.05):
@@ -502,7 +530,8 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        dt, nf, fe_or = oracle_sweep(args.cpu_frames)
+        kept = []
+        dt, nf, fe_or = oracle_sweep(args.cpu_frames, keep=kept)
         cpu = {"value": nf * 1152 / dt / 1e9, "unit": "Gbit/s", "cores": host_cores(), "kind": "oracle",
                "sample": f"{args.cpu_frames} frames at each of the {len(EBN0)} Eb/N0 points (same channel "
                          f"definition and seeds), {dt:.1f} s", "seconds": dt}
@@ -515,6 +544,7 @@ def run_ours(args):
         cpu["oracle_fer"] = [f / args.cpu_frames for f in fe_or]
         cpu["oracle_fer_ci95"] = fer_ci
         cpu["gpu_fer_inside_ci"] = all(lo <= g <= hi for g, (lo, hi) in zip(fer, fer_ci))
+        cpu["paired"] = paired_check(nd, torch, code, c, groups, params, kept, args.cpu_frames, dev, stream)
         # the same oracle on one core (a smaller sample)
         dt1, nf1, _ = oracle_sweep(args.cpu_frames_1core, threads=1)
         cpu["one_core"] = {"value": nf1 * 1152 / dt1 / 1e9, "unit": "Gbit/s", "cores": 1,
