@@ -1137,8 +1137,13 @@ def run_precision(args):
 
 def run_decode(args):
     """One code alone (the profiling command of the committed kernel summaries): --code at --ebn0,
-    --frames frames of GPU-generated LLRs, cyclic 2-layer NDGSBP, I_max 25, --msg storage,
-    --variant; --warmup untimed then --steps timed decodes (CUDA events)."""
+    --frames frames of GPU-generated LLRs, cyclic 2-layer NDGSBP (or --vertical G VN groups),
+    I_max 25, --msg storage, --variant; --warmup untimed then --steps timed decodes (CUDA events).
+    Beside it: the MUFU roofline of the schedule's Eq. (1) operations against the per-op rates
+    measured by ndgsbp_mufu_probe, and the FP64 oracle (same schedule and groups) timed on the
+    host cores on the first --decode-oracle-frames frames, with the frames on which GPU and
+    oracle disagree about a frame error counted."""
+    import numpy as np
     import torch
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
@@ -1157,35 +1162,76 @@ def run_decode(args):
     stats = torch.zeros(nd.STATS_LEN, dtype=torch.int64, device=dev)
     dt = {"f32": nd.F32, "f16": nd.F16, "bf16": nd.BF16}[args.msg]
     p = nd.params_default(max_iter=IMAX_ND, msg_dtype=dt, variant=args.variant, ctas_per_sm=args.ctas_per_sm)
+    from oracle import oracle as O
+    O.build()
+    q = g.query()
+    deg = np.diff(np.asarray(c.row_ptr, dtype=np.int64))
     if args.vertical > 0:
         # the vertical (VN-group) schedule with --vertical random VN groups
         vg = nd.VGroups.build(code, args.vertical, GROUP_SEED)
+        vq = vg.query()
+        oracle_run = lambda x: O.vertical_decode(c, vq["grp_ptr"], vq["grp_vn"], x, IMAX_ND, want_total=False)
+        # Eq. (1) per edge of a group's VNs: d - 1 exponentials, one reciprocal and one logarithm
+        ops_per_iter = {"ex2": int((deg * (deg - 1)).sum()), "rcp": int(c.E), "lg2": int(c.E)}
         sched = f"vertical shuffled BP, {args.vertical} VN groups"
         ws = torch.zeros(max(256, vg.workspace_size(p, F)), dtype=torch.uint8, device=dev)
         run = lambda **kw: nd.decode_vertical(vg, p, llr, ws, hard, stream=st_, **kw)
         plan = {"schedule": "vertical", "G": args.vertical, "workspace_bytes": vg.workspace_size(p, F)}
     else:
         sched = "cyclic 2-layer NDGSBP"
+        oracle_run = lambda x: O.ndgsbp_decode(c, q["grp_ptr"], q["cn_idx"], x, IMAX_ND, want_total=False)
+        eu = q["edge_updates_per_iter"]
+        ops_per_iter = {"ex2": eu, "rcp": eu, "lg2": eu}
         ws = torch.zeros(max(256, g.workspace_size(p, F)), dtype=torch.uint8, device=dev)
         run = lambda **kw: nd.decode(g, p, llr, ws, hard, stream=st_, **kw)
         plan = g.plan(p, F).as_dict()
     for _ in range(args.warmup):
         run()
+    clocks = ClockSampler(0)
+    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st_)
     for _ in range(args.steps):
         run(stats=stats)
     e1.record(st_)
     torch.cuda.synchronize()
+    clk = clocks.stop()
     sec = e0.elapsed_time(e1) / 1e3
     s = stats.cpu().numpy()
+    # MUFU roofline: the schedule's operations at the measured per-op rates
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    probe = mufu_peak(nd, torch, dev, sms, clk.get("sm_mhz") or 2070.0)
+    iters_total = float(s[nd.STAT_ITERATIONS])
+    n_ops = {k: v * iters_total for k, v in ops_per_iter.items()}
+    t_mufu = sum(n_ops[k] / (probe[k]["tops"] * 1e12) for k in n_ops)
+    ops = sum(n_ops.values())
+    roof = {"bound": "alu", "achieved": ops / sec / 1e12, "peak": ops / t_mufu / 1e12, "unit": "Top/s",
+            "frac": t_mufu / sec, "traffic": None, "mufu_ops": {k: int(v) for k, v in n_ops.items()},
+            "mufu_probe": probe,
+            "what": "Eq. (1)'s ex2/rcp/lg2 operations of the timed decodes over their CUDA-event time; peak = the "
+                    "rate of this operation mix at the per-op rates measured by ndgsbp_mufu_probe"}
+    # the oracle beside it, on the first frames of the same LLRs; paired frame-error status
+    n_or = min(args.decode_oracle_frames if args.decode_oracle_frames > 0 else (256 if c.N <= 2304 else 64), F)
+    host = llr[:n_or].cpu().numpy().astype(np.float64)
+    t0 = time.perf_counter()
+    ref = oracle_run(host)
+    t_or = time.perf_counter() - t0
+    run()   # the GPU's decisions on all frames (no statistics)
+    torch.cuda.synchronize()
+    bits = nd.unpack_bits(hard[:n_or], c.N)
+    cpu = {"value": n_or * (c.N - c.M) / t_or / 1e9, "unit": "Gbit/s", "cores": host_cores(), "kind": "oracle",
+           "sample": f"the first {n_or} of the {F} frames, same schedule and groups, {t_or:.1f} s",
+           "frames_per_s": n_or / t_or,
+           "frame_error_status_differs": int((bits.any(axis=1) != ref.hard.any(axis=1)).sum()),
+           "oracle_frame_errors": int(ref.hard.any(axis=1).sum())}
     line = {"metric": METRIC, "value": F * args.steps * (c.N - c.M) / sec / 1e9, "unit": "Gbit/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.msg, "data": "synthetic",
             "config": {"workload": f"decode: {args.code} at {eb} dB, {F} frames, {sched}, I_max {IMAX_ND}"},
             "fer": float(s[nd.STAT_FRAME_ERRORS] / max(s[nd.STAT_FRAMES], 1)),
             "mean_iterations": float(s[nd.STAT_ITERATIONS] / max(s[nd.STAT_FRAMES], 1)),
-            "plan": plan, "roofline": None, "e2e": None, "cpu_baseline": None}
+            "plan": plan, "clocks": clk, "gpu_launches": args.steps, "roofline": roof, "e2e": None,
+            "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1300,6 +1346,8 @@ def main():
     ap.add_argument("--ebn0", type=float, default=None, help="decode workload: Eb/N0 (default: the FER~1e-3 point)")
     ap.add_argument("--msg", choices=["f32", "f16", "bf16"], default="f16", help="decode workload: message storage")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="decode workload: residency cap (0 = library choice)")
+    ap.add_argument("--decode-oracle-frames", type=int, default=0,
+                    help="decode workload: frames the oracle decodes beside it (0 = 256 up to n=2304, else 64)")
     ap.add_argument("--vertical", type=int, default=0,
                     help="decode workload: decode with the vertical schedule over this many VN groups (0 = NDGSBP)")
     ap.add_argument("--precision-oracle-frames", type=int, default=65536,
