@@ -9,10 +9,11 @@
 // A frame keeps its channel LLRs L_n and the running totals P_n = L_n + sum of the CN->VN
 // messages into n in shared memory; the VN->CN message of edge (m, n) is P_n - L_{m->n} at any
 // time, because the messages into a VN change only while its own group runs, when P_n is
-// recomputed from them.  Per group: (1) one thread per edge of the group computes Eq. (1) for
-// that edge alone, in the positive-pair tanh-product form of the other kernels, into a
-// staging array; (2) one thread per VN of the group stores its new messages and recomputes
-// P_n.  Two barriers per group.  The CN->VN messages (CSR order) live in shared memory when
+// recomputed from them.  Per group: (1) Eq. (1) in the positive-pair tanh-product form of the
+// other kernels into a staging array, either one thread per group edge (the product over the
+// CN's other edges) or, for groups whose edges reach few CNs, one thread per CN (one
+// prefix/suffix pass, outputs for the CN's group edges); (2) one thread per VN of the group
+// stores its new messages and recomputes P_n.  Two barriers per group.  The CN->VN messages (CSR order) live in shared memory when
 // the frame fits, else in the CTA's workspace slot.
 #include <algorithm>
 #include <cstring>
@@ -42,6 +43,10 @@ struct DeviceVTables {
     const int32_t* grp_vn = nullptr;    // [N]
     const int32_t* vn_epos = nullptr;   // [N+1] group-edge position of grp_vn[i]'s first edge
     const int32_t* row_ptr = nullptr;   // [M+1]
+    const int4* vtask = nullptr;        // per-CN groups: the CNs the group's edges reach, (row start b,
+                                        // degree d, mask of their group edges' row positions, output base)
+    const int32_t* gtask_ptr = nullptr; // [G+1] into vtask (an empty range: a per-edge group)
+    const int32_t* vtout = nullptr;     // staging positions of each task's group edges, by row position
 };
 
 }  // namespace ndgsbp
@@ -52,7 +57,10 @@ struct ndgsbp_vgroups {
     std::vector<int32_t> grp_ptr, grp_vn;    // a partition of the N VNs
     std::vector<int4> gtab;                  // [E] group edges, VN-major within each group
     std::vector<int32_t> vn_epos;            // [N+1]
-    int max_group_edges = 0, max_group_vns = 0;
+    std::vector<int4> vtask;                 // CN tasks of every group (see DeviceVTables)
+    std::vector<int32_t> gtask_ptr, vtout;
+    int max_group_edges = 0, max_group_vns = 0, max_group_work = 0;
+    bool per_cn = false;                     // every group takes the per-CN form
     mutable std::mutex mu;
     mutable std::map<int, ndgsbp::DeviceVTables> dev;
     ~ndgsbp_vgroups();
@@ -103,6 +111,58 @@ static ndgsbp_status finish_vgroups(const std::shared_ptr<const Code>& code, std
         h->max_group_vns = std::max(h->max_group_vns, gp[g + 1] - gp[g]);
     }
     h->vn_epos[c.N] = static_cast<int32_t>(h->gtab.size());
+    // Phase 1 runs either one thread per group edge (the product over the CN's other edges
+    // directly) or one thread per CN the group reaches (one prefix/suffix pass over the CN, outputs
+    // at the group's row positions).  A barrier ends the phase, so its time is that of the slowest
+    // thread: the per-CN form is taken when in every group the edges average >= 4 per CN they
+    // reach (e.g. one group of all VNs), the per-edge form otherwise, for the whole decode
+    // (measured on n=2304, 10 iterations of 65,536 frames: one group, 6.6 edges per CN, per-CN
+    // 34.5 against 59.2 ms; 4 groups, 1.9 edges per CN, 73.7 against 62.1 ms; mixing the two
+    // forms in one phase, or keeping the per-CN code in the per-edge kernel, ran 12-70 % slower
+    // than the plain per-edge kernel).
+    h->gtask_ptr.assign(1, 0);
+    h->vtout.assign(c.E, 0);
+    std::vector<int32_t> task_of(c.M, -1);
+    size_t obase = 0;
+    for (int g = 0; g < G; ++g) {
+        const size_t q0 = static_cast<size_t>(h->vn_epos[gp[g]]), q1 = static_cast<size_t>(h->vn_epos[gp[g + 1]]);
+        std::vector<std::vector<std::pair<int, int>>> outs;   // per CN: (row position k, staging position)
+        std::vector<int32_t> touched;
+        for (size_t q = q0; q < q1; ++q) {
+            const int4 ge = h->gtab[q];
+            const int m = edge_row[ge.x];
+            if (task_of[m] < 0) {
+                task_of[m] = static_cast<int32_t>(outs.size());
+                touched.push_back(m);
+                outs.emplace_back();
+            }
+            outs[task_of[m]].push_back({ge.w, static_cast<int>(q - q0)});
+        }
+        for (int32_t m : touched) task_of[m] = -1;
+        const size_t edges = q1 - q0;
+        const bool dense = c.max_row <= 32 && edges >= 4 * touched.size();
+        if (g == 0) h->per_cn = dense;
+        h->per_cn = h->per_cn && dense;
+        if (c.max_row <= 32) {   // the per-CN tasks (row-position masks need degrees <= 32)
+            for (size_t i = 0; i < touched.size(); ++i) {
+                const int m = touched[i], b = c.row_ptr[m], d = c.row_ptr[m + 1] - b;
+                auto& o = outs[i];
+                std::sort(o.begin(), o.end());
+                uint32_t mask = 0u;
+                for (const auto& kv : o) {
+                    mask |= 1u << kv.first;
+                    h->vtout[obase++] = kv.second;
+                }
+                h->vtask.push_back(make_int4(b, d, static_cast<int>(mask), static_cast<int>(obase - o.size())));
+            }
+        }
+        h->gtask_ptr.push_back(static_cast<int32_t>(h->vtask.size()));
+    }
+    // threads: the most work items of a group phase in the chosen form
+    for (int g = 0; g < G; ++g) {
+        const int items = h->per_cn ? h->gtask_ptr[g + 1] - h->gtask_ptr[g] : h->vn_epos[gp[g + 1]] - h->vn_epos[gp[g]];
+        h->max_group_work = std::max({h->max_group_work, items, gp[g + 1] - gp[g]});
+    }
     h->grp_ptr = std::move(gp);
     h->grp_vn = std::move(gv);
     *out = h;
@@ -123,7 +183,8 @@ static ndgsbp_status vgroups_device(const ndgsbp_vgroups* h, const DeviceVTables
     auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
     const size_t o_col = 0, o_gtab = al(o_col + 4 * c.E), o_gp = al(o_gtab + 16 * c.E),
                  o_gv = al(o_gp + 4 * (h->G + 1)), o_ep = al(o_gv + 4 * c.N), o_rp = al(o_ep + 4 * (c.N + 1)),
-                 total = al(o_rp + 4 * (c.M + 1));
+                 o_vt = al(o_rp + 4 * (c.M + 1)), o_tp = al(o_vt + 16 * h->vtask.size()),
+                 o_vo = al(o_tp + 4 * h->gtask_ptr.size()), total = al(o_vo + 4 * h->vtout.size());
     std::vector<unsigned char> host(total, 0);
     std::memcpy(host.data() + o_col, c.col_idx.data(), 4 * c.E);
     std::memcpy(host.data() + o_gtab, h->gtab.data(), 16 * c.E);
@@ -131,6 +192,9 @@ static ndgsbp_status vgroups_device(const ndgsbp_vgroups* h, const DeviceVTables
     std::memcpy(host.data() + o_gv, h->grp_vn.data(), 4 * c.N);
     std::memcpy(host.data() + o_ep, h->vn_epos.data(), 4 * (c.N + 1));
     std::memcpy(host.data() + o_rp, c.row_ptr.data(), 4 * (c.M + 1));
+    std::memcpy(host.data() + o_vt, h->vtask.data(), 16 * h->vtask.size());
+    std::memcpy(host.data() + o_tp, h->gtask_ptr.data(), 4 * h->gtask_ptr.size());
+    std::memcpy(host.data() + o_vo, h->vtout.data(), 4 * h->vtout.size());
     void* d = nullptr;
     VCUDA_TRY(cudaMalloc(&d, total));
     cudaError_t e = cudaMemcpy(d, host.data(), total, cudaMemcpyHostToDevice);
@@ -147,6 +211,9 @@ static ndgsbp_status vgroups_device(const ndgsbp_vgroups* h, const DeviceVTables
     t.grp_vn = reinterpret_cast<const int32_t*>(b + o_gv);
     t.vn_epos = reinterpret_cast<const int32_t*>(b + o_ep);
     t.row_ptr = reinterpret_cast<const int32_t*>(b + o_rp);
+    t.vtask = reinterpret_cast<const int4*>(b + o_vt);
+    t.gtask_ptr = reinterpret_cast<const int32_t*>(b + o_tp);
+    t.vtout = reinterpret_cast<const int32_t*>(b + o_vo);
     out = &(h->dev[dev] = t);
     return NDGSBP_OK;
 }
@@ -163,11 +230,8 @@ struct VArgs {
     int msg_bytes;       // E messages rounded up to 16 bytes
 };
 
-// Eq. (1) for one edge: the CN->VN message of edge k of a CN whose other edges carry the VN->CN
-// messages v_j (log2 units), as a product of (N, E) pairs (tanh(x/2) = N / (N + E), u = e^-x,
-// (N, E) = ((1 - u) / 2, u); pairs combine as (Na Nb, Ea (Eb + Nb) + Na Eb)) and
-// 2 atanh(N / (N + E)) = ln(1 + 2 N / E).  Inputs and the output are clipped to lim.  A CN of
-// degree 1 gives +lim (the empty product is 1).
+// Eq. (1) for one group edge (row position k) of a CN of degree d: the product over the CN's
+// other edges directly, in the same (N, E) pair form.  A CN of degree 1 gives +lim.
 template <typename MsgT>
 __device__ __forceinline__ float vertical_edge_message(const float* __restrict__ P, const MsgT* msg,
                                                        const int32_t* __restrict__ col_idx, int b, int d, int k,
@@ -187,7 +251,57 @@ __device__ __forceinline__ float vertical_edge_message(const float* __restrict__
     return __uint_as_float(__float_as_uint(mag) | (par & 0x80000000u));
 }
 
-template <typename MsgT>
+// Eq. (1) for one CN of degree d <= MAXDC (row start b): the VN->CN messages of its edges
+// (P_n - L_{m->n}, log2 units) as a product of (N, E) pairs (tanh(x/2) = N / (N + E), u = e^-x,
+// (N, E) = ((1 - u) / 2, u); pairs combine as (Na Nb, Ea (Eb + Nb) + Na Eb)), "all edges but k" =
+// prefix(k) x suffix(k + 1), and 2 atanh(N / (N + E)) = ln(1 + 2 N / E); inputs and outputs
+// clipped to lim.  Only the row positions in mask (the group's edges) get an output: written to
+// stage[out[i]], the i-th set bit of mask counted from position 0.  A CN of degree 1 gives +lim
+// (the empty product is 1).
+template <int MAXDC, typename MsgT>
+__device__ __forceinline__ void vertical_cn_task(const float* __restrict__ P, const MsgT* msg,
+                                                 const int32_t* __restrict__ col_idx, int b, int d, unsigned mask,
+                                                 const int32_t* __restrict__ out, float* stage, float lim) {
+    float xs[MAXDC], pn[MAXDC], pe[MAXDC];
+    unsigned par = 0u;
+    float cn = 1.f, ce = 0.f;
+#pragma unroll
+    for (int k = 0; k < MAXDC; ++k) {
+        if (k < d) {
+            const float v = P[__ldg(col_idx + b + k)] - to_f(msg[b + k]);   // L_{n->m} = P_n - L_{m->n}
+            const unsigned tb = __float_as_uint(v);
+            par ^= tb;
+            const float u = ex2_approx(-fminf(fabsf(v), lim));
+            xs[k] = __uint_as_float(__float_as_uint(u) | (tb & 0x80000000u));
+            pn[k] = cn;
+            pe[k] = ce;
+            ce = fmaf(ce, fmaf(0.5f, u, 0.5f), cn * u);
+            cn = cn * fmaf(-0.5f, u, 0.5f);
+        }
+    }
+    const unsigned pm = par & 0x80000000u;
+    int o = __popc(mask) - 1;   // outputs in decreasing row position
+    float sn = 1.f, se = 0.f;
+#pragma unroll
+    for (int k = MAXDC - 1; k >= 0; --k) {
+        if (k < d) {
+            const float u = fabsf(xs[k]);
+            const float ss = sn + se;
+            if ((mask >> k) & 1u) {
+                const float en = pn[k] * sn;
+                const float ee = fmaf(pe[k], ss, pn[k] * se);
+                const float w = fmaf(en * rcp_approx(ee), 2.f, 1.f);
+                const float mag = fminf(lg2_approx(w), lim);
+                stage[__ldg(out + o)] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(xs[k]) ^ pm) & 0x80000000u));
+                --o;
+            }
+            se = fmaf(u, ss, se * fmaf(-0.5f, u, 0.5f));
+            sn = sn * fmaf(-0.5f, u, 0.5f);
+        }
+    }
+}
+
+template <typename MsgT, int MAXDC, bool PCN>
 __global__ void __launch_bounds__(512) vertical_decode_kernel(const VArgs a) {
     extern __shared__ __align__(16) unsigned char vsm[];
     __shared__ long long s_frame;
@@ -214,11 +328,22 @@ __global__ void __launch_bounds__(512) vertical_decode_kernel(const VArgs a) {
         for (; !invalid; ++it) {
             for (int g = 0; g < a.G; ++g) {
                 const int v0 = __ldg(t.grp_ptr + g), v1 = __ldg(t.grp_ptr + g + 1);
-                const int a0 = __ldg(t.vn_epos + v0), a1 = __ldg(t.vn_epos + v1);
-                // Eq. (1) into every edge of the group's VNs, from the messages at the group's start
-                for (int q = a0 + tid; q < a1; q += nt) {
-                    const int4 ge = __ldg(t.gtab + q);
-                    stage[q - a0] = vertical_edge_message(P, msg, t.col_idx, ge.y, ge.z, ge.w, lim);
+                const int a0 = __ldg(t.vn_epos + v0);
+                // Eq. (1) into every edge of the group's VNs, from the messages at the group's
+                // start: one pass per CN the group reaches, or one thread per group edge
+                if constexpr (PCN) {
+                    const int t1 = __ldg(t.gtask_ptr + g + 1);
+                    for (int i = __ldg(t.gtask_ptr + g) + tid; i < t1; i += nt) {
+                        const int4 tk = __ldg(t.vtask + i);
+                        vertical_cn_task<MAXDC>(P, msg, t.col_idx, tk.x, tk.y, static_cast<unsigned>(tk.z),
+                                                t.vtout + tk.w, stage, lim);
+                    }
+                } else {
+                    const int a1 = __ldg(t.vn_epos + v1);
+                    for (int q = a0 + tid; q < a1; q += nt) {
+                        const int4 ge = __ldg(t.gtab + q);
+                        stage[q - a0] = vertical_edge_message(P, msg, t.col_idx, ge.y, ge.z, ge.w, lim);
+                    }
                 }
                 __syncthreads();
                 // Eq. (2): store the group's messages; P_n = L_n + their sum
@@ -254,11 +379,20 @@ __global__ void __launch_bounds__(512) vertical_decode_kernel(const VArgs a) {
 
 typedef void (*VKernelFn)(const VArgs);
 
-static VKernelFn pick_vertical_kernel(int msg_dtype) {
+template <typename MsgT>
+static VKernelFn pick_vertical_degree(int maxdc, bool per_cn) {
+    if (!per_cn) return vertical_decode_kernel<MsgT, 8, false>;   // the degree bound is not used
+    if (maxdc <= 8) return vertical_decode_kernel<MsgT, 8, true>;
+    if (maxdc <= 16) return vertical_decode_kernel<MsgT, 16, true>;
+    if (maxdc <= 32) return vertical_decode_kernel<MsgT, 32, true>;
+    return nullptr;
+}
+
+static VKernelFn pick_vertical_kernel(int msg_dtype, int maxdc, bool per_cn) {
     switch (msg_dtype) {
-        case NDGSBP_F16: return vertical_decode_kernel<__half>;
-        case NDGSBP_BF16: return vertical_decode_kernel<__nv_bfloat16>;
-        default: return vertical_decode_kernel<float>;
+        case NDGSBP_F16: return pick_vertical_degree<__half>(maxdc, per_cn);
+        case NDGSBP_BF16: return pick_vertical_degree<__nv_bfloat16>(maxdc, per_cn);
+        default: return pick_vertical_degree<float>(maxdc, per_cn);
     }
 }
 
@@ -308,14 +442,14 @@ static ndgsbp_status make_vplan(const ndgsbp_vgroups* h, const ndgsbp_params* p,
     if (k == k1)
         return fail(NDGSBP_ERR_UNSUPPORTED, "vertical: %d VNs and %lld edges do not fit in %d bytes of shared memory%s",
                     c.N, static_cast<long long>(c.E), optin, p->variant == NDGSBP_VARIANT_SMEM ? " (variant SMEM)" : "");
-    vp.fn = pick_vertical_kernel(p->msg_dtype);
+    vp.fn = pick_vertical_kernel(p->msg_dtype, c.max_row, h->per_cn);
     vp.msg_smem = opts[k][0];
     vp.stage_smem = opts[k][1];
     vp.msg_bytes = static_cast<int>(mb);
     vp.smem = base + (vp.msg_smem ? mb : 0) + (vp.stage_smem ? sb : 0);
     vp.slot_bytes = ((vp.msg_smem ? 0 : mb) + (vp.stage_smem ? 0 : sb) + 255) & ~static_cast<size_t>(255);
-    vp.threads = p->block_threads ? p->block_threads
-                                  : std::min(512, std::max(64, (h->max_group_edges + 31) / 32 * 32));
+    const int work = h->max_group_work;
+    vp.threads = p->block_threads ? p->block_threads : std::min(512, std::max(64, (work + 31) / 32 * 32));
     const void* fn = reinterpret_cast<const void*>(vp.fn);
     VCUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(vp.smem)));
     VCUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vp.per_sm, fn, vp.threads, vp.smem));
