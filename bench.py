@@ -1236,6 +1236,89 @@ def run_decode(args):
     return 0
 
 
+GA_ENSEMBLES = [("(3,6)", {3: 1.0}, {6: 1.0}, 0.5, 1.163), ("(4,6)", {4: 1.0}, {6: 1.0}, 1 / 3, 1.730)]
+GA_SCHEDULES = [("flooding", 1, 0.0), ("GSBP", 4, 0.0), ("NDGSBP", 4, 0.4)]
+
+
+def run_ga(args):
+    """The Gaussian-approximation analysis of Sec. III in FP64 on the GPU beside the oracle's
+    (oracle/ga.py), closed-form Phi (the form that reproduces Table I): per ensemble and schedule,
+    the threshold by bisection (tolerance 1e-4 dB) and the iterations to error-free decoding at
+    the printed flooding threshold; and a batch of 1,024 Eb/N0 points (0.5-3 dB) decoded by the
+    recursion in one launch per schedule, timed against the oracle on 32 of those points."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from oracle import ga
+    from paper_1202_1060_gb300 import ndgsbp as nd
+    pk = nd.GA_PHI_CLOSED
+
+    def gpu_run(lam, rho, R, G, r, snr):
+        if G == 1:
+            return nd.ga_flood(lam, rho, R, snr, phi_kind=pk)
+        return nd.ga_groups(lam, rho, R, G, r, snr, phi_kind=pk)
+
+    def gpu_threshold(lam, rho, R, G, r):
+        if G == 1:
+            return nd.ga_flood_threshold(lam, rho, R, phi_kind=pk, lo_db=0.5, hi_db=3.0, tol_db=1e-4)
+        return nd.ga_groups_threshold(lam, rho, R, G, r, phi_kind=pk, lo_db=0.5, hi_db=3.0, tol_db=1e-4)
+
+    def oracle_run(lam, rho, R, G, r, e):
+        if G == 1:
+            return ga.flood_ga(e, lam, rho, R, kind="approx")
+        return ga.group_ga(e, lam, rho, R, G, r, kind="approx")
+
+    rows = []
+    snr = np.linspace(0.5, 3.0, 1024)
+    sample = snr[::32]
+    gpu_points_s, or_points_s, agree, total = 0.0, 0.0, 0, 0
+    for name, lam, rho, R, printed in GA_ENSEMBLES:
+        for sched, G, r in GA_SCHEDULES:
+            t0 = time.perf_counter()
+            th_gpu = gpu_threshold(lam, rho, R, G, r)
+            t_th_gpu = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            th_or = ga.threshold(lambda e: oracle_run(lam, rho, R, G, r, e), lo=0.5, hi=3.0, tol=1e-4)
+            t_th_or = time.perf_counter() - t0
+            _, it_gpu, _ = gpu_run(lam, rho, R, G, r, np.array([printed + 0.05]))
+            _, it_or, _ = oracle_run(lam, rho, R, G, r, printed + 0.05)
+            gpu_run(lam, rho, R, G, r, snr)   # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cv, it, _ = gpu_run(lam, rho, R, G, r, snr)
+            t_b_gpu = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            ref = [oracle_run(lam, rho, R, G, r, float(e)) for e in sample]
+            t_b_or = time.perf_counter() - t0
+            same = sum(int(bool(cv[32 * k]) == bool(ref[k][0])) for k in range(len(sample)))
+            agree += same
+            total += len(sample)
+            gpu_points_s += len(snr) / t_b_gpu
+            or_points_s += len(sample) / t_b_or
+            rows.append({"ensemble": name, "schedule": sched, "G": G, "r": r,
+                         "threshold_db": {"gpu": th_gpu, "oracle": th_or, "table_I_flooding": printed},
+                         "threshold_seconds": {"gpu": t_th_gpu, "oracle": t_th_or},
+                         "iterations_at_threshold_plus_0.05dB": {"gpu": int(it_gpu[0]), "oracle": int(it_or)},
+                         "batch": {"points": len(snr), "gpu_seconds": t_b_gpu, "gpu_points_per_s": len(snr) / t_b_gpu,
+                                   "oracle_points": len(sample), "oracle_seconds": t_b_or,
+                                   "oracle_points_per_s": len(sample) / t_b_or,
+                                   "convergence_agrees_on_oracle_points": f"{same}/{len(sample)}"}})
+    n = len(rows)
+    line = {"metric": "GA recursion Eb/N0 points per second (FP64)", "value": gpu_points_s / n,
+            "unit": "points/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "GA analysis (Sec. III, Eqs. (4)-(17)): (3,6) and (4,6) ensembles; flooding, GSBP "
+                                   "(4 groups), NDGSBP (4 groups, r = 0.4); closed-form Phi; 1,024 Eb/N0 points"},
+            "rows": rows, "convergence_agreement": f"{agree}/{total}",
+            "roofline": None, "e2e": None,
+            "cpu_baseline": {"value": or_points_s / n, "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": "32 of the 1,024 points per ensemble and schedule, oracle/ga.py on one core"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_c1(args):
     """The Gallager (3,6) n=1008 workload: 500 frames at Eb/N0 1.5 dB, FP64 channel LLRs, flooding,
     disjoint GSBP (4 groups) and NDGSBP (4 groups, r = 0.4) at I_max 50, and NDGSBP at the equal
@@ -1338,7 +1421,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the flooding and precision extras")
     ap.add_argument("--extras-frames", type=int, default=65536, help="frames per code and dtype, precision extra")
-    ap.add_argument("--workload", choices=["sweep", "ragged", "serving", "precision", "c1", "decode"],
+    ap.add_argument("--workload", choices=["sweep", "ragged", "serving", "precision", "c1", "decode", "ga"],
                     default="sweep",
                     help="sweep = the default n=2304 Eb/N0 sweep line; the others are supplementary")
     ap.add_argument("--precision-frames", type=int, default=262144)
@@ -1366,7 +1449,7 @@ def main():
         return run_reference(args)
     if args.workload != "sweep":
         return {"ragged": run_ragged, "serving": run_serving, "precision": run_precision,
-                "c1": run_c1, "decode": run_decode}[args.workload](args)
+                "c1": run_c1, "decode": run_decode, "ga": run_ga}[args.workload](args)
     return run_ours(args)
 
 

@@ -519,8 +519,8 @@ ndgsbp_status ndgsbp_ga_flood(const double* lambda, int32_t dv_max, const double
                               int32_t max_iter, double mu_cap, uint8_t* converged, int32_t* iters,
                               double* mu_c);
 /* GA threshold: the smallest Eb/N0 in [lo_db, hi_db] at which ndgsbp_ga_flood converges, found
- * by refining the bracketing pair of a 64-point grid until it is narrower than tol_db; the upper
- * end of the final pair is returned.  Errors: INVALID, INFEASIBLE (no convergence at hi_db), CUDA. */
+ * by refining the bracketing pair of a grid of at most 64 points (no finer than tol_db where that
+ * takes fewer) until it is narrower than tol_db; the upper end of the final pair is returned.  Errors: INVALID, INFEASIBLE (no convergence at hi_db), CUDA. */
 ndgsbp_status ndgsbp_ga_flood_threshold(const double* lambda, int32_t dv_max, const double* rho,
                                         int32_t dc_max, double rate, int32_t phi_kind,
                                         int32_t max_iter, double mu_cap, double lo_db, double hi_db,

@@ -18,7 +18,8 @@
 // and integrated by the trapezoidal rule in x (T = mu + 2 sqrt(mu) x, weight e^{-x^2} / sqrt(pi))
 // over [-12, 12] with step 1/32, the 769 nodes split over the warp's lanes; the rule converges
 // geometrically for this analytic integrand.  Alternatively the closed form of the GA analysis
-// the paper cites.  Phi^-1 is bisection on [0, 200].
+// the paper cites.  Phi^-1 is bisection on [0, 200]; for the closed form, whose one evaluation
+// needs no warp, the lanes evaluate the next five levels' midpoints at once.
 #include <cmath>
 #include <vector>
 
@@ -31,6 +32,8 @@ constexpr int kGaNodes = 769;            // x = -12 + k / 32, k = 0..768
 constexpr double kGaStep = 1.0 / 32.0;
 constexpr int kGaMaxDeg = 64;
 constexpr int kGaMaxGroups = 64;
+constexpr int kGaWarps = 1;              // one point per block: a point's serial FP64 chain gets an SM's FP64 pipe
+constexpr int kGaWTab = 512;             // class-b weights of Eq. (9) cached per warp (shared memory)
 
 struct GaArgs {
     double lam[kGaMaxDeg + 1];
@@ -74,10 +77,93 @@ __device__ double ga_phi(double mu, int kind, int lane) {
     return warp_sum(acc) * kGaStep * 0.56418958354775628;   // 1 / sqrt(pi)
 }
 
-__device__ double ga_phi_inv(double p, int kind, int lane) {
-    if (p >= 1.0 && kind != NDGSBP_GA_PHI_CLOSED) return 0.0;
+// Bisection for the closed form, five levels per step, from the bracket (lo, hi) reached after
+// `steps` halvings of [0, 200]: lane j - 1 evaluates node j (1..31, heap order: children 2j below
+// the midpoint, 2j + 1 above) of the next five levels' tree, its bracket rebuilt from (lo, hi) by
+// the same halvings; the ballot then replays the five decisions one by one with the stop test
+// after each, so every midpoint, decision and the result are those of the one-level loop of
+// ga_phi_inv.
+__device__ double ga_bisect_closed(double p, double lo, double hi, int steps, int lane) {
+    const int j = lane + 1;
+    const int depth = 31 - __clz(j);
+    while (steps < 200) {
+        double l = lo, h = hi;
+        for (int b = depth - 1; b >= 0; --b) {
+            const double m = 0.5 * (l + h);
+            if ((j >> b) & 1)
+                l = m;
+            else
+                h = m;
+        }
+        const bool above = lane < 31 && ga_phi(0.5 * (l + h), NDGSBP_GA_PHI_CLOSED, lane) > p;
+        const unsigned ball = __ballot_sync(0xffffffffu, above);
+        int node = 1;
+        for (int lev = 0; lev < 5 && steps < 200; ++lev, ++steps) {
+            const double m = 0.5 * (lo + hi);
+            if ((ball >> (node - 1)) & 1u) {
+                lo = m;
+                node = 2 * node + 1;
+            } else {
+                hi = m;
+                node = 2 * node;
+            }
+            if (hi - lo <= 1e-13 * fmax(1.0, hi)) return 0.5 * (lo + hi);
+        }
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Phi^-1 of the closed form, with the result of the one-level bisection.  Each piece of the closed
+// form decreases, and the jump at mu = 10 goes up (from Phi(10-) = 0.03847 to Phi(10) = 0.03944):
+// outside that band of p and below Phi(0+) = e^0.0218 there is one root r, in closed form on
+// (0, 10) and by Newton's method on the logarithm above.  Every bisection midpoint farther than
+// delta = 4e-14 max(1, r) from r is decided by its side of r (there Phi moves by over ten times
+// its rounding error), and the midpoints of the levels above a bracket are that bracket's ends;
+// so the bisection starts from the bracket five levels above the last one (the level at which
+// the width first meets the stop test), when both its ends are that far from r, and runs from
+// [0, 200] otherwise (the band, p near Phi(0+), or an end within delta).
+__device__ double ga_phi_inv_closed(double p, double phi_top, int lane) {
+    if (phi_top >= p) return 200.0;
+    const double p_left = exp(-0.4527 * pow(10.0, 0.86) + 0.0218);
+    const double p_right = sqrt(M_PI / 10.0) * exp(-10.0 / 4.0) * (1.0 - 10.0 / 70.0);
+    const bool left = p > p_right * (1.0 + 1e-9) && p < exp(0.0218) * (1.0 - 1e-9);
+    if (!left && !(p < p_left * (1.0 - 1e-9))) return ga_bisect_closed(p, 0.0, 200.0, 0, lane);
+    const double lp = log(p);
+    double r;
+    if (left) {
+        r = pow((0.0218 - lp) / 0.4527, 1.0 / 0.86);
+    } else {
+        r = fmin(200.0, fmax(10.0, -4.0 * lp));
+        for (int it = 0; it < 6; ++it) {
+            const double g = log(sqrt(M_PI / r) * (1.0 - 10.0 / (7.0 * r))) - r / 4.0 - lp;
+            const double dg = -0.5 / r - 0.25 + (10.0 / (7.0 * r * r)) / (1.0 - 10.0 / (7.0 * r));
+            r = fmin(200.0, fmax(10.0, r - g / dg));
+        }
+    }
+    // the first level whose bracket around r meets the stop test (two to four levels below k)
+    int k = (int)ceil(log2(200.0 / (1e-13 * fmax(1.0, r)))) - 2;
+    bool found = false;
+    for (int t = 0; t < 8 && !found; ++t, ++k) {
+        const double w = ldexp(200.0, -k);
+        const double lo = w * floor(r / w);
+        found = w <= 1e-13 * fmax(1.0, lo + w);
+    }
+    if (!found) return ga_bisect_closed(p, 0.0, 200.0, 0, lane);
+    k -= 6;   // the loop stepped once past the level found
+    const double w = ldexp(200.0, -k);
+    const double lo = w * floor(r / w), hi = lo + w;
+    const double delta = 4e-14 * fmax(1.0, r);
+    if (lo <= r && r < hi && (lo == 0.0 || r - lo > delta) && (hi == 200.0 || hi - r > delta))
+        return ga_bisect_closed(p, lo, hi, k, lane);
+    return ga_bisect_closed(p, 0.0, 200.0, 0, lane);
+}
+
+// phi_top = Phi(200), the upper end of the search (the same in every call of a kernel).
+__device__ double ga_phi_inv(double p, double phi_top, int kind, int lane) {
+    if (kind == NDGSBP_GA_PHI_CLOSED) return ga_phi_inv_closed(p, phi_top, lane);
+    if (p >= 1.0) return 0.0;
     double lo = 0.0, hi = 200.0;
-    if (ga_phi(hi, kind, lane) >= p) return hi;
+    if (phi_top >= p) return hi;
     for (int it = 0; it < 200; ++it) {
         const double mid = 0.5 * (lo + hi);
         if (ga_phi(mid, kind, lane) > p)
@@ -90,13 +176,13 @@ __device__ double ga_phi_inv(double p, int kind, int lane) {
 }
 
 // Eqs. (15)-(16): the CN mean from the VN means mu_v[i], i = 2 .. dv_max.
-__device__ double ga_cn_mean(const GaArgs& a, const double* mu_v, int lane) {
+__device__ double ga_cn_mean(const GaArgs& a, const double* mu_v, double phi_top, int lane) {
     double s = 0.0;
     for (int i = 2; i <= a.dv_max; ++i)
         if (a.lam[i] > 0.0) s += a.lam[i] * ga_phi(mu_v[i], a.kind, lane);
     double next = 0.0;
     for (int j = 2; j <= a.dc_max; ++j)
-        if (a.rho[j] > 0.0) next += a.rho[j] * ga_phi_inv(1.0 - pow(1.0 - s, j - 1), a.kind, lane);
+        if (a.rho[j] > 0.0) next += a.rho[j] * ga_phi_inv(1.0 - pow(1.0 - s, j - 1), phi_top, a.kind, lane);
     return next;
 }
 
@@ -122,12 +208,13 @@ __global__ void ga_flood_kernel(const GaArgs a) {
     const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (k >= a.n) return;   // whole warps leave together
     const double mu0 = ga_mu0(a, k);
+    const double phi_top = ga_phi(200.0, a.kind, lane);
     double mu_c = 0.0, mu_v[kGaMaxDeg + 1];
     int it = 1;
     unsigned char conv = 0;
     for (; it <= a.max_iter; ++it) {
         for (int i = 2; i <= a.dv_max; ++i) mu_v[i] = mu0 + (i - 1) * mu_c;
-        if (ga_step(a, ga_cn_mean(a, mu_v, lane), mu_c, conv)) break;
+        if (ga_step(a, ga_cn_mean(a, mu_v, phi_top, lane), mu_c, conv)) break;
     }
     if (lane == 0) {
         a.conv[k] = conv;
@@ -141,10 +228,39 @@ __global__ void ga_group_kernel(const GaArgs a) {
     const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (k >= a.n) return;   // whole warps leave together
     const double mu0 = ga_mu0(a, k);
+    const double phi_top = ga_phi(200.0, a.kind, lane);
     const int G = a.G;
     const double r = a.r;
     const double D = G - (G - 1) * r;   // N_G / M of the size relation G N_G - (G - 1) N_G r = M
     const double x = 1.0 / D, z = r / D;
+    // The weights of Eq. (9) restricted to p >= 1 depend on g, i, p and q only: when they fit,
+    // the lanes compute them once (term t by lane t mod 32) into a table read by every iteration.
+    __shared__ double wtab[kGaWarps][kGaWTab];
+    double* wt = wtab[threadIdx.x >> 5];
+    int terms = 0;   // terms per group: sum over the VN degrees i of (i - 1) i / 2
+    for (int i = 2; i <= a.dv_max; ++i)
+        if (a.lam[i] > 0.0) terms += (i - 1) * i / 2;
+    const bool tab = r > 0.0 && G > 1 && (G - 1) * terms <= kGaWTab;
+    if (tab) {
+        int t = 0;
+        for (int g = 2; g <= G; ++g) {
+            const double fd = g * (1.0 - r) / D, fb = z, fa = fmax(0.0, 1.0 - fd - fb);
+            for (int i = 2; i <= a.dv_max; ++i) {
+                if (!(a.lam[i] > 0.0)) continue;
+                const int n = i - 1;
+                double cnp = 1.0;
+                for (int pp = 1; pp <= n; ++pp) {
+                    cnp = cnp * (n - pp + 1) / pp;
+                    double cq = 1.0;
+                    for (int q = 0; q <= n - pp; ++q, ++t) {
+                        if (q > 0) cq = cq * (n - pp - q + 1) / q;
+                        if ((t & 31) == lane) wt[t] = cnp * cq * pow(fd, pp) * pow(fb, q) * pow(fa, n - pp - q);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
     // cc[g] / cb[g]: class-c and class-b outputs of group g in this iteration; prev: last iteration's cc
     double cc[kGaMaxGroups + 1], cb[kGaMaxGroups + 1], prev[kGaMaxGroups + 1], mu_v[kGaMaxDeg + 1];
     for (int g = 0; g <= G; ++g) prev[g] = 0.0;
@@ -175,9 +291,10 @@ __global__ void ga_group_kernel(const GaArgs a) {
             // Eq. (8) with the weights of Eq. (9): linear in (p, q)
             const double other = fd * mu_d + fb * mu_b + fa * mu_c;
             for (int i = 2; i <= a.dv_max; ++i) mu_v[i] = mu0 + (i - 1) * other;
-            cc[g] = ga_cn_mean(a, mu_v, lane);
+            cc[g] = ga_cn_mean(a, mu_v, phi_top, lane);
             if (g > 1 && r > 0.0) {
                 // class-b CN: at least one class-d neighbour among the other i - 1 (p >= 1)
+                int t = (g - 2) * terms;
                 for (int i = 2; i <= a.dv_max; ++i) {
                     if (!(a.lam[i] > 0.0)) continue;
                     const int n = i - 1;
@@ -187,14 +304,15 @@ __global__ void ga_group_kernel(const GaArgs a) {
                         double cq = 1.0;                        // C(n - p, q)
                         for (int q = 0; q <= n - pp; ++q) {
                             if (q > 0) cq = cq * (n - pp - q + 1) / q;
-                            const double w = cnp * cq * pow(fd, pp) * pow(fb, q) * pow(fa, n - pp - q);
+                            const double w =
+                                tab ? wt[t++] : cnp * cq * pow(fd, pp) * pow(fb, q) * pow(fa, n - pp - q);
                             tot += w;
                             acc += w * (mu0 + pp * mu_d + q * mu_b + (n - pp - q) * mu_c);
                         }
                     }
                     if (tot > 0.0) mu_v[i] = acc / tot;
                 }
-                cb[g] = ga_cn_mean(a, mu_v, lane);
+                cb[g] = ga_cn_mean(a, mu_v, phi_top, lane);
             } else {
                 cb[g] = cc[g];
             }
@@ -254,7 +372,6 @@ static ndgsbp_status ga_run(GaArgs a, bool groups, const double* ebn0_db, int32_
     double* d_mu = nullptr;
     int* d_it = nullptr;
     unsigned char* d_cv = nullptr;
-    constexpr int warps = 4;
     GA_TRY(cudaMalloc(&d_e, sizeof(double) * n_points));
     GA_TRY(cudaMalloc(&d_mu, sizeof(double) * n_points));
     GA_TRY(cudaMalloc(&d_it, sizeof(int) * n_points));
@@ -265,9 +382,9 @@ static ndgsbp_status ga_run(GaArgs a, bool groups, const double* ebn0_db, int32_
     a.iters = d_it;
     a.mu = d_mu;
     if (groups)
-        ga_group_kernel<<<(n_points + warps - 1) / warps, 32 * warps>>>(a);
+        ga_group_kernel<<<(n_points + kGaWarps - 1) / kGaWarps, 32 * kGaWarps>>>(a);
     else
-        ga_flood_kernel<<<(n_points + warps - 1) / warps, 32 * warps>>>(a);
+        ga_flood_kernel<<<(n_points + kGaWarps - 1) / kGaWarps, 32 * kGaWarps>>>(a);
     GA_TRY(cudaGetLastError());
     GA_TRY(cudaMemcpy(converged, d_cv, n_points, cudaMemcpyDeviceToHost));
     GA_TRY(cudaMemcpy(iters, d_it, sizeof(int) * n_points, cudaMemcpyDeviceToHost));
@@ -281,15 +398,20 @@ done:
 }
 
 // The smallest Eb/N0 in [lo, hi] at which the recursion converges: the recursion converges at
-// every Eb/N0 above the threshold, so the bracketing pair of a 64-point grid is refined until it
-// is narrower than tol; the upper end of the final pair is returned.
+// every Eb/N0 above the threshold, so the bracketing pair of a grid of at most 64 points is
+// refined until it is narrower than tol; the upper end of the final pair is returned.  A grid no
+// finer than tol is used where one suffices: points closer to the threshold than that only cost
+// iterations (the recursion slows down on both sides of it), and a launch lasts as long as its
+// slowest point.
 static ndgsbp_status ga_threshold(const GaArgs& a, bool groups, double lo_db, double hi_db, double tol_db,
                                   double* threshold_db, const char* who) {
-    constexpr int n = 64;
-    std::vector<double> e(n), mu(n);
-    std::vector<uint8_t> cv(n);
-    std::vector<int32_t> it(n);
+    constexpr int n_max = 64;
+    std::vector<double> e(n_max), mu(n_max);
+    std::vector<uint8_t> cv(n_max);
+    std::vector<int32_t> it(n_max);
     for (int round = 0; round < 16; ++round) {
+        const double need = std::ceil((hi_db - lo_db) / tol_db) + 1.0;
+        const int n = need < n_max ? std::max(3, (int)need) : n_max;
         for (int k = 0; k < n; ++k) e[k] = lo_db + (hi_db - lo_db) * k / (n - 1);
         ndgsbp_status st = ga_run(a, groups, e.data(), n, cv.data(), it.data(), mu.data());
         if (st) return st;
