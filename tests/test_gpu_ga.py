@@ -82,6 +82,21 @@ def test_gpu_group_ga_matches_oracle(nd, G, r):
         assert mu[k] == pytest.approx(m, rel=1e-9 if not c else 1e-6)
 
 
+@pytest.mark.parametrize("G", [12, 36])
+def test_gpu_group_ga_irregular_profile(nd, G):
+    """The group recursion on the n=2304 QC code's profile (VN degrees {2,3,6}, CN degrees {6,7}),
+    r = 0.4: 19 class-b weight terms per group, so G = 12 reads them from the per-point table and
+    G = 36 (665 terms) computes them in the loop; both equal the oracle."""
+    prof = I.degree_profile(I.code_by_name("qc_n2304_r12"))
+    lam, rho = prof["lambda"], prof["rho"]
+    snr = np.array([0.3, 0.6, 1.2, 2.0])
+    cv, it, mu = nd.ga_groups(lam, rho, 0.5, G, 0.4, snr, phi_kind=nd.GA_PHI_CLOSED)
+    for k, e in enumerate(snr):
+        c, i, m = ga.group_ga(float(e), lam, rho, 0.5, G, 0.4, kind="approx")
+        assert (cv[k], it[k]) == (c, i), (G, e, it[k], i)
+        assert mu[k] == pytest.approx(m, rel=1e-9 if not c else 1e-6)
+
+
 def test_gpu_group_ga_exact_phi(nd):
     """The exact Eq. (14) (trapezoidal on the GPU, Gauss-Hermite in the oracle) on points well
     above and below the threshold, G = 4, r = 0.4."""
