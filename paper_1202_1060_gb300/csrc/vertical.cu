@@ -228,11 +228,21 @@ struct VArgs {
     void* ws_slots;      // [grid][slot_bytes]
     long long slot_bytes;
     int msg_bytes;       // E messages rounded up to 16 bytes
+    int cidx_off;        // kernels with CSMEM: byte offset in shared memory of a copy of col_idx (E entries)
 };
+
+// Column index i: from the shared-memory copy (CSMEM) or through the read-only cache.
+template <bool CSMEM>
+__device__ __forceinline__ int32_t col_at(const int32_t* __restrict__ col_idx, int i) {
+    if constexpr (CSMEM)
+        return col_idx[i];
+    else
+        return __ldg(col_idx + i);
+}
 
 // Eq. (1) for one group edge (row position k) of a CN of degree d: the product over the CN's
 // other edges directly, in the same (N, E) pair form.  A CN of degree 1 gives +lim.
-template <typename MsgT>
+template <bool CSMEM, typename MsgT>
 __device__ __forceinline__ float vertical_edge_message(const float* __restrict__ P, const MsgT* msg,
                                                        const int32_t* __restrict__ col_idx, int b, int d, int k,
                                                        float lim) {
@@ -240,7 +250,7 @@ __device__ __forceinline__ float vertical_edge_message(const float* __restrict__
     float cn = 1.f, ce = 0.f;
     for (int j = 0; j < d; ++j) {
         if (j == k) continue;
-        const float v = P[__ldg(col_idx + b + j)] - to_f(msg[b + j]);   // L_{n'->m} = P_n' - L_{m->n'}
+        const float v = P[col_at<CSMEM>(col_idx, b + j)] - to_f(msg[b + j]);   // L_{n'->m} = P_n' - L_{m->n'}
         par ^= __float_as_uint(v);
         const float u = ex2_approx(-fminf(fabsf(v), lim));
         ce = fmaf(ce, fmaf(0.5f, u, 0.5f), cn * u);
@@ -258,7 +268,7 @@ __device__ __forceinline__ float vertical_edge_message(const float* __restrict__
 // clipped to lim.  Only the row positions in mask (the group's edges) get an output: written to
 // stage[out[i]], the i-th set bit of mask counted from position 0.  A CN of degree 1 gives +lim
 // (the empty product is 1).
-template <int MAXDC, typename MsgT>
+template <int MAXDC, bool CSMEM, typename MsgT>
 __device__ __forceinline__ void vertical_cn_task(const float* __restrict__ P, const MsgT* msg,
                                                  const int32_t* __restrict__ col_idx, int b, int d, unsigned mask,
                                                  const int32_t* __restrict__ out, float* stage, float lim) {
@@ -268,7 +278,7 @@ __device__ __forceinline__ void vertical_cn_task(const float* __restrict__ P, co
 #pragma unroll
     for (int k = 0; k < MAXDC; ++k) {
         if (k < d) {
-            const float v = P[__ldg(col_idx + b + k)] - to_f(msg[b + k]);   // L_{n->m} = P_n - L_{m->n}
+            const float v = P[col_at<CSMEM>(col_idx, b + k)] - to_f(msg[b + k]);   // L_{n->m} = P_n - L_{m->n}
             const unsigned tb = __float_as_uint(v);
             par ^= tb;
             const float u = ex2_approx(-fminf(fabsf(v), lim));
@@ -301,7 +311,9 @@ __device__ __forceinline__ void vertical_cn_task(const float* __restrict__ P, co
     }
 }
 
-template <typename MsgT, int MAXDC, bool PCN>
+// CSMEM: col_idx read from a shared-memory copy (the plan found room for it without losing a CTA
+// per SM), else through the read-only cache.
+template <typename MsgT, int MAXDC, bool PCN, bool CSMEM>
 __global__ void __launch_bounds__(512) vertical_decode_kernel(const VArgs a) {
     extern __shared__ __align__(16) unsigned char vsm[];
     __shared__ long long s_frame;
@@ -317,6 +329,14 @@ __global__ void __launch_bounds__(512) vertical_decode_kernel(const VArgs a) {
     MsgT* msg = reinterpret_cast<MsgT*>(a.msg_smem ? rest : slot);
     float* stage = reinterpret_cast<float*>(a.stage_smem ? (a.msg_smem ? rest + a.msg_bytes : rest)
                                                          : (a.msg_smem ? slot : slot + a.msg_bytes));
+    // the column indices, read d times per edge output (the copy is made once; next_frame's
+    // barrier orders it)
+    const int32_t* col_idx = t.col_idx;
+    if constexpr (CSMEM) {
+        int32_t* cs = reinterpret_cast<int32_t*>(vsm + a.cidx_off);
+        for (int e = tid; e < E; e += nt) cs[e] = __ldg(t.col_idx + e);
+        col_idx = cs;
+    }
     if (tid == 0) s_err = 0u;
     for (long long f = next_frame(r, &s_frame); f < r.n_frames; f = next_frame(r, &s_frame)) {
         if (r.start_ns && tid == 0) r.start_ns[f] = global_timer_ns();
@@ -335,14 +355,14 @@ __global__ void __launch_bounds__(512) vertical_decode_kernel(const VArgs a) {
                     const int t1 = __ldg(t.gtask_ptr + g + 1);
                     for (int i = __ldg(t.gtask_ptr + g) + tid; i < t1; i += nt) {
                         const int4 tk = __ldg(t.vtask + i);
-                        vertical_cn_task<MAXDC>(P, msg, t.col_idx, tk.x, tk.y, static_cast<unsigned>(tk.z),
+                        vertical_cn_task<MAXDC, CSMEM>(P, msg, col_idx, tk.x, tk.y, static_cast<unsigned>(tk.z),
                                                 t.vtout + tk.w, stage, lim);
                     }
                 } else {
                     const int a1 = __ldg(t.vn_epos + v1);
                     for (int q = a0 + tid; q < a1; q += nt) {
                         const int4 ge = __ldg(t.gtab + q);
-                        stage[q - a0] = vertical_edge_message(P, msg, t.col_idx, ge.y, ge.z, ge.w, lim);
+                        stage[q - a0] = vertical_edge_message<CSMEM>(P, msg, col_idx, ge.y, ge.z, ge.w, lim);
                     }
                 }
                 __syncthreads();
@@ -365,7 +385,7 @@ __global__ void __launch_bounds__(512) vertical_decode_kernel(const VArgs a) {
             for (int m = tid; m < a.M && !bad; m += nt) {
                 bool p = false;
                 const int e1 = __ldg(t.row_ptr + m + 1);
-                for (int e = __ldg(t.row_ptr + m); e < e1; ++e) p ^= P[__ldg(t.col_idx + e)] < 0.f;
+                for (int e = __ldg(t.row_ptr + m); e < e1; ++e) p ^= P[col_at<CSMEM>(col_idx, e)] < 0.f;
                 bad = p;
             }
             unsat = __syncthreads_or(bad);
@@ -379,27 +399,33 @@ __global__ void __launch_bounds__(512) vertical_decode_kernel(const VArgs a) {
 
 typedef void (*VKernelFn)(const VArgs);
 
-template <typename MsgT>
+template <typename MsgT, bool CSMEM>
 static VKernelFn pick_vertical_degree(int maxdc, bool per_cn) {
-    if (!per_cn) return vertical_decode_kernel<MsgT, 8, false>;   // the degree bound is not used
-    if (maxdc <= 8) return vertical_decode_kernel<MsgT, 8, true>;
-    if (maxdc <= 16) return vertical_decode_kernel<MsgT, 16, true>;
-    if (maxdc <= 32) return vertical_decode_kernel<MsgT, 32, true>;
+    if (!per_cn) return vertical_decode_kernel<MsgT, 8, false, CSMEM>;   // the degree bound is not used
+    if (maxdc <= 8) return vertical_decode_kernel<MsgT, 8, true, CSMEM>;
+    if (maxdc <= 16) return vertical_decode_kernel<MsgT, 16, true, CSMEM>;
+    if (maxdc <= 32) return vertical_decode_kernel<MsgT, 32, true, CSMEM>;
     return nullptr;
 }
 
-static VKernelFn pick_vertical_kernel(int msg_dtype, int maxdc, bool per_cn) {
+template <bool CSMEM>
+static VKernelFn pick_vertical_csmem(int msg_dtype, int maxdc, bool per_cn) {
     switch (msg_dtype) {
-        case NDGSBP_F16: return pick_vertical_degree<__half>(maxdc, per_cn);
-        case NDGSBP_BF16: return pick_vertical_degree<__nv_bfloat16>(maxdc, per_cn);
-        default: return pick_vertical_degree<float>(maxdc, per_cn);
+        case NDGSBP_F16: return pick_vertical_degree<__half, CSMEM>(maxdc, per_cn);
+        case NDGSBP_BF16: return pick_vertical_degree<__nv_bfloat16, CSMEM>(maxdc, per_cn);
+        default: return pick_vertical_degree<float, CSMEM>(maxdc, per_cn);
     }
+}
+
+static VKernelFn pick_vertical_kernel(int msg_dtype, int maxdc, bool per_cn, bool csmem) {
+    return csmem ? pick_vertical_csmem<true>(msg_dtype, maxdc, per_cn)
+                 : pick_vertical_csmem<false>(msg_dtype, maxdc, per_cn);
 }
 
 // ---- planning --------------------------------------------------------------------------------
 struct VPlan {
     VKernelFn fn = nullptr;
-    int threads = 0, per_sm = 0, msg_smem = 0, stage_smem = 0, msg_bytes = 0;
+    int threads = 0, per_sm = 0, msg_smem = 0, stage_smem = 0, msg_bytes = 0, cidx_off = -1;
     size_t smem = 0, slot_bytes = 0;
     int64_t grid = 0, ws_bytes = 0;
 };
@@ -442,7 +468,7 @@ static ndgsbp_status make_vplan(const ndgsbp_vgroups* h, const ndgsbp_params* p,
     if (k == k1)
         return fail(NDGSBP_ERR_UNSUPPORTED, "vertical: %d VNs and %lld edges do not fit in %d bytes of shared memory%s",
                     c.N, static_cast<long long>(c.E), optin, p->variant == NDGSBP_VARIANT_SMEM ? " (variant SMEM)" : "");
-    vp.fn = pick_vertical_kernel(p->msg_dtype, c.max_row, h->per_cn);
+    vp.fn = pick_vertical_kernel(p->msg_dtype, c.max_row, h->per_cn, false);
     vp.msg_smem = opts[k][0];
     vp.stage_smem = opts[k][1];
     vp.msg_bytes = static_cast<int>(mb);
@@ -454,6 +480,20 @@ static ndgsbp_status make_vplan(const ndgsbp_vgroups* h, const ndgsbp_params* p,
     VCUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(vp.smem)));
     VCUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vp.per_sm, fn, vp.threads, vp.smem));
     if (vp.per_sm < 1) return fail(NDGSBP_ERR_UNSUPPORTED, "vertical kernel does not fit on an SM with %d threads", vp.threads);
+    // the kernel reading a copy of col_idx placed after the rest, when it costs no CTA per SM
+    const size_t cb = a16(4 * static_cast<size_t>(c.E));
+    if (vp.smem + cb <= static_cast<size_t>(optin)) {
+        const VKernelFn fn2 = pick_vertical_kernel(p->msg_dtype, c.max_row, h->per_cn, true);
+        const void* f2 = reinterpret_cast<const void*>(fn2);
+        int per_sm2 = 0;
+        VCUDA_TRY(cudaFuncSetAttribute(f2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(vp.smem + cb)));
+        VCUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, f2, vp.threads, vp.smem + cb));
+        if (per_sm2 >= vp.per_sm) {
+            vp.fn = fn2;
+            vp.cidx_off = static_cast<int>(vp.smem);
+            vp.smem += cb;
+        }
+    }
     if (p->ctas_per_sm > 0) vp.per_sm = std::min(vp.per_sm, p->ctas_per_sm);
     vp.grid = std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(vp.per_sm) * sms, std::max<int64_t>(n_frames, 1)));
     vp.ws_bytes = static_cast<int64_t>(kVHeaderBytes) + vp.grid * static_cast<int64_t>(vp.slot_bytes);
@@ -595,6 +635,7 @@ ndgsbp_status ndgsbp_decode_vertical(const ndgsbp_vgroups* vg, const ndgsbp_para
     a.ws_slots = ws + kVHeaderBytes;
     a.slot_bytes = static_cast<long long>(vp.slot_bytes);
     a.msg_bytes = vp.msg_bytes;
+    a.cidx_off = vp.cidx_off;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VCUDA_TRY(cudaMemsetAsync(ws, 0, 16, s));   // frame counter
     vp.fn<<<static_cast<unsigned>(vp.grid), vp.threads, vp.smem, s>>>(a);
