@@ -50,6 +50,9 @@ struct GaArgs {
     double* mu;
     int G;        // groups (ga_group_kernel)
     double r;     // overlap ratio (ga_group_kernel)
+    // closed form: Phi(10-), Phi(10) and Phi(0+), which only sort p into the cases of
+    // ga_phi_inv_closed (with a 1e-9 relative margin; computed on the host)
+    double p_left, p_right, p_zero;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -122,12 +125,10 @@ __device__ double ga_bisect_closed(double p, double lo, double hi, int steps, in
 // so the bisection starts from the bracket five levels above the last one (the level at which
 // the width first meets the stop test), when both its ends are that far from r, and runs from
 // [0, 200] otherwise (the band, p near Phi(0+), or an end within delta).
-__device__ double ga_phi_inv_closed(double p, double phi_top, int lane) {
+__device__ double ga_phi_inv_closed(const GaArgs& a, double p, double phi_top, int lane) {
     if (phi_top >= p) return 200.0;
-    const double p_left = exp(-0.4527 * pow(10.0, 0.86) + 0.0218);
-    const double p_right = sqrt(M_PI / 10.0) * exp(-10.0 / 4.0) * (1.0 - 10.0 / 70.0);
-    const bool left = p > p_right * (1.0 + 1e-9) && p < exp(0.0218) * (1.0 - 1e-9);
-    if (!left && !(p < p_left * (1.0 - 1e-9))) return ga_bisect_closed(p, 0.0, 200.0, 0, lane);
+    const bool left = p > a.p_right * (1.0 + 1e-9) && p < a.p_zero * (1.0 - 1e-9);
+    if (!left && !(p < a.p_left * (1.0 - 1e-9))) return ga_bisect_closed(p, 0.0, 200.0, 0, lane);
     const double lp = log(p);
     double r;
     if (left) {
@@ -159,8 +160,8 @@ __device__ double ga_phi_inv_closed(double p, double phi_top, int lane) {
 }
 
 // phi_top = Phi(200), the upper end of the search (the same in every call of a kernel).
-__device__ double ga_phi_inv(double p, double phi_top, int kind, int lane) {
-    if (kind == NDGSBP_GA_PHI_CLOSED) return ga_phi_inv_closed(p, phi_top, lane);
+__device__ double ga_phi_inv(const GaArgs& a, double p, double phi_top, int kind, int lane) {
+    if (kind == NDGSBP_GA_PHI_CLOSED) return ga_phi_inv_closed(a, p, phi_top, lane);
     if (p >= 1.0) return 0.0;
     double lo = 0.0, hi = 200.0;
     if (phi_top >= p) return hi;
@@ -182,7 +183,7 @@ __device__ double ga_cn_mean(const GaArgs& a, const double* mu_v, double phi_top
         if (a.lam[i] > 0.0) s += a.lam[i] * ga_phi(mu_v[i], a.kind, lane);
     double next = 0.0;
     for (int j = 2; j <= a.dc_max; ++j)
-        if (a.rho[j] > 0.0) next += a.rho[j] * ga_phi_inv(1.0 - pow(1.0 - s, j - 1), phi_top, a.kind, lane);
+        if (a.rho[j] > 0.0) next += a.rho[j] * ga_phi_inv(a, 1.0 - pow(1.0 - s, j - 1), phi_top, a.kind, lane);
     return next;
 }
 
@@ -360,6 +361,9 @@ static bool ga_args(GaArgs& a, const double* lambda, int32_t dv_max, const doubl
     a.mu_cap = mu_cap;
     a.G = 1;
     a.r = 0.0;
+    a.p_left = std::exp(-0.4527 * std::pow(10.0, 0.86) + 0.0218);
+    a.p_right = std::sqrt(M_PI / 10.0) * std::exp(-10.0 / 4.0) * (1.0 - 10.0 / 70.0);
+    a.p_zero = std::exp(0.0218);
     return true;
 }
 
